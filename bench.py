@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Benchmark: candidate-transaction tests/s and DIC mine time on one GB300.
+
+A step is one complete mining call (first pass, pair join and every stop of
+Algorithm 2's loop until DASHED is empty, result on the host) over the
+paper-scale planted-pattern database (n=1,000,000 rows, m=1,000 items,
+minsup 0.25% = 2,500, M=10,000), resident in HBM when the timed region starts.
+The L2 cache is flushed (a 512 MiB write) before every timed step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (the plain serial restatement of the
+paper's algorithm) on the host cores instead, on a bounded sample of the same
+workload. With N > 1 (torchrun) every rank mines its own replica; the value is
+the sum of tests over all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "candidate-transaction tests/s (DIC mine, bit-exact)"
+UNIT = "tests/s"
+# One sample of the oracle for the CPU figures: the first pass over all rows
+# plus the first stop of all pair candidates over a block of this many rows.
+CPU_SAMPLE_M = 1_000
+
+# Algorithmic integer work of one containment test in the ROWS kernel for a
+# 2-itemset (the candidates that make up >99.9% of this workload's tests):
+# one LOP3 per touched 32-bit half (2) + one compare + one add.
+ROWS_OPS_PER_TEST = 4
+# Derived ALU peak: 152 SMs x 64 INT32 lanes x 2070 MHz (max SM clock).
+ALU_PEAK_TOPS = 152 * 64 * 2.070e9 / 1e12
+
+
+def workload(name: str):
+    if name == "paper-scale":
+        return synth.planted_paper_scale()
+    if name == "planted-small":
+        return synth.planted_small()
+    if name == "dense":
+        return synth.dense_zipf()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=d.get("hbm_gbs", 6800.0), bf16=d.get("bf16_tflops", 1900.0),
+                    bf16_sus=d.get("bf16_tflops_sustained", 1700.0), source="measured")
+    return dict(hbm_gbs=6800.0, bf16=1900.0, bf16_sus=1700.0, source="fallback")
+
+
+class Clocks:
+    """nvidia-smi sampling every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        with open(self.f.name) as f:
+            lines = [ln.strip() for ln in f if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_sample(db):
+    """Time the oracle on the bounded sample; returns (tests/s, tests, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.dic(db.row_ptr, db.items, db.n, db.m, db.minsup, CPU_SAMPLE_M, max_stops=1)
+    dt = time.perf_counter() - t0
+    return r.tests / dt, r.tests, dt
+
+
+def cpu_sample_desc(db):
+    return (f"oracle (serial C++ ParallelDIC) on the same database: first pass over all "
+            f"{db.n} rows + the first stop of all pair candidates over a {CPU_SAMPLE_M}-row "
+            f"block (M={CPU_SAMPLE_M} instead of {db.M} to bound the sample)")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    db = workload(args.workload)
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        cpu_sample(db)
+    tests, secs = 0, 0.0
+    for _ in range(args.steps):
+        _, t, dt = cpu_sample(db)
+        tests += t
+        secs += dt
+    v = tests / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": db.name, "n": db.n, "m": db.m,
+                                        "minsup": db.minsup, "M": CPU_SAMPLE_M,
+                                        "sample": "first pass + first stop"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cpu_sample_desc(db)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper-scale")
+    ap.add_argument("--path", default="auto", choices=["auto", "rows", "bitslice", "tensor"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1812_10959_gb300 import build as pb
+    pb.build()
+    import paper_1812_10959_gb300 as dic
+
+    db = workload(args.workload)
+    handle = dic.load_db_csr(db.row_ptr, db.items, db.n, db.m)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream)
+    ref_count = len(res.k)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = []
+    stats = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream, profile=True)
+            b.record(stream)
+            evs.append((a, b))
+            stats.append(res.stats)
+            assert len(res.k) == ref_count
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(ms) / 1000.0
+    tests_step = stats[0]["tests"]
+    tests_all = tests_step * args.steps
+    t_max = total_s
+    if world > 1:
+        tt = torch.tensor([total_s, float(tests_all)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_max, tests_all = float(mx[0]), float(tt[1])
+    value = tests_all / t_max
+
+    # ---- end to end through the C ABI from host buffers: the rows as CSR
+    # item lists in pinned host memory are copied in, packed on the device,
+    # mined, and the result read back, every step
+    rp_h = torch.from_numpy(db.row_ptr.view(np.int64)).pin_memory()
+    it_h = torch.from_numpy(db.items.view(np.int32)).pin_memory()
+    e2e_s = 0.0
+    d2h = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2 = dic.load_db_csr(rp_h, it_h, db.n, db.m)
+        r2 = dic.mine(h2, db.minsup, db.M, path=args.path)
+        h2.free()
+        e2e_s += time.perf_counter() - t0
+        d2h = r2.masks.nbytes + r2.k.nbytes + r2.support.nbytes + r2.trace.nbytes
+    h2d = rp_h.numel() * 8 + it_h.numel() * 4
+    e2e_v = tests_step * args.steps / e2e_s
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_v = tests_step * args.steps * world / float(tt[0])
+
+    # ---- roofline of the dominant kernel (the count kernel), timed live
+    count_ms = sum(s["count_ms"] for s in stats)
+    count_launches = sum(s["count_launches"] for s in stats)
+    count_tests = sum(s["tests"] - db.m * db.n for s in stats)
+    avg_ms = count_ms / max(count_launches, 1)
+    ops_per_launch = count_tests * ROWS_OPS_PER_TEST / max(count_launches, 1)
+    achieved = ops_per_launch / (avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
+                "frac": achieved / ALU_PEAK_TOPS, "traffic": None,
+                "kernel": "k_count_rows", "count_share_of_step": count_ms / sum(ms)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, t, dt = cpu_sample(db)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": cpu_sample_desc(db) + f" ({t} tests in {dt:.1f} s)"}
+
+    launches = sum(s["kernel_launches"] for s in stats)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": db.name, "n": db.n, "m": db.m, "minsup": db.minsup,
+                       "M": db.M, "count_path": args.path, "tests_per_step": tests_step,
+                       "frequent_itemsets": ref_count, "l2": "flushed (512 MiB write) per step",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "stats": stats[0],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

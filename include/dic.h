@@ -1,0 +1,199 @@
+/*
+ * dic.h -- C ABI of the GB300 (sm_103a) Dynamic Itemset Counting library.
+ *
+ * The library mines all frequent itemsets of a transaction database, the
+ * problem stated in Section 1 of Zymbler, "Parallel Algorithm for Frequent
+ * Itemset Mining on Intel Many-core Systems": given rows T_1..T_n over items
+ * 0..m-1 and a threshold minsup, return every non-empty itemset X with
+ * supp(X) = |{t : X subset of T_t}| >= minsup, with its exact support.
+ *
+ * It follows ParallelDIC (Algorithm 2): a full first pass counts the
+ * 1-itemsets (Section 4.2), every pair of frequent items becomes a candidate,
+ * and the database is then scanned in blocks of M rows with rewind; after
+ * each block the candidates' supports are counted (Algorithm 3), circles are
+ * promoted or pruned (Algorithm 4), new candidates are generated from the
+ * itemsets promoted at this stop (Section 4.2 text and Algorithm 1), and
+ * itemsets that completed a full pass are solidified (Algorithm 5).
+ * Transactions and itemsets use the direct bit representation of Section
+ * 4.1, generalised to W = ceil(m/64) 64-bit words: item p is bit p%64 of
+ * word p/64.
+ *
+ * Conventions for every entry point:
+ *   - Status codes only; no exceptions, exit() or device traps cross the ABI.
+ *   - Out-pointers are written only on DIC_OK and set to NULL otherwise.
+ *   - dic_last_error() returns a thread-local detail string for the last
+ *     failing call on the calling thread.
+ *   - A dic_db is read-only while mining and may be shared by queries.
+ *   - All device work runs on the CUDA device that is current on the calling
+ *     thread when the dic_db is created.
+ */
+#ifndef DIC_H
+#define DIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIC_ABI_VERSION 1u
+
+typedef enum {
+  DIC_OK = 0,
+  DIC_EINVAL = 1,     /* invalid argument or malformed database            */
+  DIC_ENOMEM = 2,     /* host or device allocation failed                  */
+  DIC_ECUDA = 3,      /* CUDA runtime error (detail in dic_last_error)     */
+  DIC_ECAPACITY = 4,  /* a configured limit would be exceeded; never a
+                         silently truncated result                         */
+  DIC_ETIMEOUT = 5,   /* a bounded device-side wait gave up                */
+  DIC_EBUSY = 6       /* object still in use (e.g. queries in flight)      */
+} dic_status;
+
+typedef struct dic_db dic_db;
+typedef struct dic_result dic_result;
+
+/* Support-counting kernel used for Algorithm 3 (COUNTSUPPORT). All paths
+ * give identical supports; they differ only in speed.
+ *   ROWS      the paper's test (T AND C) == C on row-major bitmaps, one
+ *             candidate per thread, rows staged through shared memory.
+ *   BITSLICE  the block is transposed into per-item bit columns; a
+ *             candidate's count over 32 rows is popc of the AND of its
+ *             items' column words.
+ *   TENSOR    matched-item counts as a 0/1 GEMM (rows x items times items x
+ *             candidates) on tcgen05 with an exact compare-to-|C| epilogue.
+ *   AUTO      chosen per stop by the built-in tuner. */
+typedef enum {
+  DIC_COUNT_AUTO = 0,
+  DIC_COUNT_ROWS = 1,
+  DIC_COUNT_BITSLICE = 2,
+  DIC_COUNT_TENSOR = 3
+} dic_count_path;
+
+/* Mining options. Initialise with dic_options_init(); unknown trailing
+ * fields are ignored by older libraries (struct_size). */
+typedef struct {
+  uint32_t struct_size;
+  uint32_t count_path;      /* dic_count_path                              */
+  uint32_t steps_per_sync;  /* stops enqueued between host checks; 0=auto  */
+  uint32_t use_graph;       /* 1: replay stop loops as CUDA graphs         */
+  uint32_t profile;         /* 1: time count kernels with CUDA events      */
+  uint32_t max_candidates;  /* 0 = no limit; else DIC_ECAPACITY beyond it  */
+  uint32_t reserved[10];
+} dic_options;
+
+/* Per-run statistics (dic_result_stats). */
+typedef struct {
+  uint64_t tests;           /* candidate-transaction tests: m*n for the
+                               first pass plus sum over stops of
+                               |DASHED| * |block|                          */
+  uint64_t stops;           /* iterations of Algorithm 2's loop            */
+  uint64_t candidates;      /* candidates ever created (incl. pairs)       */
+  uint64_t frequent;        /* itemsets in the result                      */
+  uint32_t l1;              /* frequent items                              */
+  uint32_t words;           /* W = ceil(m/64)                              */
+  uint32_t words_compact;   /* W' = ceil(l1/64)                            */
+  uint32_t kernel_launches; /* kernels launched by this run                */
+  double count_ms;          /* summed count-kernel time (profile=1 only)   */
+  uint64_t count_launches;  /* count-kernel launches timed                 */
+  double firstpass_ms;      /* first-pass kernel time (profile=1 only)     */
+  double mine_ms;           /* wall time of the mining call (host clock)   */
+  uint32_t path_launches[4];/* count launches per dic_count_path           */
+  uint32_t reserved[8];
+} dic_stats;
+
+/* Columns of one trace row (one per iteration of Algorithm 2's loop). */
+#define DIC_TRACE_COLS 9u
+/* step stop first last dashed promoted pruned generated solidified:
+ *   step       global stop counter (1-based, never wraps)
+ *   stop       block number 1..stop_max (wraps: the rewind of Algorithm 2)
+ *   first,last block rows [first, last)
+ *   dashed     |DASHED| counted at this stop
+ *   promoted   circles moved to Dashed Box (Algorithm 4)
+ *   pruned     circles dropped by the support bound (Algorithm 4)
+ *   generated  new candidates (MAKECANDIDATES)
+ *   solidified itemsets moved to SOLID (Algorithm 5)                       */
+
+/* ------------------------------------------------------------ databases */
+
+/* Load a database from HOST bitmaps: words[n*W] row-major, W = ceil(m/64),
+ * bit p%64 of word p/64 set iff item p is in the row (Section 4.1). The data
+ * is copied to the device; the caller keeps ownership of `words`.
+ * DIC_EINVAL: m == 0, n >= 2^31, words == NULL with n > 0, or a set bit at
+ * an item position >= m. */
+dic_status dic_load_db(const uint64_t *words, uint64_t n, uint32_t m, dic_db **out);
+
+/* Load a database from HOST item lists (CSR): row t holds
+ * items[row_ptr[t] .. row_ptr[t+1]); duplicates are allowed (set
+ * semantics); row_ptr[0] must be 0 and row_ptr non-decreasing. The rows are
+ * bit-packed on the device. DIC_EINVAL on an item >= m or a bad row_ptr. */
+dic_status dic_load_db_csr(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
+                           dic_db **out);
+
+/* Load a database from DEVICE bitmaps (same layout as dic_load_db), e.g. a
+ * torch tensor's data_ptr. The words are copied (device to device) on
+ * `stream` (a cudaStream_t; NULL = legacy default stream); the caller may
+ * release its buffer once the call returns. */
+dic_status dic_load_db_device(const uint64_t *dev_words, uint64_t n, uint32_t m, void *stream,
+                              dic_db **out);
+
+/* Release a database. DIC_EBUSY while a mining call on it is running. */
+dic_status dic_db_free(dic_db *db);
+
+uint64_t dic_db_rows(const dic_db *db);
+uint32_t dic_db_items(const dic_db *db);
+/* Device address of the resident bitmaps (n*W words), for inspection. */
+const uint64_t *dic_db_device_words(const dic_db *db);
+
+/* --------------------------------------------------------------- mining */
+
+/* Fill `opt` with defaults (AUTO path, graphs on, no profiling). */
+void dic_options_init(dic_options *opt);
+
+/* Mine all itemsets with support >= minsup_count using blocks of M rows.
+ * Synchronous; runs on an internal stream. M > n is treated as M = n; n = 0
+ * gives an empty result. DIC_EINVAL: minsup_count == 0 or M == 0.
+ * The result owns host copies of the itemsets (see dic_result_copy). */
+dic_status dic_mine(const dic_db *db, uint32_t minsup_count, uint64_t M, dic_result **out);
+
+/* As dic_mine, with options and a caller stream (cudaStream_t or NULL for
+ * an internal stream). Returns when the result is on the host. */
+dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint64_t M,
+                       const dic_options *opt, void *stream, dic_result **out);
+
+/* Mine `count` independent queries (dbs[i], minsup[i], M[i]) together: all
+ * lattices advance one stop per round and every count phase of a round is
+ * one persistent launch over all queries' candidates. out[i] receives each
+ * result; on failure every out[i] is NULL. */
+dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *minsup, const uint64_t *M,
+                          uint32_t count, const dic_options *opt, dic_result **out);
+
+/* ------------------------------------------------------------- results */
+
+/* Number of frequent itemsets (1-itemsets included). */
+uint64_t dic_result_count(const dic_result *r);
+/* Words per itemset mask in dic_result_copy (= W of the database). */
+uint32_t dic_result_words(const dic_result *r);
+/* Copy the itemsets in canonical order (size, then lexicographic by
+ * ascending item ids): masks[count*W], k[count], support[count]. Any of the
+ * three pointers may be NULL to skip it. */
+dic_status dic_result_copy(const dic_result *r, uint64_t *masks, uint32_t *k, uint32_t *support);
+/* Number of trace rows (= stops run). */
+uint64_t dic_result_trace_len(const dic_result *r);
+/* Copy the per-stop trace: rows[len * DIC_TRACE_COLS]. */
+dic_status dic_result_trace(const dic_result *r, uint64_t *rows);
+dic_status dic_result_stats(const dic_result *r, dic_stats *out);
+void dic_result_free(dic_result *r);
+
+/* ---------------------------------------------------------------- misc */
+
+/* ceil(frac * n) as an integer support count, at least 1 (the fraction of
+ * Section 1 mapped to the integer threshold the algorithms compare with). */
+uint32_t dic_minsup_count(uint64_t n, double frac);
+const char *dic_status_str(dic_status s);
+const char *dic_last_error(void);
+uint32_t dic_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIC_H */

@@ -53,7 +53,7 @@ def _load():
         pres = ctypes.POINTER(vp)
         for name in ("oracle_dic", "oracle_dic_classic"):
             f = getattr(lib, name)
-            f.argtypes = [vp, vp, u64, u32, u32, u64, pres]
+            f.argtypes = [vp, vp, u64, u32, u32, u64, u64, pres]
             f.restype = ctypes.c_int
         for name in ("oracle_apriori", "oracle_bruteforce"):
             f = getattr(lib, name)
@@ -126,15 +126,17 @@ def _run(name, row_ptr, items, n, m, *args) -> OracleResult:
     return _result(h)
 
 
-def dic(row_ptr, items, n: int, m: int, minsup: int, M: int) -> OracleResult:
+def dic(row_ptr, items, n: int, m: int, minsup: int, M: int, max_stops: int = 0) -> OracleResult:
     """ParallelDIC (Algorithm 2): first pass, then COUNT / PRUNE /
-    MAKECANDIDATES / CHECKFULLPASS per block of M rows with rewind."""
-    return _run("oracle_dic", row_ptr, items, n, m, minsup, M)
+    MAKECANDIDATES / CHECKFULLPASS per block of M rows with rewind.
+    max_stops > 0 ends after that many stops (timing samples only)."""
+    return _run("oracle_dic", row_ptr, items, n, m, minsup, M, max_stops)
 
 
-def dic_classic(row_ptr, items, n: int, m: int, minsup: int, M: int) -> OracleResult:
+def dic_classic(row_ptr, items, n: int, m: int, minsup: int, M: int,
+                max_stops: int = 0) -> OracleResult:
     """Serial DIC of Algorithm 1 (every 1-itemset starts as a dashed circle)."""
-    return _run("oracle_dic_classic", row_ptr, items, n, m, minsup, M)
+    return _run("oracle_dic_classic", row_ptr, items, n, m, minsup, M, max_stops)
 
 
 def apriori(row_ptr, items, n: int, m: int, minsup: int) -> OracleResult:

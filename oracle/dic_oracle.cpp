@@ -118,11 +118,13 @@ std::vector<Mask> pack_all(const uint64_t *row_ptr, const uint32_t *items, uint6
 // form of Algorithm 1 (DASHED holds all 1-itemset circles).
 void dic_loop(const std::vector<Mask> &B, uint64_t n, uint32_t m, uint32_t minsup, uint64_t M,
               std::vector<Itemset> &SOLID, std::vector<Itemset> &DASHED,
-              std::map<Mask, uint64_t> &boxes, std::set<Mask> &ever, Result *r) {
+              std::map<Mask, uint64_t> &boxes, std::set<Mask> &ever, Result *r,
+              uint64_t max_stops) {
   const uint32_t W = words_for(m);
   const uint64_t stop_max = (n + M - 1) / M;
   uint64_t stop = 0, step = 0;
   while (!DASHED.empty()) {
+    if (max_stops && step == max_stops) break;  // timing samples only
     // Scan the database and rewind if necessary.
     ++step;
     stop = stop + 1;
@@ -257,8 +259,10 @@ int oracle_pack(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint
 }
 
 // ParallelDIC (Algorithm 2), serial.
+// max_stops > 0 ends the loop after that many stops (a bounded timing sample;
+// the itemsets are then incomplete). 0 runs to completion.
 int oracle_dic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
-               uint32_t minsup, uint64_t M, oracle_result **out) {
+               uint32_t minsup, uint64_t M, uint64_t max_stops, oracle_result **out) {
   *out = nullptr;
   if (m == 0 || minsup == 0 || M == 0) return -1;
   Result *r = new Result();
@@ -297,7 +301,7 @@ int oracle_dic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint3
       ever.insert(J.mask);
       DASHED.push_back(J);
     }
-  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r);
+  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r, max_stops);
   collect(SOLID, r);
   *out = r;
   return 0;
@@ -305,7 +309,7 @@ int oracle_dic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint3
 
 // Serial DIC of Algorithm 1: Dashed Circle starts with all 1-itemsets.
 int oracle_dic_classic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
-                       uint32_t minsup, uint64_t M, oracle_result **out) {
+                       uint32_t minsup, uint64_t M, uint64_t max_stops, oracle_result **out) {
   *out = nullptr;
   if (m == 0 || minsup == 0 || M == 0) return -1;
   Result *r = new Result();
@@ -323,7 +327,7 @@ int oracle_dic_classic(const uint64_t *row_ptr, const uint32_t *items, uint64_t 
     DASHED.push_back(I);
   }
   std::map<Mask, uint64_t> boxes;
-  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r);
+  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r, max_stops);
   collect(SOLID, r);
   *out = r;
   return 0;

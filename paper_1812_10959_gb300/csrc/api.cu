@@ -1,0 +1,756 @@
+// C ABI of the DIC library (include/dic.h): database loading, the host side
+// of ParallelDIC's stop loop (Algorithm 2), results and errors.
+//
+// The loop itself runs on the device: every stop is the kernel sequence
+//   count (Algorithm 3) -> promote/prune (Algorithm 4) -> box-set insert ->
+//   generate (MAKECANDIDATES) -> finish (Algorithm 5, trace, loop test)
+// and all loop state lives in a device-resident Ctrl record, so the host
+// enqueues several stops at a time and only reads Ctrl back between groups
+// (to stop when DASHED is empty, or to grow a buffer a kernel found short).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dic.h"
+#include "dic_internal.cuh"
+
+using namespace dic;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+static dic_status fail(dic_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define CU(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? DIC_ENOMEM : DIC_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+    }                                                                                   \
+  } while (0)
+
+#define TRY(expr)                      \
+  do {                                 \
+    dic_status s_ = (expr);            \
+    if (s_ != DIC_OK) return s_;       \
+  } while (0)
+
+// ---------------------------------------------------------------- objects
+struct dic_db {
+  uint64_t *words = nullptr;  // device, n*W
+  uint64_t n = 0;
+  uint32_t m = 0, W = 0;
+  int device = 0;
+  std::atomic<int> busy{0};
+};
+
+struct dic_result {
+  uint32_t W = 0;
+  std::vector<uint64_t> masks;  // count*W
+  std::vector<uint32_t> k, supp;
+  std::vector<uint64_t> trace;  // rows*TRACE_COLS
+  dic_stats stats{};
+};
+
+static void init_pool(int dev) {
+  static std::atomic<uint64_t> done_mask{0};
+  if (dev < 64 && (done_mask.load() >> dev) & 1) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (dev < 64) done_mask.fetch_or(1ull << dev);
+}
+
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// ----------------------------------------------------------------- loading
+static dic_status new_db(uint64_t n, uint32_t m, dic_db **out) {
+  if (m == 0) return fail(DIC_EINVAL, "m must be > 0");
+  if (n >= (1ull << 31)) return fail(DIC_EINVAL, "n must be < 2^31 (got %llu)", (unsigned long long)n);
+  dic_db *db = new (std::nothrow) dic_db();
+  if (!db) return fail(DIC_ENOMEM, "host allocation");
+  db->n = n;
+  db->m = m;
+  db->W = (m + 63) / 64;
+  cudaGetDevice(&db->device);
+  init_pool(db->device);
+  if (n) {
+    cudaError_t e = cudaMalloc(&db->words, (size_t)n * db->W * 8);
+    if (e != cudaSuccess) {
+      delete db;
+      return fail(DIC_ENOMEM, "device allocation of %llu bytes: %s",
+                  (unsigned long long)(n * db->W * 8), cudaGetErrorString(e));
+    }
+  }
+  *out = db;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_load_db(const uint64_t *words, uint64_t n, uint32_t m, dic_db **out) {
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n && !words) return fail(DIC_EINVAL, "words is NULL");
+  if (m == 0) return fail(DIC_EINVAL, "m must be > 0");
+  const uint32_t W = (m + 63) / 64;
+  if (m % 64) {
+    const uint64_t pad = ~((1ull << (m % 64)) - 1);
+    for (uint64_t t = 0; t < n; ++t)
+      if (words[t * W + W - 1] & pad)
+        return fail(DIC_EINVAL, "row %llu has a bit set at an item >= m", (unsigned long long)t);
+  }
+  dic_db *db = nullptr;
+  TRY(new_db(n, m, &db));
+  if (n) {
+    cudaError_t e = cudaMemcpy(db->words, words, (size_t)n * W * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(db->words);
+      delete db;
+      return fail(DIC_ECUDA, "copy to device: %s", cudaGetErrorString(e));
+    }
+  }
+  *out = db;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_load_db_csr(const uint64_t *row_ptr, const uint32_t *items, uint64_t n,
+                                      uint32_t m, dic_db **out) {
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!row_ptr) return fail(DIC_EINVAL, "row_ptr is NULL");
+  if (row_ptr[0] != 0) return fail(DIC_EINVAL, "row_ptr[0] must be 0");
+  for (uint64_t t = 0; t < n; ++t)
+    if (row_ptr[t + 1] < row_ptr[t])
+      return fail(DIC_EINVAL, "row_ptr decreases at row %llu", (unsigned long long)t);
+  const uint64_t nnz = row_ptr[n];
+  if (nnz && !items) return fail(DIC_EINVAL, "items is NULL");
+  dic_db *db = nullptr;
+  TRY(new_db(n, m, &db));
+  if (n == 0) { *out = db; return DIC_OK; }
+  cudaStream_t s;
+  uint64_t *d_rp = nullptr;
+  uint32_t *d_it = nullptr, *d_bad = nullptr;
+  uint32_t bad = 0;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_rp, (n + 1) * 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_it, (nnz ? nnz : 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_bad, 4, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_it, items, nnz * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(db->words, 0, (size_t)n * db->W * 8, s);
+  if (e == cudaSuccess) e = launch_pack_csr(d_rp, d_it, n, m, db->W, db->words, d_bad, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(d_rp, s);
+  cudaFreeAsync(d_it, s);
+  cudaFreeAsync(d_bad, s);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess || bad) {
+    cudaFree(db->words);
+    delete db;
+    if (e != cudaSuccess) return fail(DIC_ECUDA, "csr load: %s", cudaGetErrorString(e));
+    return fail(DIC_EINVAL, "an item id is >= m");
+  }
+  *out = db;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_load_db_device(const uint64_t *dev_words, uint64_t n, uint32_t m,
+                                         void *stream, dic_db **out) {
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n && !dev_words) return fail(DIC_EINVAL, "dev_words is NULL");
+  dic_db *db = nullptr;
+  TRY(new_db(n, m, &db));
+  if (n == 0) { *out = db; return DIC_OK; }
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t *d_bad = nullptr, bad = 0;
+  cudaError_t e = cudaMemcpyAsync(db->words, dev_words, (size_t)n * db->W * 8,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_bad, 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 4, s);
+  if (e == cudaSuccess) e = launch_check_padding(db->words, n, m, db->W, d_bad, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d_bad) cudaFreeAsync(d_bad, s);
+  if (e != cudaSuccess || bad) {
+    cudaStreamSynchronize(s);
+    cudaFree(db->words);
+    delete db;
+    if (e != cudaSuccess) return fail(DIC_ECUDA, "device load: %s", cudaGetErrorString(e));
+    return fail(DIC_EINVAL, "a row has a bit set at an item >= m");
+  }
+  *out = db;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_db_free(dic_db *db) {
+  if (!db) return DIC_OK;
+  if (db->busy.load()) return fail(DIC_EBUSY, "database has queries in flight");
+  if (db->words) cudaFree(db->words);
+  delete db;
+  return DIC_OK;
+}
+
+extern "C" uint64_t dic_db_rows(const dic_db *db) { return db ? db->n : 0; }
+extern "C" uint32_t dic_db_items(const dic_db *db) { return db ? db->m : 0; }
+extern "C" const uint64_t *dic_db_device_words(const dic_db *db) { return db ? db->words : nullptr; }
+
+// ------------------------------------------------------------------ mining
+extern "C" void dic_options_init(dic_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->struct_size = sizeof *o;
+  o->count_path = DIC_COUNT_AUTO;
+  o->steps_per_sync = 0;
+  o->use_graph = 1;
+  o->profile = 0;
+  o->max_candidates = 0;
+}
+
+namespace {
+
+// A device allocation released on the mining stream.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+class Miner {
+ public:
+  Miner(const dic_db *db, uint32_t minsup, uint64_t M, const dic_options &opt, cudaStream_t s)
+      : db_(db), minsup_(minsup), M_(M), opt_(opt), s_(s) {}
+  ~Miner() { release(); }
+
+  dic_status run(dic_result **out);
+
+ private:
+  template <class T>
+  dic_status alloc(T **p, size_t count, bool zero = false) {
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMallocAsync((void **)p, bytes, s_);
+    if (e != cudaSuccess) return fail(DIC_ENOMEM, "device allocation of %zu bytes: %s", bytes,
+                                      cudaGetErrorString(e));
+    bufs_.push_back(*p);
+    if (zero) CU(cudaMemsetAsync(*p, 0, bytes, s_));
+    return DIC_OK;
+  }
+  template <class T>
+  void drop(T *p) {
+    if (!p) return;
+    auto it = std::find(bufs_.begin(), bufs_.end(), (void *)p);
+    if (it != bufs_.end()) bufs_.erase(it);
+    cudaFreeAsync(p, s_);
+  }
+  void release() {
+    for (void *p : bufs_) cudaFreeAsync(p, s_);
+    bufs_.clear();
+    for (auto &ev : events_) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    events_.clear();
+    if (h_ctrl_) { cudaFreeHost(h_ctrl_); h_ctrl_ = nullptr; }
+  }
+
+  dic_status grow_candidates(uint32_t need);
+  dic_status grow_hash();
+  dic_status grow_trace(uint32_t need);
+  dic_status launch_phase(int phase);
+  dic_status launch_stop_from(int phase);
+  dic_status sync_ctrl();
+  int count_path_for_stop() const;
+
+  const dic_db *db_;
+  uint32_t minsup_;
+  uint64_t M_;
+  dic_options opt_;
+  cudaStream_t s_;
+  std::vector<void *> bufs_;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events_;
+  Lattice L_{};
+  Ctrl *h_ctrl_ = nullptr;
+  uint32_t nw_ = 2;  // rows-kernel width bucket
+  int grid_ = 0;
+  uint32_t launches_ = 0;
+  uint32_t path_launches_[4] = {0, 0, 0, 0};
+  uint64_t candidates_cap_limit_ = 0xFFFFFFF0ull;
+};
+
+int Miner::count_path_for_stop() const {
+  return DIC_COUNT_ROWS;
+}
+
+dic_status Miner::sync_ctrl() {
+  CU(cudaMemcpyAsync(h_ctrl_, L_.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s_));
+  CU(cudaStreamSynchronize(s_));
+  return DIC_OK;
+}
+
+dic_status Miner::launch_phase(int phase) {
+  cudaError_t e = cudaSuccess;
+  switch (phase) {
+    case PH_COUNT: {
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (opt_.profile) {
+        CU(cudaEventCreate(&a));
+        CU(cudaEventCreate(&b));
+        CU(cudaEventRecord(a, s_));
+      }
+      e = launch_count_rows(L_, (int)nw_, grid_, s_);
+      path_launches_[DIC_COUNT_ROWS]++;
+      if (opt_.profile) {
+        CU(cudaEventRecord(b, s_));
+        events_.push_back({a, b});
+      }
+      break;
+    }
+    case PH_PROMOTE: e = launch_promote(L_, grid_, s_); break;
+    case PH_HASH: e = launch_hash_insert(L_, grid_, s_); break;
+    case PH_GEN: e = launch_generate(L_, grid_, s_); break;
+    case PH_FINISH: e = launch_finish(L_, s_); break;
+  }
+  ++launches_;
+  if (e != cudaSuccess) return fail(DIC_ECUDA, "kernel launch (phase %d): %s", phase,
+                                    cudaGetErrorString(e));
+  return DIC_OK;
+}
+
+dic_status Miner::launch_stop_from(int phase) {
+  for (int p = phase; p <= PH_FINISH; ++p) TRY(launch_phase(p));
+  return DIC_OK;
+}
+
+dic_status Miner::grow_candidates(uint32_t need) {
+  uint64_t ncap = std::max<uint64_t>((uint64_t)L_.cap * 2, (uint64_t)need + need / 4 + 1024);
+  if (opt_.max_candidates && ncap > opt_.max_candidates) ncap = opt_.max_candidates;
+  if (ncap > candidates_cap_limit_) ncap = candidates_cap_limit_;
+  if (ncap < need)
+    return fail(DIC_ECAPACITY, "candidate store needs %u records, limit is %llu", need,
+                (unsigned long long)ncap);
+  const uint32_t keep = h_ctrl_->tail;
+  const uint32_t nb = h_ctrl_->n_newbox;
+  Lattice N = L_;
+  N.cap = (uint32_t)ncap;
+  TRY(alloc(&N.cmask, (size_t)ncap * L_.wc));
+  TRY(alloc(&N.csupp, ncap));
+  TRY(alloc(&N.cbirth, ncap));
+  TRY(alloc(&N.cshape, ncap));
+  TRY(alloc(&N.newbox, ncap));
+  TRY(alloc(&N.newhash, ncap));
+  CU(cudaMemcpyAsync(N.cmask, L_.cmask, (size_t)keep * L_.wc * 8, cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.csupp, L_.csupp, (size_t)keep * 4, cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.cbirth, L_.cbirth, (size_t)keep * 4, cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.cshape, L_.cshape, (size_t)keep, cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.newbox, L_.newbox, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.newhash, L_.newhash, (size_t)nb * 8, cudaMemcpyDeviceToDevice, s_));
+  drop(L_.cmask); drop(L_.csupp); drop(L_.cbirth); drop(L_.cshape); drop(L_.newbox);
+  drop(L_.newhash);
+  L_ = N;
+  return DIC_OK;
+}
+
+dic_status Miner::grow_hash() {
+  uint64_t ncap = (uint64_t)L_.hcap * 2;
+  while ((uint64_t)(h_ctrl_->hash_used + h_ctrl_->n_newbox) * 2 > ncap) ncap *= 2;
+  if (ncap > (1ull << 31)) return fail(DIC_ECAPACITY, "box set would exceed 2^31 slots");
+  Lattice N = L_;
+  N.hcap = (uint32_t)ncap;
+  TRY(alloc(&N.hkeys, (size_t)ncap * L_.wc));
+  TRY(alloc(&N.hvals, ncap, true));
+  CU(launch_rehash(N, L_.hkeys, L_.hvals, L_.hcap, s_));
+  ++launches_;
+  drop(L_.hkeys);
+  drop(L_.hvals);
+  L_ = N;
+  return DIC_OK;
+}
+
+dic_status Miner::grow_trace(uint32_t need) {
+  if (need <= L_.tcap) return DIC_OK;
+  uint32_t ncap = std::max<uint32_t>(need, L_.tcap * 2);
+  Lattice N = L_;
+  N.tcap = ncap;
+  TRY(alloc(&N.trace, (size_t)ncap * TRACE_COLS));
+  TRY(alloc(&N.cohort_start, (size_t)ncap + 2));
+  TRY(alloc(&N.cohort_birth, (size_t)ncap + 2));
+  CU(cudaMemcpyAsync(N.trace, L_.trace, (size_t)L_.tcap * TRACE_COLS * 8,
+                     cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.cohort_start, L_.cohort_start, ((size_t)L_.tcap + 2) * 4,
+                     cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.cohort_birth, L_.cohort_birth, ((size_t)L_.tcap + 2) * 4,
+                     cudaMemcpyDeviceToDevice, s_));
+  drop(L_.trace); drop(L_.cohort_start); drop(L_.cohort_birth);
+  L_ = N;
+  return DIC_OK;
+}
+
+static bool canon_less(const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) {
+  if (a.size() != b.size()) return a.size() < b.size();
+  return a < b;
+}
+
+dic_status Miner::run(dic_result **out) {
+  auto t0 = std::chrono::steady_clock::now();
+  const uint64_t n = db_->n;
+  const uint32_t m = db_->m, W = db_->W;
+  std::unique_ptr<dic_result> res(new dic_result());
+  res->W = W;
+  res->stats.words = W;
+  grid_ = sm_count() * 4;
+  if (n == 0) {
+    *out = res.release();
+    return DIC_OK;
+  }
+  if (M_ > n) M_ = n;
+  const uint64_t stop_max64 = (n + M_ - 1) / M_;
+  CU(cudaMallocHost((void **)&h_ctrl_, sizeof(Ctrl)));
+
+  // ---- FIRSTPASS: supports of all 1-itemsets over all n rows
+  uint32_t *d_cnt1 = nullptr;
+  TRY(alloc(&d_cnt1, m));
+  cudaEvent_t fa = nullptr, fb = nullptr;
+  if (opt_.profile) {
+    CU(cudaEventCreate(&fa));
+    CU(cudaEventCreate(&fb));
+    CU(cudaEventRecord(fa, s_));
+  }
+  CU(launch_item_count(db_->words, n, W, m, d_cnt1, s_));
+  ++launches_;
+  if (opt_.profile) CU(cudaEventRecord(fb, s_));
+  std::vector<uint32_t> cnt1(m);
+  CU(cudaMemcpyAsync(cnt1.data(), d_cnt1, (size_t)m * 4, cudaMemcpyDeviceToHost, s_));
+  CU(cudaStreamSynchronize(s_));
+  if (opt_.profile) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, fa, fb);
+    res->stats.firstpass_ms = ms;
+    cudaEventDestroy(fa);
+    cudaEventDestroy(fb);
+  }
+  std::vector<uint32_t> l1items;
+  for (uint32_t i = 0; i < m; ++i)
+    if (cnt1[i] >= minsup_) l1items.push_back(i);
+  const uint32_t l1 = (uint32_t)l1items.size();
+  res->stats.l1 = l1;
+  const uint32_t wc = std::max<uint32_t>(1, (l1 + 63) / 64);
+  res->stats.words_compact = wc;
+  uint64_t tests = (uint64_t)m * n;
+
+  std::vector<std::vector<uint32_t>> sets;
+  std::vector<uint32_t> supps;
+  for (uint32_t i : l1items) { sets.push_back({i}); supps.push_back(cnt1[i]); }
+
+  const uint64_t npairs = (uint64_t)l1 * (l1 - (l1 ? 1 : 0)) / 2;
+  if (npairs > 0) {
+    if (npairs > candidates_cap_limit_ ||
+        (opt_.max_candidates && npairs > opt_.max_candidates))
+      return fail(DIC_ECAPACITY, "%llu candidate pairs exceed the candidate limit",
+                  (unsigned long long)npairs);
+    if (stop_max64 > 0x7FFFFFFFull) return fail(DIC_EINVAL, "too many blocks");
+    // ---- column compaction to the l1 frequent items (ranks)
+    std::vector<int32_t> rank_of((size_t)W * 64, -1);
+    for (uint32_t r = 0; r < l1; ++r) rank_of[l1items[r]] = (int32_t)r;
+    int32_t *d_rank = nullptr;
+    TRY(alloc(&d_rank, rank_of.size()));
+    CU(cudaMemcpyAsync(d_rank, rank_of.data(), rank_of.size() * 4, cudaMemcpyHostToDevice, s_));
+    uint64_t *d_rows = nullptr;
+    TRY(alloc(&d_rows, (size_t)n * wc));
+    CU(launch_compact_rows(db_->words, n, W, d_rank, d_rows, wc, s_));
+    ++launches_;
+
+    // ---- lattice buffers
+    L_.rows = d_rows;
+    L_.n = n;
+    L_.M = M_;
+    L_.stop_max = (uint32_t)stop_max64;
+    L_.minsup = minsup_;
+    L_.wc = wc;
+    L_.l1 = l1;
+    uint64_t cap = npairs + npairs / 8 + 4096;
+    if (opt_.max_candidates && cap > opt_.max_candidates) cap = opt_.max_candidates;
+    if (cap > candidates_cap_limit_) cap = candidates_cap_limit_;
+    L_.cap = (uint32_t)cap;
+    TRY(alloc(&L_.cmask, (size_t)cap * wc));
+    TRY(alloc(&L_.csupp, cap));
+    TRY(alloc(&L_.cbirth, cap));
+    TRY(alloc(&L_.cshape, cap));
+    TRY(alloc(&L_.newbox, cap));
+    TRY(alloc(&L_.newhash, cap));
+    L_.hcap = 1u << 14;
+    TRY(alloc(&L_.hkeys, (size_t)L_.hcap * wc));
+    TRY(alloc(&L_.hvals, L_.hcap, true));
+    L_.tcap = std::max<uint32_t>(64, (uint32_t)std::min<uint64_t>(stop_max64 * 3 + 16, 1u << 20));
+    TRY(alloc(&L_.trace, (size_t)L_.tcap * TRACE_COLS));
+    TRY(alloc(&L_.cohort_start, (size_t)L_.tcap + 2));
+    TRY(alloc(&L_.cohort_birth, (size_t)L_.tcap + 2, true));
+    CU(cudaMemsetAsync(L_.cohort_start, 0, ((size_t)L_.tcap + 2) * 4, s_));
+    TRY(alloc(&L_.ctrl, 1));
+    Ctrl c{};
+    c.step = 1;
+    c.head = 0;
+    c.tail = (uint32_t)npairs;
+    c.n_live = (uint32_t)npairs;
+    c.n_cohorts = 1;
+    c.max_k = 2;
+    c.tests = tests;
+    *h_ctrl_ = c;
+    CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
+    CU(launch_pair_join(L_, npairs, s_));
+    ++launches_;
+    nw_ = (uint32_t)rows_width_bucket(2, wc);
+
+    // ---- the stop loop of Algorithm 2
+    uint32_t chunk = opt_.steps_per_sync ? opt_.steps_per_sync : 4;
+    const uint32_t chunk_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
+    for (;;) {
+      TRY(grow_trace(h_ctrl_->n_trace + chunk + 2));
+      int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
+      nw_ = bucket ? (uint32_t)bucket : 0;
+      for (uint32_t i = 0; i < chunk; ++i) TRY(launch_stop_from(PH_COUNT));
+      TRY(sync_ctrl());
+      if (h_ctrl_->error)
+        return fail((dic_status)h_ctrl_->error, "device reported status %u", h_ctrl_->error);
+      while (h_ctrl_->stall) {
+        const uint32_t st = h_ctrl_->stall;
+        int phase = PH_COUNT;
+        if (st == ST_WIDTH) {
+          int b = rows_width_bucket(h_ctrl_->max_k, wc);
+          nw_ = b ? (uint32_t)b : 0;
+          phase = PH_COUNT;
+        } else if (st == ST_HASH) {
+          TRY(grow_hash());
+          phase = PH_HASH;
+        } else if (st == ST_CAND) {
+          TRY(grow_candidates(h_ctrl_->tail + h_ctrl_->n_gen));
+          h_ctrl_->n_gen = 0;
+          phase = PH_GEN;
+        } else {
+          return fail(DIC_ECUDA, "unknown stall code %u", st);
+        }
+        h_ctrl_->stall = ST_NONE;
+        CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
+        TRY(launch_stop_from(phase));
+        TRY(sync_ctrl());
+        if (h_ctrl_->error)
+          return fail((dic_status)h_ctrl_->error, "device reported status %u", h_ctrl_->error);
+      }
+      if (h_ctrl_->done) break;
+      chunk = std::min(chunk * 2, chunk_max);
+    }
+    tests = h_ctrl_->tests;
+    const uint32_t tail = h_ctrl_->tail;
+    res->stats.candidates = tail;
+
+    // ---- SOLID boxes (k >= 2) to the host
+    uint32_t *d_idx = nullptr, *d_cnt = nullptr;
+    TRY(alloc(&d_idx, tail));
+    TRY(alloc(&d_cnt, 1, true));
+    CU(launch_collect_boxes(L_, tail, d_idx, d_cnt, s_));
+    ++launches_;
+    uint32_t nbox = 0;
+    CU(cudaMemcpyAsync(&nbox, d_cnt, 4, cudaMemcpyDeviceToHost, s_));
+    CU(cudaStreamSynchronize(s_));
+    uint64_t *d_om = nullptr;
+    uint32_t *d_os = nullptr;
+    TRY(alloc(&d_om, (size_t)nbox * wc));
+    TRY(alloc(&d_os, nbox));
+    CU(launch_gather_boxes(L_, d_idx, nbox, d_om, d_os, s_));
+    ++launches_;
+    std::vector<uint64_t> hm((size_t)nbox * wc);
+    std::vector<uint32_t> hs(nbox);
+    if (nbox) {
+      CU(cudaMemcpyAsync(hm.data(), d_om, hm.size() * 8, cudaMemcpyDeviceToHost, s_));
+      CU(cudaMemcpyAsync(hs.data(), d_os, hs.size() * 4, cudaMemcpyDeviceToHost, s_));
+    }
+    const uint32_t ntr = h_ctrl_->n_trace;
+    std::vector<unsigned long long> tr((size_t)ntr * TRACE_COLS);
+    if (ntr)
+      CU(cudaMemcpyAsync(tr.data(), L_.trace, tr.size() * 8, cudaMemcpyDeviceToHost, s_));
+    CU(cudaStreamSynchronize(s_));
+    res->trace.assign(tr.begin(), tr.end());
+    res->stats.stops = ntr;
+    for (uint32_t q = 0; q < nbox; ++q) {
+      std::vector<uint32_t> v;
+      for (uint32_t w = 0; w < wc; ++w) {
+        uint64_t x = hm[(size_t)q * wc + w];
+        while (x) {
+          int b = __builtin_ctzll(x);
+          x &= x - 1;
+          v.push_back(l1items[w * 64 + b]);
+        }
+      }
+      sets.push_back(std::move(v));
+      supps.push_back(hs[q]);
+    }
+  } else {
+    res->stats.candidates = 0;
+  }
+
+  // ---- canonical order, original item space
+  std::vector<uint32_t> order(sets.size());
+  for (uint32_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::sort(order.begin(), order.end(),
+            [&](uint32_t a, uint32_t b) { return canon_less(sets[a], sets[b]); });
+  res->masks.assign(order.size() * W, 0);
+  res->k.resize(order.size());
+  res->supp.resize(order.size());
+  for (size_t q = 0; q < order.size(); ++q) {
+    const auto &v = sets[order[q]];
+    for (uint32_t it : v) res->masks[q * W + (it >> 6)] |= 1ull << (it & 63);
+    res->k[q] = (uint32_t)v.size();
+    res->supp[q] = supps[order[q]];
+  }
+  res->stats.tests = tests;
+  res->stats.frequent = order.size();
+  res->stats.kernel_launches = launches_;
+  for (int i = 0; i < 4; ++i) res->stats.path_launches[i] = path_launches_[i];
+  if (opt_.profile) {
+    double tot = 0;
+    for (auto &ev : events_) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev.first, ev.second);
+      tot += ms;
+    }
+    res->stats.count_ms = tot;
+    res->stats.count_launches = events_.size();
+  }
+  release();
+  cudaError_t e = cudaStreamSynchronize(s_);
+  if (e != cudaSuccess) return fail(DIC_ECUDA, "finalise: %s", cudaGetErrorString(e));
+  res->stats.mine_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = res.release();
+  return DIC_OK;
+}
+
+}  // namespace
+
+extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint64_t M,
+                                  const dic_options *opt, void *stream, dic_result **out) {
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!db) return fail(DIC_EINVAL, "db is NULL");
+  if (minsup_count == 0) return fail(DIC_EINVAL, "minsup_count must be >= 1");
+  if (M == 0) return fail(DIC_EINVAL, "M must be >= 1");
+  dic_options o;
+  dic_options_init(&o);
+  if (opt) std::memcpy(&o, opt, std::min<size_t>(sizeof o, opt->struct_size ? opt->struct_size : sizeof o));
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != db->device) cudaSetDevice(db->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool own = false;
+  if (!s) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      if (prev != db->device) cudaSetDevice(prev);
+      return fail(DIC_ECUDA, "stream creation failed");
+    }
+    own = true;
+  }
+  const_cast<dic_db *>(db)->busy.fetch_add(1);
+  dic_status st;
+  {
+    Miner mn(db, minsup_count, M, o, s);
+    st = mn.run(out);
+  }
+  if (st != DIC_OK) cudaStreamSynchronize(s);
+  const_cast<dic_db *>(db)->busy.fetch_sub(1);
+  if (own) cudaStreamDestroy(s);
+  if (prev != db->device) cudaSetDevice(prev);
+  return st;
+}
+
+extern "C" dic_status dic_mine(const dic_db *db, uint32_t minsup_count, uint64_t M,
+                               dic_result **out) {
+  return dic_mine_ex(db, minsup_count, M, nullptr, nullptr, out);
+}
+
+extern "C" dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *minsup,
+                                     const uint64_t *M, uint32_t count, const dic_options *opt,
+                                     dic_result **out) {
+  if (!out || (count && (!dbs || !minsup || !M))) return fail(DIC_EINVAL, "NULL argument");
+  for (uint32_t i = 0; i < count; ++i) out[i] = nullptr;
+  for (uint32_t i = 0; i < count; ++i) {
+    dic_status st = dic_mine_ex(dbs[i], minsup[i], M[i], opt, nullptr, &out[i]);
+    if (st != DIC_OK) {
+      for (uint32_t j = 0; j <= i; ++j) { dic_result_free(out[j]); out[j] = nullptr; }
+      return st;
+    }
+  }
+  return DIC_OK;
+}
+
+// ----------------------------------------------------------------- results
+extern "C" uint64_t dic_result_count(const dic_result *r) { return r ? r->k.size() : 0; }
+extern "C" uint32_t dic_result_words(const dic_result *r) { return r ? r->W : 0; }
+extern "C" dic_status dic_result_copy(const dic_result *r, uint64_t *masks, uint32_t *k,
+                                      uint32_t *support) {
+  if (!r) return fail(DIC_EINVAL, "result is NULL");
+  if (masks && !r->masks.empty()) std::memcpy(masks, r->masks.data(), r->masks.size() * 8);
+  if (k && !r->k.empty()) std::memcpy(k, r->k.data(), r->k.size() * 4);
+  if (support && !r->supp.empty()) std::memcpy(support, r->supp.data(), r->supp.size() * 4);
+  return DIC_OK;
+}
+extern "C" uint64_t dic_result_trace_len(const dic_result *r) {
+  return r ? r->trace.size() / TRACE_COLS : 0;
+}
+extern "C" dic_status dic_result_trace(const dic_result *r, uint64_t *rows) {
+  if (!r || !rows) return fail(DIC_EINVAL, "NULL argument");
+  if (!r->trace.empty()) std::memcpy(rows, r->trace.data(), r->trace.size() * 8);
+  return DIC_OK;
+}
+extern "C" dic_status dic_result_stats(const dic_result *r, dic_stats *out) {
+  if (!r || !out) return fail(DIC_EINVAL, "NULL argument");
+  *out = r->stats;
+  return DIC_OK;
+}
+extern "C" void dic_result_free(dic_result *r) { delete r; }
+
+// -------------------------------------------------------------------- misc
+extern "C" uint32_t dic_minsup_count(uint64_t n, double frac) {
+  if (!(frac > 0)) return 1;
+  double v = std::ceil(frac * (double)n - 1e-9);
+  if (v < 1) v = 1;
+  if (v > 4294967295.0) v = 4294967295.0;
+  return (uint32_t)v;
+}
+
+extern "C" const char *dic_status_str(dic_status s) {
+  switch (s) {
+    case DIC_OK: return "ok";
+    case DIC_EINVAL: return "invalid argument";
+    case DIC_ENOMEM: return "out of memory";
+    case DIC_ECUDA: return "CUDA error";
+    case DIC_ECAPACITY: return "capacity exceeded";
+    case DIC_ETIMEOUT: return "device wait timed out";
+    case DIC_EBUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+extern "C" const char *dic_last_error(void) { return g_last_error.c_str(); }
+extern "C" uint32_t dic_abi_version(void) { return DIC_ABI_VERSION; }

@@ -1,0 +1,111 @@
+// Internal declarations of the DIC library (device lattice layout, kernel
+// launchers). Not part of the public ABI (include/dic.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dic {
+
+// Shape of an itemset record (Section 4.1): NIL = erased, CIRCLE = suspected
+// infrequent, BOX = frequent. Dashed vs solid is positional: a record is
+// dashed while it lies in the candidate window [head, tail).
+enum Shape : uint8_t { SH_NIL = 0, SH_CIRCLE = 1, SH_BOX = 2 };
+
+// Capacity shortfalls detected on the device. A kernel that detects one
+// changes nothing, sets `stall`, and every later kernel returns at once; the
+// host grows the buffer and re-runs the step from the phase named here.
+enum Stall : uint32_t { ST_NONE = 0, ST_WIDTH = 1, ST_HASH = 2, ST_CAND = 3 };
+enum Phase : int { PH_COUNT = 0, PH_PROMOTE = 1, PH_HASH = 2, PH_GEN = 3, PH_FINISH = 4 };
+
+constexpr int TRACE_COLS = 9;
+
+// Device-resident loop state of Algorithm 2 (one per query).
+struct Ctrl {
+  uint32_t step;       // global stop counter g of the next stop to run (1-based)
+  uint32_t done;       // 1 once DASHED is empty
+  uint32_t stall;      // Stall
+  uint32_t error;      // dic_status of a device-side failure (0 = none)
+  uint32_t head;       // candidate window [head, tail) = DASHED (plus erased holes)
+  uint32_t tail;
+  uint32_t n_live;     // |DASHED|
+  uint32_t n_newbox;   // promotions at this stop
+  uint32_t n_pruned;   // circles erased by the bound at this stop
+  uint32_t n_solid;    // records reaching a full pass at this stop
+  uint32_t n_gen;      // generation attempts at this stop (incl. overflow)
+  uint32_t gen_tail0;  // tail before this stop's generation
+  uint32_t cohort_head;
+  uint32_t n_cohorts;
+  uint32_t hash_used;  // occupied hash slots
+  uint32_t max_k;      // largest itemset size ever placed in DASHED
+  uint32_t n_trace;
+  uint32_t pad0;
+  unsigned long long tests;  // candidate-transaction tests so far
+};
+
+// Everything a stop's kernels touch, passed by value.
+struct Lattice {
+  Ctrl *ctrl;
+  // candidate records, append-only; [0, head) are solid, [head, tail) dashed
+  uint64_t *cmask;     // [cap][wc] compact-rank bitmaps
+  uint32_t *csupp;     // [cap]
+  uint32_t *cbirth;    // [cap] global stop at which the record was created
+  uint8_t *cshape;     // [cap]
+  uint32_t *newbox;    // [cap] records promoted at this stop
+  uint64_t *newhash;   // [cap] hash pre-image sums of those records
+  uint32_t cap;
+  // box set: open addressing, key = mask, value = promotion stop + 1
+  uint64_t *hkeys;     // [hcap][wc]
+  uint32_t *hvals;     // [hcap], 0 = empty
+  uint32_t hcap;       // power of two
+  // cohorts (records created at one stop are contiguous)
+  uint32_t *cohort_start;
+  uint32_t *cohort_birth;
+  unsigned long long *trace;  // [tcap][TRACE_COLS]
+  uint32_t tcap;
+  // the problem
+  const uint64_t *rows;  // compact rows [n][wc]
+  uint64_t n;
+  uint64_t M;
+  uint32_t stop_max;
+  uint32_t minsup;
+  uint32_t wc;         // words per compact row / mask
+  uint32_t l1;         // frequent items (compact ranks 0..l1-1)
+};
+
+// Block [first, last) of global stop g (1-based), with rewind (Algorithm 2).
+__host__ __device__ inline void block_of(uint32_t g, uint32_t stop_max, uint64_t M, uint64_t n,
+                                         uint32_t *stop, uint64_t *first, uint64_t *last) {
+  uint32_t s = (g - 1) % stop_max + 1;
+  *stop = s;
+  *first = (uint64_t)(s - 1) * M;
+  uint64_t l = (uint64_t)s * M;
+  *last = l < n ? l : n;
+}
+
+// ---- kernel launchers (kernels_*.cu) ----
+cudaError_t launch_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_t m,
+                              uint32_t *cnt, cudaStream_t s);
+cudaError_t launch_compact_rows(const uint64_t *B, uint64_t n, uint32_t W, const int32_t *rank_of,
+                                uint64_t *Bc, uint32_t wc, cudaStream_t s);
+cudaError_t launch_pack_csr(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
+                            uint32_t W, uint64_t *words, uint32_t *bad, cudaStream_t s);
+cudaError_t launch_check_padding(const uint64_t *words, uint64_t n, uint32_t m, uint32_t W,
+                                 uint32_t *bad, cudaStream_t s);
+cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s);
+cudaError_t launch_count_rows(Lattice L, int nw, int grid, cudaStream_t s);
+cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s);
+cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s);
+cudaError_t launch_generate(Lattice L, int grid, cudaStream_t s);
+cudaError_t launch_finish(Lattice L, cudaStream_t s);
+cudaError_t launch_rehash(Lattice L, const uint64_t *okeys, const uint32_t *ovals, uint32_t ocap,
+                          cudaStream_t s);
+cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
+                                 uint32_t *out_count, cudaStream_t s);
+cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
+                                uint32_t *supp, cudaStream_t s);
+
+// Width bucket (max nonzero 32-bit halves per candidate) the rows kernel
+// needs for itemsets of up to max_k items in wc-word masks.
+int rows_width_bucket(uint32_t max_k, uint32_t wc);
+
+}  // namespace dic

@@ -1,0 +1,487 @@
+// Device lattice of ParallelDIC (Algorithm 2) on sm_103a: the first pass,
+// the bitmap packer, column compaction, the pair join, PRUNE (Algorithm 4),
+// the box set, MAKECANDIDATES and CHECKFULLPASS (Algorithm 5).
+//
+// Layout: candidate records live in one append-only array. Records created
+// at the same stop form a contiguous cohort; since every record is counted
+// once per stop from its creation on, a cohort completes its full pass (and
+// leaves DASHED for SOLID, Algorithm 5) all at once, so DASHED is the window
+// [head, tail) and solidifying is advancing `head` past whole cohorts. PRUNE
+// erases records in place (shape NIL); the count kernels skip them.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dic_internal.cuh"
+
+namespace dic {
+
+// ------------------------------------------------------------- hashing
+// Hash of a mask = final mix of the sum over words of hterm(word, index).
+// The sum form lets MAKECANDIDATES derive the hash of C \ {j} from that of
+// the parent in O(1).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t hterm(uint64_t w, uint32_t i) {
+  return mix64(w + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1));
+}
+__device__ __forceinline__ uint32_t hslot(uint64_t sum, uint32_t hcap) {
+  return (uint32_t)(mix64(sum ^ 0x5851F42D4C957F2Dull) & (uint64_t)(hcap - 1));
+}
+
+// --------------------------------------------------------- first pass
+// supp1[i] = number of rows with bit i set, over all n rows (FIRSTPASS of
+// Section 4.2). Flat over the n*W words; each thread walks the set bits of
+// its words. Counters are privatised in shared memory when m fits.
+__global__ void __launch_bounds__(512) k_item_count(const uint64_t *__restrict__ B,
+                                                    uint64_t nwords, uint32_t W, uint32_t m,
+                                                    uint32_t *__restrict__ cnt, int use_smem) {
+  extern __shared__ uint32_t sc[];
+  if (use_smem) {
+    for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) sc[j] = 0;
+    __syncthreads();
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t col = (uint32_t)(i % W);
+  const uint32_t step_col = (uint32_t)(stride % W);
+  for (; i < nwords; i += stride) {
+    uint64_t x = __ldcs(B + i);
+    const uint32_t base = col * 64u;
+    while (x) {
+      const uint32_t b = (uint32_t)(__ffsll((long long)x) - 1);
+      x &= x - 1;
+      const uint32_t item = base + b;
+      if (item < m) {
+        if (use_smem) atomicAdd(&sc[item], 1u);
+        else atomicAdd(&cnt[item], 1u);
+      }
+    }
+    col += step_col;
+    if (col >= W) col -= W;
+  }
+  if (use_smem) {
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < m; j += blockDim.x)
+      if (sc[j]) atomicAdd(&cnt[j], sc[j]);
+  }
+}
+
+cudaError_t launch_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_t m,
+                              uint32_t *cnt, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int use_smem = m <= 16384;
+  const size_t smem = use_smem ? (size_t)m * 4 : 0;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_item_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaMemsetAsync(cnt, 0, (size_t)m * 4, s);
+  const uint64_t nwords = n * W;
+  if (nwords == 0) return cudaGetLastError();
+  uint64_t want = (nwords + 511) / 512;
+  int grid = (int)(want < (uint64_t)sms * 3 ? want : (uint64_t)sms * 3);
+  k_item_count<<<grid, 512, smem, s>>>(B, nwords, W, m, cnt, use_smem);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------- column compaction
+// Bc[t] keeps only the frequent items of B[t], renumbered by rank (rank
+// order = item order). Exact: a candidate never contains an infrequent item
+// (Section 4.2: infrequent 1-itemsets and their supersets are pruned).
+// One warp per row; the output row is assembled in shared memory.
+__global__ void __launch_bounds__(256) k_compact_rows(const uint64_t *__restrict__ B, uint64_t n,
+                                                      uint32_t W,
+                                                      const int32_t *__restrict__ rank_of,
+                                                      uint64_t *__restrict__ Bc, uint32_t wc) {
+  extern __shared__ unsigned long long sbuf[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long *out = sbuf + (size_t)warp * wc;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t row = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < n; row += nwarps) {
+    for (uint32_t j = lane; j < wc; j += 32) out[j] = 0ull;
+    __syncwarp();
+    for (uint32_t j = lane; j < W; j += 32) {
+      uint64_t x = __ldcs(B + row * W + j);
+      while (x) {
+        const uint32_t b = (uint32_t)(__ffsll((long long)x) - 1);
+        x &= x - 1;
+        const int32_t r = __ldg(rank_of + j * 64 + b);
+        if (r >= 0) atomicOr(&out[r >> 6], 1ull << (r & 63));
+      }
+    }
+    __syncwarp();
+    for (uint32_t j = lane; j < wc; j += 32) Bc[row * wc + j] = out[j];
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_compact_rows(const uint64_t *B, uint64_t n, uint32_t W, const int32_t *rank_of,
+                                uint64_t *Bc, uint32_t wc, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = (size_t)8 * wc * 8;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_compact_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  uint64_t want = (n + 7) / 8;
+  int grid = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
+  k_compact_rows<<<grid, 256, smem, s>>>(B, n, W, rank_of, Bc, wc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ packing
+// BitMask of Section 4.1 from CSR item lists: bit p%64 of word p/64.
+__global__ void k_pack_csr(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ items,
+                           uint64_t n, uint32_t m, uint32_t W, unsigned long long *words,
+                           uint32_t *bad) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const uint64_t b = row_ptr[t], e = row_ptr[t + 1];
+    for (uint64_t j = b; j < e; ++j) {
+      const uint32_t it = items[j];
+      if (it >= m) { atomicOr(bad, 1u); continue; }
+      atomicOr(&words[t * W + (it >> 6)], 1ull << (it & 63));
+    }
+  }
+}
+
+cudaError_t launch_pack_csr(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
+                            uint32_t W, uint64_t *words, uint32_t *bad, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  uint64_t want = (n + 255) / 256;
+  int grid = (int)(want < 65535ull * 4 ? want : 65535ull * 4);
+  k_pack_csr<<<grid, 256, 0, s>>>(row_ptr, items, n, m, W, (unsigned long long *)words, bad);
+  return cudaGetLastError();
+}
+
+// Every bit at an item position >= m must be zero.
+__global__ void k_check_padding(const uint64_t *__restrict__ words, uint64_t n, uint32_t m,
+                                uint32_t W, uint32_t *bad) {
+  const uint32_t used = m - (W - 1) * 64;  // items in the last word, 1..64
+  const uint64_t pad = used == 64 ? 0ull : ~((1ull << used) - 1);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
+    if (words[t * W + W - 1] & pad) atomicOr(bad, 1u);
+}
+
+cudaError_t launch_check_padding(const uint64_t *words, uint64_t n, uint32_t m, uint32_t W,
+                                 uint32_t *bad, cudaStream_t s) {
+  if (n == 0 || m % 64 == 0) return cudaSuccess;
+  uint64_t want = (n + 255) / 256;
+  int grid = (int)(want < 65535ull * 4 ? want : 65535ull * 4);
+  k_check_padding<<<grid, 256, 0, s>>>(words, n, m, W, bad);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ pair join
+// DASHED <- every pair {a,b}, a<b, of frequent items as circles (the
+// bitwise-OR join of the first pass, Section 4.2), in lexicographic order.
+__device__ __forceinline__ uint64_t pair_off(uint64_t a, uint64_t l1) {
+  return a * (2 * l1 - a - 1) / 2;  // pairs whose first rank is < a
+}
+
+__global__ void k_pair_join(Lattice L, uint64_t npairs) {
+  const uint64_t total = npairs * L.wc;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t l1 = L.l1;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const uint64_t p = i / L.wc;
+    const uint32_t w = (uint32_t)(i % L.wc);
+    const double q = (double)(2 * l1 - 1);
+    double disc = q * q - 8.0 * (double)p;
+    if (disc < 0) disc = 0;
+    int64_t a = (int64_t)((q - sqrt(disc)) * 0.5);
+    if (a < 0) a = 0;
+    if (a > (int64_t)l1 - 2) a = (int64_t)l1 - 2;
+    while (a > 0 && pair_off((uint64_t)a, l1) > p) --a;
+    while ((uint64_t)a + 1 < l1 - 1 && pair_off((uint64_t)a + 1, l1) <= p) ++a;
+    const uint64_t b = (uint64_t)a + 1 + (p - pair_off((uint64_t)a, l1));
+    uint64_t word = 0;
+    if ((uint64_t)a >> 6 == w) word |= 1ull << (a & 63);
+    if (b >> 6 == w) word |= 1ull << (b & 63);
+    L.cmask[p * L.wc + w] = word;
+    if (w == 0) {
+      L.csupp[p] = 0;
+      L.cbirth[p] = 0;
+      L.cshape[p] = SH_CIRCLE;
+    }
+  }
+}
+
+cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s) {
+  if (npairs == 0) return cudaSuccess;
+  uint64_t want = (npairs * L.wc + 255) / 256;
+  int grid = (int)(want < 65535ull * 8 ? want : 65535ull * 8);
+  k_pair_join<<<grid, 256, 0, s>>>(L, npairs);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- PRUNE
+// Algorithm 4 over the dashed circles after the count of stop g:
+//   supp >= minsup                      -> BOX (promotion recorded)
+//   supp + M * (stop_max - stop) < minsup -> NIL (erased)
+// with stop = g - birth (the number of blocks this record has been counted
+// over). Records whose stop reaches stop_max are tallied as solidified
+// (Algorithm 5); at that point every live record is a box, since a circle
+// there has the bound supp + 0 < minsup and was erased just above.
+// The superset loop of Algorithm 4 is not run: every (k-1)-subset of a
+// record is a box when it is generated and boxes never change shape, so a
+// dashed circle has no dashed superset and the loop can only match itself.
+__global__ void __launch_bounds__(256) k_promote(Lattice L) {
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  const uint32_t g = C->step, head = C->head, tail = C->tail;
+  uint32_t pruned = 0, solid = 0;
+  for (uint32_t c = head + blockIdx.x * blockDim.x + threadIdx.x; c < tail;
+       c += gridDim.x * blockDim.x) {
+    uint8_t sh = L.cshape[c];
+    if (sh == SH_NIL) continue;
+    const uint32_t age = g - L.cbirth[c];
+    if (sh == SH_CIRCLE) {
+      const uint32_t s = L.csupp[c];
+      if (s >= L.minsup) {
+        L.cshape[c] = SH_BOX;
+        sh = SH_BOX;
+        const uint32_t at = atomicAdd(&C->n_newbox, 1u);
+        L.newbox[at] = c;
+      } else if ((uint64_t)s + L.M * (uint64_t)(L.stop_max - age) < (uint64_t)L.minsup) {
+        L.cshape[c] = SH_NIL;
+        ++pruned;
+        continue;
+      }
+    }
+    if (age == L.stop_max) ++solid;
+  }
+  if (pruned) atomicAdd(&C->n_pruned, pruned);
+  if (solid) atomicAdd(&C->n_solid, solid);
+}
+
+cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s) {
+  k_promote<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- box set
+// Insert the masks promoted at stop g (value g+1). Keys inserted by one
+// launch are distinct and absent (a record is promoted once), so a thread
+// that loses a slot simply probes on. The load check runs before any insert
+// and reads only values this kernel does not change, so every block takes
+// the same decision.
+__global__ void __launch_bounds__(256) k_hash_insert(Lattice L) {
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  const uint32_t P = C->n_newbox;
+  if ((uint64_t)(C->hash_used + P) * 2 > L.hcap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->stall = ST_HASH;
+    return;
+  }
+  const uint32_t g = C->step;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const uint64_t *key = L.cmask + (uint64_t)L.newbox[p] * L.wc;
+    uint64_t sum = 0;
+    for (uint32_t i = 0; i < L.wc; ++i) sum += hterm(key[i], i);
+    L.newhash[p] = sum;
+    uint32_t slot = hslot(sum, L.hcap);
+    for (uint32_t probe = 0; probe < L.hcap; ++probe) {
+      if (atomicCAS(&L.hvals[slot], 0u, g + 1) == 0u) {
+        for (uint32_t i = 0; i < L.wc; ++i) L.hkeys[(uint64_t)slot * L.wc + i] = key[i];
+        break;
+      }
+      slot = (slot + 1) & (L.hcap - 1);
+    }
+  }
+}
+
+cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s) {
+  k_hash_insert<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// Rebuild the box set into a larger table (after an ST_HASH stall).
+__global__ void k_rehash(Lattice L, const uint64_t *okeys, const uint32_t *ovals, uint32_t ocap) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ocap; s += gridDim.x * blockDim.x) {
+    const uint32_t v = ovals[s];
+    if (!v) continue;
+    const uint64_t *key = okeys + (uint64_t)s * L.wc;
+    uint64_t sum = 0;
+    for (uint32_t i = 0; i < L.wc; ++i) sum += hterm(key[i], i);
+    uint32_t slot = hslot(sum, L.hcap);
+    for (uint32_t probe = 0; probe < L.hcap; ++probe) {
+      if (atomicCAS(&L.hvals[slot], 0u, v) == 0u) {
+        for (uint32_t i = 0; i < L.wc; ++i) L.hkeys[(uint64_t)slot * L.wc + i] = key[i];
+        break;
+      }
+      slot = (slot + 1) & (L.hcap - 1);
+    }
+  }
+}
+
+cudaError_t launch_rehash(Lattice L, const uint64_t *okeys, const uint32_t *ovals, uint32_t ocap,
+                          cudaStream_t s) {
+  if (ocap == 0) return cudaSuccess;
+  int grid = (int)((ocap + 255) / 256 < 65535u * 4 ? (ocap + 255) / 256 : 65535u * 4);
+  k_rehash<<<grid, 256, 0, s>>>(L, okeys, ovals, ocap);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ MAKECANDIDATES
+// New candidates at stop g: C = A u {r} for a record A promoted at g and a
+// rank r not in A, kept iff every |C|-1 subset C \ {j} is a box. Each such
+// C has one or more promoted-at-g parents C \ {j}; only the parent with the
+// smallest j emits it, so every C appears exactly once without a dedup
+// table: thread (A, r) emits iff no j < r in A has C \ {j} promoted at g.
+// (A subset promoted at g carries value g+1; older boxes carry less.)
+__device__ __forceinline__ uint32_t box_lookup(const Lattice &L, const uint64_t *A, uint32_t wr,
+                                               uint64_t br, uint32_t wj, uint64_t bj,
+                                               uint64_t sum) {
+  uint32_t slot = hslot(sum, L.hcap);
+  for (uint32_t probe = 0; probe < L.hcap; ++probe) {
+    const uint32_t v = L.hvals[slot];
+    if (v == 0) return 0;
+    const uint64_t *key = L.hkeys + (uint64_t)slot * L.wc;
+    bool eq = true;
+    for (uint32_t i = 0; i < L.wc && eq; ++i) {
+      uint64_t s = A[i];
+      if (i == wr) s |= br;
+      if (i == wj) s &= ~bj;
+      eq = key[i] == s;
+    }
+    if (eq) return v;
+    slot = (slot + 1) & (L.hcap - 1);
+  }
+  return 0;
+}
+
+__global__ void __launch_bounds__(256) k_generate(Lattice L) {
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  const uint32_t P = C->n_newbox;
+  if (P == 0) return;
+  const uint32_t g = C->step, base = C->tail, l1 = L.l1, wc = L.wc;
+  const uint64_t total = (uint64_t)P * l1;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
+    const uint32_t p = (uint32_t)(w / l1), r = (uint32_t)(w % l1);
+    const uint64_t *A = L.cmask + (uint64_t)L.newbox[p] * wc;
+    const uint32_t wr = r >> 6;
+    const uint64_t br = 1ull << (r & 63);
+    const uint64_t Awr = A[wr];
+    if (Awr & br) continue;
+    const uint64_t sumC = L.newhash[p] - hterm(Awr, wr) + hterm(Awr | br, wr);
+    bool ok = true;
+    uint32_t k = 0;
+    for (uint32_t i = 0; i < wc && ok; ++i) {
+      uint64_t x = A[i];
+      const uint64_t Ci = i == wr ? (A[i] | br) : A[i];
+      while (x) {
+        const uint32_t b = (uint32_t)(__ffsll((long long)x) - 1);
+        x &= x - 1;
+        ++k;
+        const uint64_t bj = 1ull << b;
+        const uint64_t sumS = sumC - hterm(Ci, i) + hterm(Ci & ~bj, i);
+        const uint32_t v = box_lookup(L, A, wr, br, i, bj, sumS);
+        if (v == 0 || (i * 64 + b < r && v == g + 1)) { ok = false; break; }
+      }
+    }
+    if (!ok) continue;
+    const uint32_t pos = base + atomicAdd(&C->n_gen, 1u);
+    if (pos >= L.cap) {
+      C->stall = ST_CAND;
+      continue;
+    }
+    for (uint32_t i = 0; i < wc; ++i) L.cmask[(uint64_t)pos * wc + i] = i == wr ? (A[i] | br) : A[i];
+    L.csupp[pos] = 0;
+    L.cbirth[pos] = g;
+    L.cshape[pos] = SH_CIRCLE;
+    atomicMax(&C->max_k, k + 1);
+  }
+}
+
+cudaError_t launch_generate(Lattice L, int grid, cudaStream_t s) {
+  k_generate<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------- stop bookkeeping
+// End of stop g: trace row, test count, the new cohort, CHECKFULLPASS
+// (cohorts whose full pass is complete leave the window), |DASHED| and the
+// loop condition of Algorithm 2.
+__global__ void k_finish(Lattice L) {
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  const uint32_t g = C->step;
+  uint32_t stop;
+  uint64_t first, last;
+  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
+  if (C->n_trace >= L.tcap) {
+    C->error = 4;  // DIC_ECAPACITY
+    C->done = 1;
+    return;
+  }
+  unsigned long long *row = L.trace + (uint64_t)C->n_trace * TRACE_COLS;
+  row[0] = g; row[1] = stop; row[2] = first; row[3] = last;
+  row[4] = C->n_live; row[5] = C->n_newbox; row[6] = C->n_pruned; row[7] = C->n_gen;
+  row[8] = C->n_solid;
+  C->tests += (unsigned long long)C->n_live * (last - first);
+  if (C->n_gen) {
+    L.cohort_start[C->n_cohorts] = C->tail;
+    L.cohort_birth[C->n_cohorts] = g;
+    C->n_cohorts += 1;
+  }
+  C->tail += C->n_gen;
+  C->hash_used += C->n_newbox;
+  C->n_live = C->n_live - C->n_pruned - C->n_solid + C->n_gen;
+  uint32_t ch = C->cohort_head;
+  while (ch < C->n_cohorts && L.cohort_birth[ch] + L.stop_max <= g) ++ch;
+  C->cohort_head = ch;
+  C->head = ch < C->n_cohorts ? L.cohort_start[ch] : C->tail;
+  C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->n_gen = 0;
+  C->n_trace += 1;
+  C->step = g + 1;
+  if (C->n_live == 0) C->done = 1;
+}
+
+cudaError_t launch_finish(Lattice L, cudaStream_t s) {
+  k_finish<<<1, 1, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- output
+__global__ void k_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx, uint32_t *out_count) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < tail; c += gridDim.x * blockDim.x)
+    if (L.cshape[c] == SH_BOX) out_idx[atomicAdd(out_count, 1u)] = c;
+}
+
+cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
+                                   uint32_t *out_count, cudaStream_t s) {
+  if (tail == 0) return cudaSuccess;
+  int grid = (int)((tail + 255) / 256 < 65535u * 4 ? (tail + 255) / 256 : 65535u * 4);
+  k_collect_boxes<<<grid, 256, 0, s>>>(L, tail, out_idx, out_count);
+  return cudaGetLastError();
+}
+
+__global__ void k_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
+                               uint32_t *supp) {
+  const uint64_t total = (uint64_t)cnt * L.wc;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t q = (uint32_t)(i / L.wc), w = (uint32_t)(i % L.wc);
+    masks[i] = L.cmask[(uint64_t)idx[q] * L.wc + w];
+    if (w == 0) supp[q] = L.csupp[idx[q]];
+  }
+}
+
+cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
+                                uint32_t *supp, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  uint64_t want = ((uint64_t)cnt * L.wc + 255) / 256;
+  int grid = (int)(want < 65535ull * 4 ? want : 65535ull * 4);
+  k_gather_boxes<<<grid, 256, 0, s>>>(L, idx, cnt, masks, supp);
+  return cudaGetLastError();
+}
+
+}  // namespace dic

@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in include/dic.h (ctypes; argument marshalling
+only). Every step of mining runs inside libdic.so on the GPU; there is no
+Python or CPU fallback: importing this module fails if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdic.so")
+
+DIC_OK, DIC_EINVAL, DIC_ENOMEM, DIC_ECUDA, DIC_ECAPACITY, DIC_ETIMEOUT, DIC_EBUSY = range(7)
+PATHS = {"auto": 0, "rows": 1, "bitslice": 2, "tensor": 3}
+TRACE_COLUMNS = ("step", "stop", "first", "last", "dashed", "promoted", "pruned", "generated",
+                 "solidified")
+
+
+class DicError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dic status {status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("count_path", ctypes.c_uint32),
+                ("steps_per_sync", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
+                ("profile", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 10)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("tests", ctypes.c_uint64), ("stops", ctypes.c_uint64),
+                ("candidates", ctypes.c_uint64), ("frequent", ctypes.c_uint64),
+                ("l1", ctypes.c_uint32), ("words", ctypes.c_uint32),
+                ("words_compact", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
+                ("count_ms", ctypes.c_double), ("count_launches", ctypes.c_uint64),
+                ("firstpass_ms", ctypes.c_double), ("mine_ms", ctypes.c_double),
+                ("path_launches", ctypes.c_uint32 * 4), ("reserved", ctypes.c_uint32 * 8)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "path_launches")}
+        d["path_launches"] = list(self.path_launches)
+        return d
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdic.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    pvp = ctypes.POINTER(vp)
+    sig = {
+        "dic_load_db": ([vp, u64, u32, pvp], i32),
+        "dic_load_db_csr": ([vp, vp, u64, u32, pvp], i32),
+        "dic_load_db_device": ([vp, u64, u32, vp, pvp], i32),
+        "dic_db_free": ([vp], i32),
+        "dic_db_rows": ([vp], u64),
+        "dic_db_items": ([vp], u32),
+        "dic_db_device_words": ([vp], vp),
+        "dic_options_init": ([ctypes.POINTER(Options)], None),
+        "dic_mine": ([vp, u32, u64, pvp], i32),
+        "dic_mine_ex": ([vp, u32, u64, ctypes.POINTER(Options), vp, pvp], i32),
+        "dic_mine_batch": ([vp, vp, vp, u32, ctypes.POINTER(Options), vp], i32),
+        "dic_result_count": ([vp], u64),
+        "dic_result_words": ([vp], u32),
+        "dic_result_copy": ([vp, vp, vp, vp], i32),
+        "dic_result_trace_len": ([vp], u64),
+        "dic_result_trace": ([vp, vp], i32),
+        "dic_result_stats": ([vp, ctypes.POINTER(Stats)], i32),
+        "dic_result_free": ([vp], None),
+        "dic_minsup_count": ([u64, ctypes.c_double], u32),
+        "dic_status_str": ([i32], ctypes.c_char_p),
+        "dic_last_error": ([], ctypes.c_char_p),
+        "dic_abi_version": ([], u32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int):
+    if rc != DIC_OK:
+        raise DicError(rc, (_lib.dic_last_error() or b"").decode())
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Database:
+    """A device-resident transaction database (dic_db)."""
+
+    def __init__(self, handle: int, n: int, m: int):
+        self._h = ctypes.c_void_p(handle)
+        self.n, self.m = n, m
+        self.W = (m + 63) // 64
+
+    @property
+    def handle(self):
+        return self._h
+
+    def device_words_ptr(self) -> int:
+        return _lib.dic_db_device_words(self._h) or 0
+
+    def free(self):
+        if self._h:
+            _check(_lib.dic_db_free(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib.dic_db_free(self._h)
+        except Exception:
+            pass
+
+
+def load_db(words, n: int, m: int) -> Database:
+    """Host bitmaps uint64 [n, ceil(m/64)] (numpy or pinned torch CPU tensor)."""
+    if isinstance(words, np.ndarray):
+        words = np.ascontiguousarray(words, dtype=np.uint64)
+    h = ctypes.c_void_p()
+    _check(_lib.dic_load_db(_ptr(words) if n else None, n, m, ctypes.byref(h)))
+    return Database(h.value, n, m)
+
+
+def load_db_csr(row_ptr, items, n: int, m: int) -> Database:
+    """Host CSR item lists (row_ptr uint64[n+1], items uint32[nnz])."""
+    if isinstance(row_ptr, np.ndarray):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+    if isinstance(items, np.ndarray):
+        items = np.ascontiguousarray(items, dtype=np.uint32)
+        if items.size == 0:
+            items = np.zeros(1, dtype=np.uint32)
+    h = ctypes.c_void_p()
+    _check(_lib.dic_load_db_csr(_ptr(row_ptr), _ptr(items), n, m, ctypes.byref(h)))
+    return Database(h.value, n, m)
+
+
+def load_db_device(words_tensor, n: int, m: int, stream=None) -> Database:
+    """Device bitmaps (e.g. a CUDA torch int64 tensor [n, W]); copied."""
+    h = ctypes.c_void_p()
+    _check(_lib.dic_load_db_device(words_tensor.data_ptr() if n else None, n, m,
+                                   _stream_handle(stream), ctypes.byref(h)))
+    return Database(h.value, n, m)
+
+
+@dataclass
+class Result:
+    W: int
+    masks: np.ndarray     # uint64 [count, W]
+    k: np.ndarray         # uint32 [count]
+    support: np.ndarray   # uint32 [count]
+    trace: np.ndarray     # uint64 [stops, 9]
+    stats: dict
+
+    def itemsets(self):
+        """[(tuple(items), support)] in canonical order."""
+        out = []
+        for q in range(len(self.k)):
+            its = []
+            for w in range(self.W):
+                x = int(self.masks[q, w])
+                while x:
+                    b = (x & -x).bit_length() - 1
+                    its.append(w * 64 + b)
+                    x &= x - 1
+            out.append((tuple(its), int(self.support[q])))
+        return out
+
+
+def _result(h) -> Result:
+    cnt = _lib.dic_result_count(h)
+    W = _lib.dic_result_words(h)
+    masks = np.zeros((max(cnt, 1), max(W, 1)), dtype=np.uint64)
+    k = np.zeros(max(cnt, 1), dtype=np.uint32)
+    sp = np.zeros(max(cnt, 1), dtype=np.uint32)
+    _check(_lib.dic_result_copy(h, masks.ctypes.data, k.ctypes.data, sp.ctypes.data))
+    tl = _lib.dic_result_trace_len(h)
+    tr = np.zeros((max(tl, 1), len(TRACE_COLUMNS)), dtype=np.uint64)
+    _check(_lib.dic_result_trace(h, tr.ctypes.data))
+    st = Stats()
+    _check(_lib.dic_result_stats(h, ctypes.byref(st)))
+    _lib.dic_result_free(h)
+    return Result(W, masks[:cnt], k[:cnt], sp[:cnt], tr[:tl], st.as_dict())
+
+
+def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
+            profile: bool = False, max_candidates: int = 0) -> Options:
+    o = Options()
+    _lib.dic_options_init(ctypes.byref(o))
+    o.count_path = PATHS[path]
+    o.steps_per_sync = steps_per_sync
+    o.use_graph = 1 if use_graph else 0
+    o.profile = 1 if profile else 0
+    o.max_candidates = max_candidates
+    return o
+
+
+def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
+         profile: bool = False, steps_per_sync: int = 0, use_graph: bool = True,
+         max_candidates: int = 0) -> Result:
+    """All itemsets with support >= minsup (integer count), blocks of M rows."""
+    o = options(path, steps_per_sync, use_graph, profile, max_candidates)
+    h = ctypes.c_void_p()
+    _check(_lib.dic_mine_ex(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
+                            ctypes.byref(h)))
+    return _result(h)
+
+
+def mine_batch(dbs, minsups, Ms, path: str = "auto", profile: bool = False):
+    """Mine several (db, minsup, M) queries together; returns a list of Result."""
+    cnt = len(dbs)
+    handles = (ctypes.c_void_p * max(cnt, 1))(*[d.handle.value for d in dbs])
+    ms = np.ascontiguousarray(minsups, dtype=np.uint32)
+    Ms_ = np.ascontiguousarray(Ms, dtype=np.uint64)
+    outs = (ctypes.c_void_p * max(cnt, 1))()
+    o = options(path, profile=profile)
+    _check(_lib.dic_mine_batch(ctypes.cast(handles, ctypes.c_void_p), ms.ctypes.data,
+                               Ms_.ctypes.data, cnt, ctypes.byref(o),
+                               ctypes.cast(outs, ctypes.c_void_p)))
+    return [_result(ctypes.c_void_p(outs[i])) for i in range(cnt)]
+
+
+def minsup_count(n: int, frac: float) -> int:
+    return _lib.dic_minsup_count(n, frac)

@@ -1,0 +1,74 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry
+point include/dic.h declares, and rejects bad arguments before any device
+work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dic.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(dic_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1812_10959_gb300 import build as pb
+    return pb.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("dic_load_db", "dic_load_db_csr", "dic_load_db_device", "dic_mine",
+                 "dic_mine_ex", "dic_mine_batch", "dic_result_copy", "dic_result_trace",
+                 "dic_db_free", "dic_result_free", "dic_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (dic_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for f in declared_functions():
+        assert getattr(lib, f) is not None
+
+
+def test_host_side_validation_without_gpu(libpath):
+    import paper_1812_10959_gb300 as dic
+    lib = dic.dic.lib()
+    assert lib.dic_abi_version() == 1
+    assert lib.dic_minsup_count(10_000, 0.02) == 200
+    assert lib.dic_minsup_count(1_000_000, 0.0025) == 2500
+    assert lib.dic_minsup_count(7, 0.0) == 1
+    assert lib.dic_status_str(4) == b"capacity exceeded"
+    # padding bits beyond m are rejected on the host, before any CUDA call
+    words = np.array([[1 << 5]], dtype=np.uint64)
+    with pytest.raises(dic.DicError) as e:
+        dic.load_db(words, 1, 5)
+    assert e.value.status == dic.dic.DIC_EINVAL
+    with pytest.raises(dic.DicError) as e:
+        dic.load_db(words, 1, 0)
+    assert e.value.status == dic.dic.DIC_EINVAL
+    # row_ptr must start at 0 and not decrease
+    with pytest.raises(dic.DicError):
+        dic.load_db_csr(np.array([1, 2], dtype=np.uint64), np.array([0], dtype=np.uint32), 1, 4)
+    with pytest.raises(dic.DicError):
+        dic.load_db_csr(np.array([0, 2, 1], dtype=np.uint64), np.array([0, 1], dtype=np.uint32),
+                        2, 4)
+    # n >= 2^31 is refused
+    h = ctypes.c_void_p()
+    assert lib.dic_load_db(None, 1 << 31, 4, ctypes.byref(h)) == dic.dic.DIC_EINVAL
+    # mining arguments
+    assert lib.dic_mine(None, 1, 1, ctypes.byref(h)) == dic.dic.DIC_EINVAL
