@@ -294,14 +294,33 @@ class Miner {
   Lattice L_{};
   Ctrl *h_ctrl_ = nullptr;
   uint32_t nw_ = 2;  // rows-kernel width bucket
+  // BITSLICE path state
+  bool bs_ok_ = false;     // the block's columns fit in shared memory
+  int bs_tw_ = 16;         // 32-row words per tile
+  uint32_t bs_l1p_ = 0;    // l1 rounded up to a multiple of 4
+  uint32_t *bs_V_ = nullptr;
+  int bs_grid_ = 0;
+  size_t smem_optin_ = 0;
+  int cur_path_ = DIC_COUNT_ROWS;
   int grid_ = 0;
   uint32_t launches_ = 0;
   uint32_t path_launches_[4] = {0, 0, 0, 0};
   uint64_t candidates_cap_limit_ = 0xFFFFFFF0ull;
 };
 
+// Count path for the next stops: BITSLICE whenever the block's columns fit in
+// shared memory and every dashed itemset has at most KRMAX items, else ROWS.
 int Miner::count_path_for_stop() const {
-  return DIC_COUNT_ROWS;
+  if (opt_.count_path == DIC_COUNT_ROWS) return DIC_COUNT_ROWS;
+  if (!bs_ok_ || h_ctrl_->max_k > (uint32_t)KRMAX) return DIC_COUNT_ROWS;
+  return DIC_COUNT_BITSLICE;
+}
+
+static int kr_bucket(uint32_t max_k) {
+  if (max_k <= 2) return 2;
+  if (max_k <= 4) return 4;
+  if (max_k <= 8) return 8;
+  return 16;
 }
 
 dic_status Miner::sync_ctrl() {
@@ -320,8 +339,23 @@ dic_status Miner::launch_phase(int phase) {
         CU(cudaEventCreate(&b));
         CU(cudaEventRecord(a, s_));
       }
-      e = launch_count_rows(L_, (int)nw_, grid_, s_);
-      path_launches_[DIC_COUNT_ROWS]++;
+      if (cur_path_ == DIC_COUNT_BITSLICE) {
+        const int kre = kr_bucket(h_ctrl_->max_k);
+        const uint32_t win = h_ctrl_->tail - h_ctrl_->head;
+        uint32_t chunk = (win + bs_grid_ - 1) / bs_grid_;
+        chunk = std::max<uint32_t>(256, (chunk + 3) & ~3u);
+        chunk = std::min(chunk, bitslice_max_chunk(bs_tw_, kre, bs_l1p_, smem_optin_));
+        e = launch_slice_block(L_, bs_V_, bs_tw_, bs_l1p_, s_);
+        ++launches_;
+        if (e == cudaSuccess) {
+          if (opt_.profile) CU(cudaEventRecord(a, s_));
+          e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_grid_, s_);
+        }
+        path_launches_[DIC_COUNT_BITSLICE]++;
+      } else {
+        e = launch_count_rows(L_, (int)nw_, grid_, s_);
+        path_launches_[DIC_COUNT_ROWS]++;
+      }
       if (opt_.profile) {
         CU(cudaEventRecord(b, s_));
         events_.push_back({a, b});
@@ -359,8 +393,12 @@ dic_status Miner::grow_candidates(uint32_t need) {
   TRY(alloc(&N.csupp, ncap));
   TRY(alloc(&N.cbirth, ncap));
   TRY(alloc(&N.cshape, ncap));
+  TRY(alloc(&N.ck, ncap));
+  TRY(alloc(&N.cranks, (size_t)ncap * KRMAX));
   TRY(alloc(&N.newbox, ncap));
   TRY(alloc(&N.newhash, ncap));
+  CU(cudaMemcpyAsync(N.ck, L_.ck, (size_t)keep, cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.cranks, L_.cranks, (size_t)keep * KRMAX * 2, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.cmask, L_.cmask, (size_t)keep * L_.wc * 8, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.csupp, L_.csupp, (size_t)keep * 4, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.cbirth, L_.cbirth, (size_t)keep * 4, cudaMemcpyDeviceToDevice, s_));
@@ -368,7 +406,7 @@ dic_status Miner::grow_candidates(uint32_t need) {
   CU(cudaMemcpyAsync(N.newbox, L_.newbox, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.newhash, L_.newhash, (size_t)nb * 8, cudaMemcpyDeviceToDevice, s_));
   drop(L_.cmask); drop(L_.csupp); drop(L_.cbirth); drop(L_.cshape); drop(L_.newbox);
-  drop(L_.newhash);
+  drop(L_.newhash); drop(L_.ck); drop(L_.cranks);
   L_ = N;
   return DIC_OK;
 }
@@ -498,6 +536,8 @@ dic_status Miner::run(dic_result **out) {
     TRY(alloc(&L_.csupp, cap));
     TRY(alloc(&L_.cbirth, cap));
     TRY(alloc(&L_.cshape, cap));
+    TRY(alloc(&L_.ck, cap));
+    TRY(alloc(&L_.cranks, (size_t)cap * KRMAX));
     TRY(alloc(&L_.newbox, cap));
     TRY(alloc(&L_.newhash, cap));
     L_.hcap = 1u << 14;
@@ -523,6 +563,32 @@ dic_status Miner::run(dic_result **out) {
     ++launches_;
     nw_ = (uint32_t)rows_width_bucket(2, wc);
 
+    // ---- BITSLICE tiles: widest tile whose double buffer leaves room for
+    // a useful candidate chunk in shared memory
+    {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      smem_optin_ = (size_t)optin;
+      bs_l1p_ = (l1 + 3) & ~3u;
+      bs_ok_ = false;
+      if (l1 <= 65535 && opt_.count_path != DIC_COUNT_ROWS) {
+        for (int tw : {16, 8, 4}) {
+          if (bitslice_max_chunk(tw, 16, bs_l1p_, smem_optin_) >= 1024) {
+            bs_tw_ = tw;
+            bs_ok_ = true;
+            break;
+          }
+        }
+      }
+      if (bs_ok_) {
+        const uint64_t blockmax = std::min<uint64_t>(M_, n);
+        const uint64_t ntiles = ((blockmax + 31) / 32 + bs_tw_ - 1) / bs_tw_;
+        TRY(alloc(&bs_V_, (size_t)ntiles * bs_l1p_ * (bs_tw_ + 1)));
+        bs_grid_ = sm_count();
+      }
+    }
+
     // ---- the stop loop of Algorithm 2
     uint32_t chunk = opt_.steps_per_sync ? opt_.steps_per_sync : 4;
     const uint32_t chunk_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
@@ -530,6 +596,7 @@ dic_status Miner::run(dic_result **out) {
       TRY(grow_trace(h_ctrl_->n_trace + chunk + 2));
       int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
       nw_ = bucket ? (uint32_t)bucket : 0;
+      cur_path_ = count_path_for_stop();
       for (uint32_t i = 0; i < chunk; ++i) TRY(launch_stop_from(PH_COUNT));
       TRY(sync_ctrl());
       if (h_ctrl_->error)
@@ -540,6 +607,7 @@ dic_status Miner::run(dic_result **out) {
         if (st == ST_WIDTH) {
           int b = rows_width_bucket(h_ctrl_->max_k, wc);
           nw_ = b ? (uint32_t)b : 0;
+          cur_path_ = count_path_for_stop();
           phase = PH_COUNT;
         } else if (st == ST_HASH) {
           TRY(grow_hash());

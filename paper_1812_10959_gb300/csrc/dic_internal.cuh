@@ -18,6 +18,9 @@ enum Stall : uint32_t { ST_NONE = 0, ST_WIDTH = 1, ST_HASH = 2, ST_CAND = 3 };
 enum Phase : int { PH_COUNT = 0, PH_PROMOTE = 1, PH_HASH = 2, PH_GEN = 3, PH_FINISH = 4 };
 
 constexpr int TRACE_COLS = 9;
+// Ranks kept per candidate record for the BITSLICE count path; itemsets with
+// more items are counted by the ROWS path.
+constexpr int KRMAX = 16;
 
 // Device-resident loop state of Algorithm 2 (one per query).
 struct Ctrl {
@@ -50,6 +53,8 @@ struct Lattice {
   uint32_t *csupp;     // [cap]
   uint32_t *cbirth;    // [cap] global stop at which the record was created
   uint8_t *cshape;     // [cap]
+  uint8_t *ck;         // [cap] itemset size (saturates at 255)
+  uint16_t *cranks;    // [cap][KRMAX] ascending ranks (first KRMAX of them)
   uint32_t *newbox;    // [cap] records promoted at this stop
   uint64_t *newhash;   // [cap] hash pre-image sums of those records
   uint32_t cap;
@@ -103,6 +108,17 @@ cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
                                  uint32_t *out_count, cudaStream_t s);
 cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
                                 uint32_t *supp, cudaStream_t s);
+
+// BITSLICE path (kernels_count_bitslice.cu). V holds the stop's block as
+// per-rank bit columns, tile-major: tile t covers rows first+32*TW*t ..,
+// V[(t*l1p + r)*(TW+1) + w] = rows first+32*(TW*t+w) .. +31 of rank r (bit j
+// = row +j); column TW is padding. l1p = l1 rounded up to a multiple of 4.
+cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, cudaStream_t s);
+cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
+                                  uint32_t chunk, int grid, cudaStream_t s);
+// Largest candidate chunk whose bitslice shared-memory footprint fits.
+uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit);
+size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk);
 
 // Width bucket (max nonzero 32-bit halves per candidate) the rows kernel
 // needs for itemsets of up to max_k items in wc-word masks.

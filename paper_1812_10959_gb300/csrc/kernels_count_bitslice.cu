@@ -1,0 +1,222 @@
+// COUNTSUPPORT (Algorithm 3), BITSLICE path.
+//
+// The containment test of Section 4.1 asks, for every candidate C and row T
+// of the block, whether every item of C is set in T. Transposing the block
+// into one bit column per frequent item (32 rows per word) turns the test of
+// 32 rows at once into an AND of C's k column words, and the count of
+// contained rows into popc of that AND. The set of (candidate, row) tests and
+// every support are exactly those of the row-wise test; only the order in
+// which the bits are combined changes.
+//
+// Per stop:
+//   k_slice_block    rows [first, last) of the compacted bitmaps -> V, the
+//                    columns of every rank, tile-major and padded so that a
+//                    tile is one contiguous, shared-memory-ready byte range.
+//   k_count_bitslice each CTA owns a contiguous chunk of the candidate
+//                    window; it streams the V tiles through a double buffer
+//                    (cp.async) and every thread ANDs and popcounts its
+//                    candidates' columns. Counts stay in shared memory until
+//                    the chunk is done, so every counter is written once.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dic_internal.cuh"
+
+namespace dic {
+
+constexpr int BS_THREADS = 512;
+
+// ------------------------------------------------------------ transpose
+__global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t *__restrict__ V, int tw,
+                                                     uint32_t l1p) {
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  uint32_t stop;
+  uint64_t first, last;
+  block_of(C->step, L.stop_max, L.M, L.n, &stop, &first, &last);
+  const uint32_t nw32 = (uint32_t)((last - first + 31) / 32);
+  const uint32_t ntiles = (nw32 + tw - 1) / tw;
+  const uint32_t wc = L.wc;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t items = (uint64_t)ntiles * tw * wc;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
+       it += nwarps) {
+    const uint32_t w = (uint32_t)(it / wc), j = (uint32_t)(it % wc);
+    const uint64_t row = first + 32ull * w + lane;
+    const uint64_t x = (w < nw32 && row < last) ? __ldg(L.rows + row * wc + j) : 0ull;
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> b) & 1u);
+      if ((int)lane == b) lo = v;
+    }
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> (b + 32)) & 1u);
+      if ((int)lane == b) hi = v;
+    }
+    const uint32_t t = w / tw, wi = w % tw;
+    const uint32_t r0 = j * 64 + lane, r1 = r0 + 32;
+    if (r0 < l1p) V[((uint64_t)t * l1p + r0) * (tw + 1) + wi] = lo;
+    if (r1 < l1p) V[((uint64_t)t * l1p + r1) * (tw + 1) + wi] = hi;
+  }
+}
+
+cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, cudaStream_t s) {
+  const uint64_t blockmax = L.M < L.n ? L.M : L.n;
+  const uint64_t nw32 = (blockmax + 31) / 32;
+  const uint64_t items = ((nw32 + tw - 1) / tw) * tw * L.wc;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint64_t want = (items + 7) / 8;
+  int grid = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
+  if (grid < 1) grid = 1;
+  k_slice_block<<<grid, 256, 0, s>>>(L, V, tw, l1p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- count
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk) {
+  const size_t tile = (size_t)l1p * (tw + 1) * 4;
+  return 2 * tile + (size_t)chunk * (2 * kre + 4 + 1) + 16;
+}
+
+uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit) {
+  const size_t tile = (size_t)l1p * (tw + 1) * 4;
+  if (2 * tile + 16 >= smem_limit) return 0;
+  size_t c = (smem_limit - 2 * tile - 16) / (2 * kre + 4 + 1);
+  c &= ~(size_t)3;
+  return c > 0x7fffffff ? 0x7fffffff : (uint32_t)c;
+}
+
+template <int TW, int KRE>
+__global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
+                                                               const uint32_t *__restrict__ V,
+                                                               uint32_t l1p, uint32_t chunk) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  if (C->max_k > (uint32_t)KRE) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->stall = ST_WIDTH;
+    return;
+  }
+  const uint32_t tile_words = l1p * (TW + 1);
+  uint32_t *S0 = sm;
+  uint32_t *S1 = sm + tile_words;
+  uint16_t *rk = reinterpret_cast<uint16_t *>(sm + 2 * tile_words);
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(rk + (size_t)chunk * KRE);
+  uint8_t *kk = reinterpret_cast<uint8_t *>(cnt + chunk);
+
+  uint32_t stop;
+  uint64_t first, last;
+  block_of(C->step, L.stop_max, L.M, L.n, &stop, &first, &last);
+  const uint32_t nw32 = (uint32_t)((last - first + 31) / 32);
+  const uint32_t ntiles = (nw32 + TW - 1) / TW;
+  const uint32_t head = C->head, tail = C->tail;
+  const uint32_t ncand = tail - head;
+  const uint32_t nchunks = (ncand + chunk - 1) / chunk;
+  const uint32_t tid = threadIdx.x;
+
+  for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const uint32_t c0 = head + ch * chunk;
+    const uint32_t cn = (tail - c0) < chunk ? (tail - c0) : chunk;
+    __syncthreads();  // shared memory of the previous chunk is free
+    {
+      const uint32_t *src = V;
+      for (uint32_t o = tid * 4; o < tile_words; o += BS_THREADS * 4) cp_async16(S0 + o, src + o);
+      cp_async_commit();
+    }
+    for (uint32_t i = tid; i < cn; i += BS_THREADS) {
+      const uint32_t c = c0 + i;
+      const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
+      kk[i] = (uint8_t)k;
+      cnt[i] = 0;
+#pragma unroll
+      for (int q = 0; q < KRE; ++q)
+        rk[(size_t)i * KRE + q] = (uint32_t)q < k ? L.cranks[(uint64_t)c * KRMAX + q] : (uint16_t)0;
+    }
+    for (uint32_t t = 0; t < ntiles; ++t) {
+      if (t + 1 < ntiles) {
+        uint32_t *dst = ((t + 1) & 1) ? S1 : S0;
+        const uint32_t *src = V + (size_t)(t + 1) * tile_words;
+        for (uint32_t o = tid * 4; o < tile_words; o += BS_THREADS * 4) cp_async16(dst + o, src + o);
+      }
+      cp_async_commit();
+      cp_async_wait_1();
+      __syncthreads();
+      const uint32_t *S = (t & 1) ? S1 : S0;
+      for (uint32_t i = tid; i < cn; i += BS_THREADS) {
+        const uint32_t k = kk[i];
+        if (k == 0) continue;
+        const uint16_t *ri = rk + (size_t)i * KRE;
+        uint32_t acc[TW];
+        {
+          const uint32_t *p = S + (uint32_t)ri[0] * (TW + 1);
+#pragma unroll
+          for (int w = 0; w < TW; ++w) acc[w] = p[w];
+        }
+        for (uint32_t q = 1; q < k; ++q) {
+          const uint32_t *p = S + (uint32_t)ri[q] * (TW + 1);
+#pragma unroll
+          for (int w = 0; w < TW; ++w) acc[w] &= p[w];
+        }
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < TW; ++w) sum += __popc(acc[w]);
+        cnt[i] += sum;
+      }
+      __syncthreads();  // the buffer of tile t may be overwritten next
+    }
+    for (uint32_t i = tid; i < cn; i += BS_THREADS)
+      if (kk[i] && cnt[i]) L.csupp[c0 + i] += cnt[i];
+  }
+}
+
+template <int TW, int KRE>
+static cudaError_t go(Lattice L, const uint32_t *V, uint32_t l1p, uint32_t chunk, int grid,
+                      cudaStream_t s) {
+  const size_t smem = bitslice_smem(TW, KRE, l1p, chunk);
+  cudaError_t e = cudaFuncSetAttribute(k_count_bitslice<TW, KRE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_count_bitslice<TW, KRE><<<grid, BS_THREADS, smem, s>>>(L, V, l1p, chunk);
+  return cudaGetLastError();
+}
+
+template <int TW>
+static cudaError_t go_k(Lattice L, const uint32_t *V, int kre, uint32_t l1p, uint32_t chunk,
+                        int grid, cudaStream_t s) {
+  switch (kre) {
+    case 2: return go<TW, 2>(L, V, l1p, chunk, grid, s);
+    case 4: return go<TW, 4>(L, V, l1p, chunk, grid, s);
+    case 8: return go<TW, 8>(L, V, l1p, chunk, grid, s);
+    default: return go<TW, 16>(L, V, l1p, chunk, grid, s);
+  }
+}
+
+cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
+                                  uint32_t chunk, int grid, cudaStream_t s) {
+  switch (tw) {
+    case 16: return go_k<16>(L, V, kre, l1p, chunk, grid, s);
+    case 8: return go_k<8>(L, V, kre, l1p, chunk, grid, s);
+    default: return go_k<4>(L, V, kre, l1p, chunk, grid, s);
+  }
+}
+
+}  // namespace dic

@@ -208,6 +208,9 @@ __global__ void k_pair_join(Lattice L, uint64_t npairs) {
       L.csupp[p] = 0;
       L.cbirth[p] = 0;
       L.cshape[p] = SH_CIRCLE;
+      L.ck[p] = 2;
+      L.cranks[p * KRMAX + 0] = (uint16_t)a;
+      L.cranks[p * KRMAX + 1] = (uint16_t)b;
     }
   }
 }
@@ -393,10 +396,18 @@ __global__ void __launch_bounds__(256) k_generate(Lattice L) {
       C->stall = ST_CAND;
       continue;
     }
-    for (uint32_t i = 0; i < wc; ++i) L.cmask[(uint64_t)pos * wc + i] = i == wr ? (A[i] | br) : A[i];
+    uint32_t q = 0;
+    uint16_t *rk = L.cranks + (uint64_t)pos * KRMAX;
+    for (uint32_t i = 0; i < wc; ++i) {
+      const uint64_t x = i == wr ? (A[i] | br) : A[i];
+      L.cmask[(uint64_t)pos * wc + i] = x;
+      for (uint64_t y = x; y && q < KRMAX; y &= y - 1)
+        rk[q++] = (uint16_t)(i * 64 + __ffsll((long long)y) - 1);
+    }
     L.csupp[pos] = 0;
     L.cbirth[pos] = g;
     L.cshape[pos] = SH_CIRCLE;
+    L.ck[pos] = (uint8_t)(k + 1 < 255 ? k + 1 : 255);
     atomicMax(&C->max_k, k + 1);
   }
 }
