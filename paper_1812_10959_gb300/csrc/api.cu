@@ -271,13 +271,16 @@ class Miner {
   void release() {
     for (void *p : bufs_) cudaFreeAsync(p, s_);
     bufs_.clear();
-    for (auto &ev : events_) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
-    events_.clear();
+    for (cudaEvent_t ev : ev_pool_) cudaEventDestroy(ev);
+    ev_pool_.clear();
+    ev_used_ = 0;
     if (h_ctrl_) { cudaFreeHost(h_ctrl_); h_ctrl_ = nullptr; }
   }
 
   dic_status grow_candidates(uint32_t need);
-  dic_status grow_hash();
+  dic_status grow_hash(uint64_t entries);
+  dic_status next_event(cudaEvent_t *ev);
+  dic_status harvest_events();
   dic_status grow_trace(uint32_t need);
   dic_status launch_phase(int phase);
   dic_status launch_stop_from(int phase);
@@ -290,7 +293,10 @@ class Miner {
   dic_options opt_;
   cudaStream_t s_;
   std::vector<void *> bufs_;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events_;
+  std::vector<cudaEvent_t> ev_pool_;   // profiling events, reused every group
+  size_t ev_used_ = 0;
+  double count_ms_ = 0;
+  uint64_t count_timed_ = 0;
   Lattice L_{};
   Ctrl *h_ctrl_ = nullptr;
   uint32_t nw_ = 2;  // rows-kernel width bucket
@@ -323,9 +329,33 @@ static int kr_bucket(uint32_t max_k) {
   return 16;
 }
 
+dic_status Miner::next_event(cudaEvent_t *ev) {
+  if (ev_used_ == ev_pool_.size()) {
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    ev_pool_.push_back(e);
+  }
+  *ev = ev_pool_[ev_used_++];
+  return DIC_OK;
+}
+
+// Sum the count-kernel event pairs recorded since the last group (the
+// stream has been synchronised).
+dic_status Miner::harvest_events() {
+  for (size_t i = 0; i + 1 < ev_used_; i += 2) {
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, ev_pool_[i], ev_pool_[i + 1]));
+    count_ms_ += ms;
+    ++count_timed_;
+  }
+  ev_used_ = 0;
+  return DIC_OK;
+}
+
 dic_status Miner::sync_ctrl() {
   CU(cudaMemcpyAsync(h_ctrl_, L_.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s_));
   CU(cudaStreamSynchronize(s_));
+  if (opt_.profile) TRY(harvest_events());
   return DIC_OK;
 }
 
@@ -334,11 +364,6 @@ dic_status Miner::launch_phase(int phase) {
   switch (phase) {
     case PH_COUNT: {
       cudaEvent_t a = nullptr, b = nullptr;
-      if (opt_.profile) {
-        CU(cudaEventCreate(&a));
-        CU(cudaEventCreate(&b));
-        CU(cudaEventRecord(a, s_));
-      }
       if (cur_path_ == DIC_COUNT_BITSLICE) {
         const int kre = kr_bucket(h_ctrl_->max_k);
         const uint32_t win = h_ctrl_->tail - h_ctrl_->head;
@@ -348,24 +373,30 @@ dic_status Miner::launch_phase(int phase) {
         e = launch_slice_block(L_, bs_V_, bs_tw_, bs_l1p_, s_);
         ++launches_;
         if (e == cudaSuccess) {
-          if (opt_.profile) CU(cudaEventRecord(a, s_));
+          if (opt_.profile) {
+            TRY(next_event(&a));
+            CU(cudaEventRecord(a, s_));
+          }
           e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_grid_, s_);
         }
         path_launches_[DIC_COUNT_BITSLICE]++;
       } else {
+        if (opt_.profile) {
+          TRY(next_event(&a));
+          CU(cudaEventRecord(a, s_));
+        }
         e = launch_count_rows(L_, (int)nw_, grid_, s_);
         path_launches_[DIC_COUNT_ROWS]++;
       }
-      if (opt_.profile) {
+      if (opt_.profile && e == cudaSuccess) {
+        TRY(next_event(&b));
         CU(cudaEventRecord(b, s_));
-        events_.push_back({a, b});
       }
       break;
     }
     case PH_PROMOTE: e = launch_promote(L_, grid_, s_); break;
     case PH_HASH: e = launch_hash_insert(L_, grid_, s_); break;
-    case PH_GEN: e = launch_generate(L_, grid_, s_); break;
-    case PH_FINISH: e = launch_finish(L_, s_); break;
+    case PH_GEN: e = launch_generate_finish(L_, grid_, s_); break;
   }
   ++launches_;
   if (e != cudaSuccess) return fail(DIC_ECUDA, "kernel launch (phase %d): %s", phase,
@@ -373,8 +404,14 @@ dic_status Miner::launch_phase(int phase) {
   return DIC_OK;
 }
 
+// The kernels of one stop from `phase` on. The ROWS path runs PRUNE and the
+// box-set insert as kernels of their own; the BITSLICE count kernel applies
+// both in its epilogue.
 dic_status Miner::launch_stop_from(int phase) {
-  for (int p = phase; p <= PH_FINISH; ++p) TRY(launch_phase(p));
+  for (int p = phase; p <= PH_GEN; ++p) {
+    if (cur_path_ != DIC_COUNT_ROWS && (p == PH_PROMOTE || p == PH_HASH)) continue;
+    TRY(launch_phase(p));
+  }
   return DIC_OK;
 }
 
@@ -395,8 +432,10 @@ dic_status Miner::grow_candidates(uint32_t need) {
   TRY(alloc(&N.cshape, ncap));
   TRY(alloc(&N.ck, ncap));
   TRY(alloc(&N.cranks, (size_t)ncap * KRMAX));
+  TRY(alloc(&N.cpromo, ncap));
   TRY(alloc(&N.newbox, ncap));
   TRY(alloc(&N.newhash, ncap));
+  CU(cudaMemcpyAsync(N.cpromo, L_.cpromo, (size_t)keep * 4, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.ck, L_.ck, (size_t)keep, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.cranks, L_.cranks, (size_t)keep * KRMAX * 2, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.cmask, L_.cmask, (size_t)keep * L_.wc * 8, cudaMemcpyDeviceToDevice, s_));
@@ -406,23 +445,22 @@ dic_status Miner::grow_candidates(uint32_t need) {
   CU(cudaMemcpyAsync(N.newbox, L_.newbox, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.newhash, L_.newhash, (size_t)nb * 8, cudaMemcpyDeviceToDevice, s_));
   drop(L_.cmask); drop(L_.csupp); drop(L_.cbirth); drop(L_.cshape); drop(L_.newbox);
-  drop(L_.newhash); drop(L_.ck); drop(L_.cranks);
+  drop(L_.newhash); drop(L_.ck); drop(L_.cranks); drop(L_.cpromo);
   L_ = N;
   return DIC_OK;
 }
 
-dic_status Miner::grow_hash() {
-  uint64_t ncap = (uint64_t)L_.hcap * 2;
-  while ((uint64_t)(h_ctrl_->hash_used + h_ctrl_->n_newbox) * 2 > ncap) ncap *= 2;
+// Rebuild the box set with room for `entries` boxes at load factor 1/4.
+dic_status Miner::grow_hash(uint64_t entries) {
+  uint64_t ncap = std::max<uint64_t>((uint64_t)L_.hcap * 2, 4096);
+  while (ncap < entries * 4) ncap *= 2;
   if (ncap > (1ull << 31)) return fail(DIC_ECAPACITY, "box set would exceed 2^31 slots");
   Lattice N = L_;
   N.hcap = (uint32_t)ncap;
-  TRY(alloc(&N.hkeys, (size_t)ncap * L_.wc));
-  TRY(alloc(&N.hvals, ncap, true));
-  CU(launch_rehash(N, L_.hkeys, L_.hvals, L_.hcap, s_));
+  TRY(alloc(&N.hslot, ncap, true));
+  CU(launch_rehash(N, L_.hslot, L_.hcap, s_));
   ++launches_;
-  drop(L_.hkeys);
-  drop(L_.hvals);
+  drop(L_.hslot);
   L_ = N;
   return DIC_OK;
 }
@@ -538,11 +576,12 @@ dic_status Miner::run(dic_result **out) {
     TRY(alloc(&L_.cshape, cap));
     TRY(alloc(&L_.ck, cap));
     TRY(alloc(&L_.cranks, (size_t)cap * KRMAX));
+    TRY(alloc(&L_.cpromo, cap));
     TRY(alloc(&L_.newbox, cap));
     TRY(alloc(&L_.newhash, cap));
-    L_.hcap = 1u << 14;
-    TRY(alloc(&L_.hkeys, (size_t)L_.hcap * wc));
-    TRY(alloc(&L_.hvals, L_.hcap, true));
+    L_.hcap = 1u << 12;
+    while ((uint64_t)L_.hcap < npairs * 4 && L_.hcap < (1u << 31)) L_.hcap <<= 1;
+    TRY(alloc(&L_.hslot, L_.hcap, true));
     L_.tcap = std::max<uint32_t>(64, (uint32_t)std::min<uint64_t>(stop_max64 * 3 + 16, 1u << 20));
     TRY(alloc(&L_.trace, (size_t)L_.tcap * TRACE_COLS));
     TRY(alloc(&L_.cohort_start, (size_t)L_.tcap + 2));
@@ -594,6 +633,8 @@ dic_status Miner::run(dic_result **out) {
     const uint32_t chunk_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
     for (;;) {
       TRY(grow_trace(h_ctrl_->n_trace + chunk + 2));
+      if ((uint64_t)(h_ctrl_->hash_used + h_ctrl_->n_live) * 2 > L_.hcap)
+        TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live));
       int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
       nw_ = bucket ? (uint32_t)bucket : 0;
       cur_path_ = count_path_for_stop();
@@ -609,9 +650,9 @@ dic_status Miner::run(dic_result **out) {
           nw_ = b ? (uint32_t)b : 0;
           cur_path_ = count_path_for_stop();
           phase = PH_COUNT;
-        } else if (st == ST_HASH) {
-          TRY(grow_hash());
-          phase = PH_HASH;
+        } else if (st == ST_HASH || st == ST_HASH_COUNT) {
+          TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live + h_ctrl_->n_newbox));
+          phase = st == ST_HASH ? PH_HASH : PH_COUNT;
         } else if (st == ST_CAND) {
           TRY(grow_candidates(h_ctrl_->tail + h_ctrl_->n_gen));
           h_ctrl_->n_gen = 0;
@@ -620,6 +661,7 @@ dic_status Miner::run(dic_result **out) {
           return fail(DIC_ECUDA, "unknown stall code %u", st);
         }
         h_ctrl_->stall = ST_NONE;
+        h_ctrl_->blocks_done = 0;
         CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
         TRY(launch_stop_from(phase));
         TRY(sync_ctrl());
@@ -697,14 +739,8 @@ dic_status Miner::run(dic_result **out) {
   res->stats.kernel_launches = launches_;
   for (int i = 0; i < 4; ++i) res->stats.path_launches[i] = path_launches_[i];
   if (opt_.profile) {
-    double tot = 0;
-    for (auto &ev : events_) {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, ev.first, ev.second);
-      tot += ms;
-    }
-    res->stats.count_ms = tot;
-    res->stats.count_launches = events_.size();
+    res->stats.count_ms = count_ms_;
+    res->stats.count_launches = count_timed_;
   }
   release();
   cudaError_t e = cudaStreamSynchronize(s_);

@@ -14,8 +14,11 @@ enum Shape : uint8_t { SH_NIL = 0, SH_CIRCLE = 1, SH_BOX = 2 };
 // Capacity shortfalls detected on the device. A kernel that detects one
 // changes nothing, sets `stall`, and every later kernel returns at once; the
 // host grows the buffer and re-runs the step from the phase named here.
-enum Stall : uint32_t { ST_NONE = 0, ST_WIDTH = 1, ST_HASH = 2, ST_CAND = 3 };
-enum Phase : int { PH_COUNT = 0, PH_PROMOTE = 1, PH_HASH = 2, PH_GEN = 3, PH_FINISH = 4 };
+// ST_HASH: the box set is too full for this stop's insertions (raised by
+// the insert kernel, or by a count kernel that inserts in its epilogue, which
+// then resumes at PH_COUNT: ST_HASH_COUNT).
+enum Stall : uint32_t { ST_NONE = 0, ST_WIDTH = 1, ST_HASH = 2, ST_CAND = 3, ST_HASH_COUNT = 4 };
+enum Phase : int { PH_COUNT = 0, PH_PROMOTE = 1, PH_HASH = 2, PH_GEN = 3 };
 
 constexpr int TRACE_COLS = 9;
 // Ranks kept per candidate record for the BITSLICE count path; itemsets with
@@ -41,7 +44,7 @@ struct Ctrl {
   uint32_t hash_used;  // occupied hash slots
   uint32_t max_k;      // largest itemset size ever placed in DASHED
   uint32_t n_trace;
-  uint32_t pad0;
+  uint32_t blocks_done;  // ticket of the generate kernel's last-block step
   unsigned long long tests;  // candidate-transaction tests so far
 };
 
@@ -57,10 +60,11 @@ struct Lattice {
   uint16_t *cranks;    // [cap][KRMAX] ascending ranks (first KRMAX of them)
   uint32_t *newbox;    // [cap] records promoted at this stop
   uint64_t *newhash;   // [cap] hash pre-image sums of those records
+  uint32_t *cpromo;    // [cap] stop at which a box was promoted
   uint32_t cap;
-  // box set: open addressing, key = mask, value = promotion stop + 1
-  uint64_t *hkeys;     // [hcap][wc]
-  uint32_t *hvals;     // [hcap], 0 = empty
+  // box set: open addressing over record indices (slot = index + 1, 0 =
+  // empty); keys are the records' masks, values their promotion stops
+  uint32_t *hslot;     // [hcap]
   uint32_t hcap;       // power of two
   // cohorts (records created at one stop are contiguous)
   uint32_t *cohort_start;
@@ -100,10 +104,10 @@ cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s);
 cudaError_t launch_count_rows(Lattice L, int nw, int grid, cudaStream_t s);
 cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s);
 cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s);
-cudaError_t launch_generate(Lattice L, int grid, cudaStream_t s);
-cudaError_t launch_finish(Lattice L, cudaStream_t s);
-cudaError_t launch_rehash(Lattice L, const uint64_t *okeys, const uint32_t *ovals, uint32_t ocap,
-                          cudaStream_t s);
+// MAKECANDIDATES followed (in the last block to finish) by the end-of-stop
+// bookkeeping: trace row, cohort, CHECKFULLPASS, loop test.
+cudaError_t launch_generate_finish(Lattice L, int grid, cudaStream_t s);
+cudaError_t launch_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap, cudaStream_t s);
 cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
                                  uint32_t *out_count, cudaStream_t s);
 cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
@@ -111,8 +115,10 @@ cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, ui
 
 // BITSLICE path (kernels_count_bitslice.cu). V holds the stop's block as
 // per-rank bit columns, tile-major: tile t covers rows first+32*TW*t ..,
-// V[(t*l1p + r)*(TW+1) + w] = rows first+32*(TW*t+w) .. +31 of rank r (bit j
-// = row +j); column TW is padding. l1p = l1 rounded up to a multiple of 4.
+// V[(t*l1p + r)*stride + w] = rows first+32*(TW*t+w) .. +31 of rank r (bit
+// j = row +j); stride = TW+4 (TW = 8, 16) or TW (TW = 4), the extra words
+// being padding. l1p = l1 rounded up to a multiple of 4.
+size_t bitslice_tile_words(int tw, uint32_t l1p);
 cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, cudaStream_t s);
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
                                   uint32_t chunk, int grid, cudaStream_t s);

@@ -15,16 +15,26 @@
 //   k_count_bitslice each CTA owns a contiguous chunk of the candidate
 //                    window; it streams the V tiles through a double buffer
 //                    (cp.async) and every thread ANDs and popcounts its
-//                    candidates' columns. Counts stay in shared memory until
-//                    the chunk is done, so every counter is written once.
+//                    candidates' columns with 128-bit shared loads. Counts
+//                    stay in shared memory until the chunk is done; then each
+//                    record's support is written once and PRUNE (Algorithm
+//                    4) is applied to it in the same pass, inserting new
+//                    boxes into the box set.
+//
+// Tile rows are padded to 16-byte multiples (TW+4 words for TW = 8, 16; TW
+// for TW = 4) so that eight threads reading consecutive ranks with 128-bit
+// loads hit distinct banks.
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "dic_internal.cuh"
+#include "lattice_device.cuh"
 
 namespace dic {
 
 constexpr int BS_THREADS = 512;
+
+__host__ __device__ constexpr uint32_t bs_stride(int tw) { return tw == 4 ? 4u : (uint32_t)tw + 4u; }
 
 // ------------------------------------------------------------ transpose
 __global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t *__restrict__ V, int tw,
@@ -58,8 +68,9 @@ __global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t *__rest
     }
     const uint32_t t = w / tw, wi = w % tw;
     const uint32_t r0 = j * 64 + lane, r1 = r0 + 32;
-    if (r0 < l1p) V[((uint64_t)t * l1p + r0) * (tw + 1) + wi] = lo;
-    if (r1 < l1p) V[((uint64_t)t * l1p + r1) * (tw + 1) + wi] = hi;
+    const uint32_t st = bs_stride(tw);
+    if (r0 < l1p) V[((uint64_t)t * l1p + r0) * st + wi] = lo;
+    if (r1 < l1p) V[((uint64_t)t * l1p + r1) * st + wi] = hi;
   }
 }
 
@@ -92,13 +103,15 @@ __device__ __forceinline__ void cp_async_wait_1() {
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
+size_t bitslice_tile_words(int tw, uint32_t l1p) { return (size_t)l1p * bs_stride(tw); }
+
 size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk) {
-  const size_t tile = (size_t)l1p * (tw + 1) * 4;
+  const size_t tile = bitslice_tile_words(tw, l1p) * 4;
   return 2 * tile + (size_t)chunk * (2 * kre + 4 + 1) + 16;
 }
 
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit) {
-  const size_t tile = (size_t)l1p * (tw + 1) * 4;
+  const size_t tile = bitslice_tile_words(tw, l1p) * 4;
   if (2 * tile + 16 >= smem_limit) return 0;
   size_t c = (smem_limit - 2 * tile - 16) / (2 * kre + 4 + 1);
   c &= ~(size_t)3;
@@ -110,38 +123,44 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
                                                                const uint32_t *__restrict__ V,
                                                                uint32_t l1p, uint32_t chunk) {
   extern __shared__ __align__(16) uint32_t sm[];
+  constexpr uint32_t ST = bs_stride(TW);
+  constexpr int NV = TW / 4;  // 128-bit loads per rank and tile
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   if (C->max_k > (uint32_t)KRE) {
     if (blockIdx.x == 0 && threadIdx.x == 0) C->stall = ST_WIDTH;
     return;
   }
-  const uint32_t tile_words = l1p * (TW + 1);
+  // room in the box set for every live record, checked before any change
+  if ((uint64_t)(C->hash_used + C->n_live) * 2 > L.hcap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->stall = ST_HASH_COUNT;
+    return;
+  }
+  const uint32_t tile_words = l1p * ST;
   uint32_t *S0 = sm;
   uint32_t *S1 = sm + tile_words;
   uint16_t *rk = reinterpret_cast<uint16_t *>(sm + 2 * tile_words);
   uint32_t *cnt = reinterpret_cast<uint32_t *>(rk + (size_t)chunk * KRE);
   uint8_t *kk = reinterpret_cast<uint8_t *>(cnt + chunk);
 
+  const uint32_t g = C->step;
   uint32_t stop;
   uint64_t first, last;
-  block_of(C->step, L.stop_max, L.M, L.n, &stop, &first, &last);
+  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
   const uint32_t nw32 = (uint32_t)((last - first + 31) / 32);
   const uint32_t ntiles = (nw32 + TW - 1) / TW;
   const uint32_t head = C->head, tail = C->tail;
   const uint32_t ncand = tail - head;
   const uint32_t nchunks = (ncand + chunk - 1) / chunk;
   const uint32_t tid = threadIdx.x;
+  uint32_t pruned = 0, solid = 0;
 
   for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const uint32_t c0 = head + ch * chunk;
     const uint32_t cn = (tail - c0) < chunk ? (tail - c0) : chunk;
     __syncthreads();  // shared memory of the previous chunk is free
-    {
-      const uint32_t *src = V;
-      for (uint32_t o = tid * 4; o < tile_words; o += BS_THREADS * 4) cp_async16(S0 + o, src + o);
-      cp_async_commit();
-    }
+    for (uint32_t o = tid * 4; o < tile_words; o += BS_THREADS * 4) cp_async16(S0 + o, V + o);
+    cp_async_commit();
     for (uint32_t i = tid; i < cn; i += BS_THREADS) {
       const uint32_t c = c0 + i;
       const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
@@ -165,27 +184,38 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
         const uint32_t k = kk[i];
         if (k == 0) continue;
         const uint16_t *ri = rk + (size_t)i * KRE;
-        uint32_t acc[TW];
+        uint4 acc[NV];
         {
-          const uint32_t *p = S + (uint32_t)ri[0] * (TW + 1);
+          const uint4 *p = reinterpret_cast<const uint4 *>(S + (uint32_t)ri[0] * ST);
 #pragma unroll
-          for (int w = 0; w < TW; ++w) acc[w] = p[w];
+          for (int v = 0; v < NV; ++v) acc[v] = p[v];
         }
         for (uint32_t q = 1; q < k; ++q) {
-          const uint32_t *p = S + (uint32_t)ri[q] * (TW + 1);
+          const uint4 *p = reinterpret_cast<const uint4 *>(S + (uint32_t)ri[q] * ST);
 #pragma unroll
-          for (int w = 0; w < TW; ++w) acc[w] &= p[w];
+          for (int v = 0; v < NV; ++v) {
+            const uint4 x = p[v];
+            acc[v].x &= x.x; acc[v].y &= x.y; acc[v].z &= x.z; acc[v].w &= x.w;
+          }
         }
         uint32_t sum = 0;
 #pragma unroll
-        for (int w = 0; w < TW; ++w) sum += __popc(acc[w]);
+        for (int v = 0; v < NV; ++v)
+          sum += __popc(acc[v].x) + __popc(acc[v].y) + __popc(acc[v].z) + __popc(acc[v].w);
         cnt[i] += sum;
       }
       __syncthreads();  // the buffer of tile t may be overwritten next
     }
-    for (uint32_t i = tid; i < cn; i += BS_THREADS)
-      if (kk[i] && cnt[i]) L.csupp[c0 + i] += cnt[i];
+    for (uint32_t i = tid; i < cn; i += BS_THREADS) {
+      if (!kk[i]) continue;
+      const uint32_t c = c0 + i;
+      const uint32_t s = L.csupp[c] + cnt[i];
+      L.csupp[c] = s;
+      settle_record(L, C, c, s, g, true, pruned, solid);
+    }
   }
+  if (pruned) atomicAdd(&C->n_pruned, pruned);
+  if (solid) atomicAdd(&C->n_solid, solid);
 }
 
 template <int TW, int KRE>

@@ -12,24 +12,9 @@
 #include <cuda_runtime.h>
 
 #include "dic_internal.cuh"
+#include "lattice_device.cuh"
 
 namespace dic {
-
-// ------------------------------------------------------------- hashing
-// Hash of a mask = final mix of the sum over words of hterm(word, index).
-// The sum form lets MAKECANDIDATES derive the hash of C \ {j} from that of
-// the parent in O(1).
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t hterm(uint64_t w, uint32_t i) {
-  return mix64(w + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1));
-}
-__device__ __forceinline__ uint32_t hslot(uint64_t sum, uint32_t hcap) {
-  return (uint32_t)(mix64(sum ^ 0x5851F42D4C957F2Dull) & (uint64_t)(hcap - 1));
-}
 
 // --------------------------------------------------------- first pass
 // supp1[i] = number of rows with bit i set, over all n rows (FIRSTPASS of
@@ -224,41 +209,20 @@ cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s) {
 }
 
 // --------------------------------------------------------------- PRUNE
-// Algorithm 4 over the dashed circles after the count of stop g:
-//   supp >= minsup                      -> BOX (promotion recorded)
-//   supp + M * (stop_max - stop) < minsup -> NIL (erased)
-// with stop = g - birth (the number of blocks this record has been counted
-// over). Records whose stop reaches stop_max are tallied as solidified
-// (Algorithm 5); at that point every live record is a box, since a circle
-// there has the bound supp + 0 < minsup and was erased just above.
-// The superset loop of Algorithm 4 is not run: every (k-1)-subset of a
-// record is a box when it is generated and boxes never change shape, so a
-// dashed circle has no dashed superset and the loop can only match itself.
+// Algorithm 4 over the dashed records after the count of stop g (the ROWS
+// path; the fast count paths apply the same rule in their epilogue). The
+// superset loop of Algorithm 4 is not run: every (k-1)-subset of a record is
+// a box when it is generated and boxes never change shape, so a dashed
+// circle has no dashed superset and the loop could only match the record
+// itself.
 __global__ void __launch_bounds__(256) k_promote(Lattice L) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   const uint32_t g = C->step, head = C->head, tail = C->tail;
   uint32_t pruned = 0, solid = 0;
   for (uint32_t c = head + blockIdx.x * blockDim.x + threadIdx.x; c < tail;
-       c += gridDim.x * blockDim.x) {
-    uint8_t sh = L.cshape[c];
-    if (sh == SH_NIL) continue;
-    const uint32_t age = g - L.cbirth[c];
-    if (sh == SH_CIRCLE) {
-      const uint32_t s = L.csupp[c];
-      if (s >= L.minsup) {
-        L.cshape[c] = SH_BOX;
-        sh = SH_BOX;
-        const uint32_t at = atomicAdd(&C->n_newbox, 1u);
-        L.newbox[at] = c;
-      } else if ((uint64_t)s + L.M * (uint64_t)(L.stop_max - age) < (uint64_t)L.minsup) {
-        L.cshape[c] = SH_NIL;
-        ++pruned;
-        continue;
-      }
-    }
-    if (age == L.stop_max) ++solid;
-  }
+       c += gridDim.x * blockDim.x)
+    settle_record(L, C, c, L.csupp[c], g, false, pruned, solid);
   if (pruned) atomicAdd(&C->n_pruned, pruned);
   if (solid) atomicAdd(&C->n_solid, solid);
 }
@@ -269,11 +233,9 @@ cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s) {
 }
 
 // -------------------------------------------------------------- box set
-// Insert the masks promoted at stop g (value g+1). Keys inserted by one
-// launch are distinct and absent (a record is promoted once), so a thread
-// that loses a slot simply probes on. The load check runs before any insert
-// and reads only values this kernel does not change, so every block takes
-// the same decision.
+// Insert the records promoted at this stop (ROWS path). The load check runs
+// before any insert and reads only values this kernel does not change, so
+// every block takes the same decision.
 __global__ void __launch_bounds__(256) k_hash_insert(Lattice L) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
@@ -282,20 +244,11 @@ __global__ void __launch_bounds__(256) k_hash_insert(Lattice L) {
     if (blockIdx.x == 0 && threadIdx.x == 0) C->stall = ST_HASH;
     return;
   }
-  const uint32_t g = C->step;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    const uint64_t *key = L.cmask + (uint64_t)L.newbox[p] * L.wc;
-    uint64_t sum = 0;
-    for (uint32_t i = 0; i < L.wc; ++i) sum += hterm(key[i], i);
+    const uint32_t c = L.newbox[p];
+    const uint64_t sum = mask_hash_sum(L.cmask + (uint64_t)c * L.wc, L.wc);
     L.newhash[p] = sum;
-    uint32_t slot = hslot(sum, L.hcap);
-    for (uint32_t probe = 0; probe < L.hcap; ++probe) {
-      if (atomicCAS(&L.hvals[slot], 0u, g + 1) == 0u) {
-        for (uint32_t i = 0; i < L.wc; ++i) L.hkeys[(uint64_t)slot * L.wc + i] = key[i];
-        break;
-      }
-      slot = (slot + 1) & (L.hcap - 1);
-    }
+    box_insert(L, c, sum);
   }
 }
 
@@ -304,30 +257,19 @@ cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Rebuild the box set into a larger table (after an ST_HASH stall).
-__global__ void k_rehash(Lattice L, const uint64_t *okeys, const uint32_t *ovals, uint32_t ocap) {
+// Rebuild the box set into a larger table.
+__global__ void k_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap) {
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ocap; s += gridDim.x * blockDim.x) {
-    const uint32_t v = ovals[s];
+    const uint32_t v = oslot[s];
     if (!v) continue;
-    const uint64_t *key = okeys + (uint64_t)s * L.wc;
-    uint64_t sum = 0;
-    for (uint32_t i = 0; i < L.wc; ++i) sum += hterm(key[i], i);
-    uint32_t slot = hslot(sum, L.hcap);
-    for (uint32_t probe = 0; probe < L.hcap; ++probe) {
-      if (atomicCAS(&L.hvals[slot], 0u, v) == 0u) {
-        for (uint32_t i = 0; i < L.wc; ++i) L.hkeys[(uint64_t)slot * L.wc + i] = key[i];
-        break;
-      }
-      slot = (slot + 1) & (L.hcap - 1);
-    }
+    box_insert(L, v - 1, mask_hash_sum(L.cmask + (uint64_t)(v - 1) * L.wc, L.wc));
   }
 }
 
-cudaError_t launch_rehash(Lattice L, const uint64_t *okeys, const uint32_t *ovals, uint32_t ocap,
-                          cudaStream_t s) {
+cudaError_t launch_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap, cudaStream_t s) {
   if (ocap == 0) return cudaSuccess;
   int grid = (int)((ocap + 255) / 256 < 65535u * 4 ? (ocap + 255) / 256 : 65535u * 4);
-  k_rehash<<<grid, 256, 0, s>>>(L, okeys, ovals, ocap);
+  k_rehash<<<grid, 256, 0, s>>>(L, oslot, ocap);
   return cudaGetLastError();
 }
 
@@ -337,33 +279,47 @@ cudaError_t launch_rehash(Lattice L, const uint64_t *okeys, const uint32_t *oval
 // C has one or more promoted-at-g parents C \ {j}; only the parent with the
 // smallest j emits it, so every C appears exactly once without a dedup
 // table: thread (A, r) emits iff no j < r in A has C \ {j} promoted at g.
-// (A subset promoted at g carries value g+1; older boxes carry less.)
-__device__ __forceinline__ uint32_t box_lookup(const Lattice &L, const uint64_t *A, uint32_t wr,
-                                               uint64_t br, uint32_t wj, uint64_t bj,
-                                               uint64_t sum) {
-  uint32_t slot = hslot(sum, L.hcap);
-  for (uint32_t probe = 0; probe < L.hcap; ++probe) {
-    const uint32_t v = L.hvals[slot];
-    if (v == 0) return 0;
-    const uint64_t *key = L.hkeys + (uint64_t)slot * L.wc;
-    bool eq = true;
-    for (uint32_t i = 0; i < L.wc && eq; ++i) {
-      uint64_t s = A[i];
-      if (i == wr) s |= br;
-      if (i == wj) s &= ~bj;
-      eq = key[i] == s;
-    }
-    if (eq) return v;
-    slot = (slot + 1) & (L.hcap - 1);
+//
+// The last block to finish then closes the stop: trace row, test count,
+// the new cohort, CHECKFULLPASS (cohorts whose full pass is complete leave
+// the window [head, tail)), |DASHED| and the loop test of Algorithm 2.
+__device__ void finish_stop(const Lattice &L, Ctrl *C) {
+  const uint32_t g = C->step;
+  uint32_t stop;
+  uint64_t first, last;
+  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
+  if (C->n_trace >= L.tcap) {
+    C->error = 4;  // DIC_ECAPACITY
+    C->done = 1;
+    return;
   }
-  return 0;
+  unsigned long long *row = L.trace + (uint64_t)C->n_trace * TRACE_COLS;
+  row[0] = g; row[1] = stop; row[2] = first; row[3] = last;
+  row[4] = C->n_live; row[5] = C->n_newbox; row[6] = C->n_pruned; row[7] = C->n_gen;
+  row[8] = C->n_solid;
+  C->tests += (unsigned long long)C->n_live * (last - first);
+  if (C->n_gen) {
+    L.cohort_start[C->n_cohorts] = C->tail;
+    L.cohort_birth[C->n_cohorts] = g;
+    C->n_cohorts += 1;
+  }
+  C->tail += C->n_gen;
+  C->hash_used += C->n_newbox;
+  C->n_live = C->n_live - C->n_pruned - C->n_solid + C->n_gen;
+  uint32_t ch = C->cohort_head;
+  while (ch < C->n_cohorts && L.cohort_birth[ch] + L.stop_max <= g) ++ch;
+  C->cohort_head = ch;
+  C->head = ch < C->n_cohorts ? L.cohort_start[ch] : C->tail;
+  C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->n_gen = 0;
+  C->n_trace += 1;
+  C->step = g + 1;
+  if (C->n_live == 0) C->done = 1;
 }
 
-__global__ void __launch_bounds__(256) k_generate(Lattice L) {
+__global__ void __launch_bounds__(256) k_generate_finish(Lattice L) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   const uint32_t P = C->n_newbox;
-  if (P == 0) return;
   const uint32_t g = C->step, base = C->tail, l1 = L.l1, wc = L.wc;
   const uint64_t total = (uint64_t)P * l1;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -410,54 +366,23 @@ __global__ void __launch_bounds__(256) k_generate(Lattice L) {
     L.ck[pos] = (uint8_t)(k + 1 < 255 ? k + 1 : 255);
     atomicMax(&C->max_k, k + 1);
   }
-}
-
-cudaError_t launch_generate(Lattice L, int grid, cudaStream_t s) {
-  k_generate<<<grid, 256, 0, s>>>(L);
-  return cudaGetLastError();
-}
-
-// -------------------------------------------------------- stop bookkeeping
-// End of stop g: trace row, test count, the new cohort, CHECKFULLPASS
-// (cohorts whose full pass is complete leave the window), |DASHED| and the
-// loop condition of Algorithm 2.
-__global__ void k_finish(Lattice L) {
-  Ctrl *C = L.ctrl;
-  if (C->stall || C->done) return;
-  const uint32_t g = C->step;
-  uint32_t stop;
-  uint64_t first, last;
-  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
-  if (C->n_trace >= L.tcap) {
-    C->error = 4;  // DIC_ECAPACITY
-    C->done = 1;
-    return;
+  // last block closes the stop
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&C->blocks_done, 1u) == gridDim.x - 1;
   }
-  unsigned long long *row = L.trace + (uint64_t)C->n_trace * TRACE_COLS;
-  row[0] = g; row[1] = stop; row[2] = first; row[3] = last;
-  row[4] = C->n_live; row[5] = C->n_newbox; row[6] = C->n_pruned; row[7] = C->n_gen;
-  row[8] = C->n_solid;
-  C->tests += (unsigned long long)C->n_live * (last - first);
-  if (C->n_gen) {
-    L.cohort_start[C->n_cohorts] = C->tail;
-    L.cohort_birth[C->n_cohorts] = g;
-    C->n_cohorts += 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    C->blocks_done = 0;
+    if (!C->stall) finish_stop(L, C);
   }
-  C->tail += C->n_gen;
-  C->hash_used += C->n_newbox;
-  C->n_live = C->n_live - C->n_pruned - C->n_solid + C->n_gen;
-  uint32_t ch = C->cohort_head;
-  while (ch < C->n_cohorts && L.cohort_birth[ch] + L.stop_max <= g) ++ch;
-  C->cohort_head = ch;
-  C->head = ch < C->n_cohorts ? L.cohort_start[ch] : C->tail;
-  C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->n_gen = 0;
-  C->n_trace += 1;
-  C->step = g + 1;
-  if (C->n_live == 0) C->done = 1;
 }
 
-cudaError_t launch_finish(Lattice L, cudaStream_t s) {
-  k_finish<<<1, 1, 0, s>>>(L);
+cudaError_t launch_generate_finish(Lattice L, int grid, cudaStream_t s) {
+  k_generate_finish<<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 

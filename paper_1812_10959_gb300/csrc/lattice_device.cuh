@@ -1,0 +1,103 @@
+// Device-side helpers of the lattice shared by the count and lattice kernels:
+// the box set (open addressing over candidate indices) and the PRUNE /
+// promotion rule of Algorithm 4 applied to one record.
+#pragma once
+#include <cstdint>
+
+#include "dic_internal.cuh"
+
+namespace dic {
+
+// Hash of a mask = final mix of the sum over words of hterm(word, index).
+// The sum form lets MAKECANDIDATES derive the hash of C \ {j} from that of
+// the parent in O(1).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t hterm(uint64_t w, uint32_t i) {
+  return mix64(w + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1));
+}
+__device__ __forceinline__ uint32_t hslot_of(uint64_t sum, uint32_t hcap) {
+  return (uint32_t)(mix64(sum ^ 0x5851F42D4C957F2Dull) & (uint64_t)(hcap - 1));
+}
+__device__ __forceinline__ uint64_t mask_hash_sum(const uint64_t *key, uint32_t wc) {
+  uint64_t sum = 0;
+  for (uint32_t i = 0; i < wc; ++i) sum += hterm(key[i], i);
+  return sum;
+}
+
+// Insert record c (a box) into the box set. Records are inserted once, so a
+// thread that finds a slot taken probes on; callers guarantee a load factor
+// <= 1/2, so a free slot exists.
+__device__ __forceinline__ void box_insert(const Lattice &L, uint32_t c, uint64_t sum) {
+  uint32_t slot = hslot_of(sum, L.hcap);
+  for (uint32_t probe = 0; probe < L.hcap; ++probe) {
+    if (atomicCAS(&L.hslot[slot], 0u, c + 1) == 0u) return;
+    slot = (slot + 1) & (L.hcap - 1);
+  }
+}
+
+// The box whose mask is A | br (in word wr) with bit bj of word wj cleared,
+// or 0 if absent; otherwise its promotion stop + 1.
+__device__ __forceinline__ uint32_t box_lookup(const Lattice &L, const uint64_t *A, uint32_t wr,
+                                               uint64_t br, uint32_t wj, uint64_t bj,
+                                               uint64_t sum) {
+  uint32_t slot = hslot_of(sum, L.hcap);
+  for (uint32_t probe = 0; probe < L.hcap; ++probe) {
+    const uint32_t v = L.hslot[slot];
+    if (v == 0) return 0;
+    const uint64_t *key = L.cmask + (uint64_t)(v - 1) * L.wc;
+    bool eq = true;
+    for (uint32_t i = 0; i < L.wc && eq; ++i) {
+      uint64_t s = A[i];
+      if (i == wr) s |= br;
+      if (i == wj) s &= ~bj;
+      eq = key[i] == s;
+    }
+    if (eq) return L.cpromo[v - 1] + 1;
+    slot = (slot + 1) & (L.hcap - 1);
+  }
+  return 0;
+}
+
+// Record a promotion of record c at stop g: shape, promotion stop, the list
+// MAKECANDIDATES reads, and (when `insert`) the box set.
+__device__ __forceinline__ void promote_record(const Lattice &L, Ctrl *C, uint32_t c, uint32_t g,
+                                               bool insert) {
+  L.cshape[c] = SH_BOX;
+  L.cpromo[c] = g;
+  const uint32_t at = atomicAdd(&C->n_newbox, 1u);
+  L.newbox[at] = c;
+  if (insert) {
+    const uint64_t sum = mask_hash_sum(L.cmask + (uint64_t)c * L.wc, L.wc);
+    L.newhash[at] = sum;
+    box_insert(L, c, sum);
+  }
+}
+
+// Algorithm 4 for one dashed record after its count at stop g, given its
+// new support s: a circle with s >= minsup becomes a box; a circle whose
+// bound s + M * (stop_max - stop) is below minsup is erased (stop = g -
+// birth, the blocks counted so far). Tallies records completing their full
+// pass (every live one is a box there). Returns nothing; updates tallies.
+__device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_t c, uint32_t s,
+                                              uint32_t g, bool insert, uint32_t &pruned,
+                                              uint32_t &solid) {
+  uint8_t sh = L.cshape[c];
+  if (sh == SH_NIL) return;
+  const uint32_t age = g - L.cbirth[c];
+  if (sh == SH_CIRCLE) {
+    if (s >= L.minsup) {
+      promote_record(L, C, c, g, insert);
+    } else if ((uint64_t)s + L.M * (uint64_t)(L.stop_max - age) < (uint64_t)L.minsup) {
+      L.cshape[c] = SH_NIL;
+      ++pruned;
+      return;
+    }
+  }
+  if (age == L.stop_max) ++solid;
+}
+
+}  // namespace dic

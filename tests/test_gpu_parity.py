@@ -159,17 +159,41 @@ def test_repeatable_and_M_invariant(dic):
 
 
 def test_paths_agree_on_wide_frequent_items(dic):
-    """Many frequent items (l1 ~ 2,000 in 4,096): bitslice picks a narrow tile;
-    every path gives the oracle's result."""
+    """~1,600 frequent items out of 4,096 (the bitslice path then uses a
+    narrower tile). All paths agree; the oracle pins the 1- and 2-itemsets
+    exactly (pair co-occurrence counts, including the infrequent pairs) and
+    the supports of every larger itemset."""
     rng = np.random.default_rng(77)
-    n, m = 3000, 4096
-    hot = rng.choice(m, 2100, replace=False)
-    rows = [np.concatenate([rng.choice(hot, 60, replace=False),
-                            rng.integers(0, m, 5)]).tolist() for _ in range(n)]
+    n, m, minsup = 2000, 4096, 60
+    hot = rng.choice(m, 1600, replace=False)
+    pats = [rng.choice(hot, 5, replace=False) for _ in range(3)]
+    rows = []
+    for t in range(n):
+        r = rng.choice(hot, 80, replace=False).tolist() + rng.integers(0, m, 5).tolist()
+        for p in pats:
+            if rng.random() < 0.06:
+                r += p.tolist()
+        rows.append(r)
     rp, it = to_csr(rows)
-    out = {}
-    for path in ("rows", "bitslice", "auto"):
-        res, ref = check(dic, rp, it, n, m, 45, 1100, path)
-        out[path] = res.itemsets()
-        assert res.stats["l1"] > 1500
-    assert out["rows"] == out["bitslice"] == out["auto"]
+    db = dic.load_db_csr(rp, it, n, m)
+    out = {path: dic.mine(db, minsup, 700, path=path) for path in ("rows", "bitslice", "auto")}
+    db.free()
+    got = out["rows"].itemsets()
+    assert got == out["bitslice"].itemsets() == out["auto"].itemsets()
+    assert out["bitslice"].stats["l1"] > 1430
+    assert out["bitslice"].stats["path_launches"][2] > 0
+    P = oracle.pair_supports(rp, it, n, m)
+    d = np.diag(P)
+    exp1 = [((i,), int(d[i])) for i in range(m) if d[i] >= minsup]
+    iu = np.argwhere(np.triu(P, 1) >= minsup)
+    exp2 = sorted(((int(a), int(b)), int(P[a, b])) for a, b in iu)
+    assert [x for x in got if len(x[0]) == 1] == exp1
+    assert [x for x in got if len(x[0]) == 2] == exp2
+    big = [x for x in got if len(x[0]) >= 3]
+    assert big, "the planted patterns give itemsets of size >= 3"
+    sup = oracle.support(rp, it, n, m, [s for s, _ in big])
+    assert [int(v) for v in sup] == [v for _, v in big]
+    gd = dict(got)
+    for X, _ in big:
+        for j in range(len(X)):
+            assert X[:j] + X[j + 1:] in gd
