@@ -305,6 +305,7 @@ class Miner {
   int bs_tw_ = 16;         // 32-row words per tile
   uint32_t bs_l1p_ = 0;    // l1 rounded up to a multiple of 4
   uint32_t *bs_V_ = nullptr;
+  uint64_t bs_V_words_ = 0;
   int bs_grid_ = 0;
   size_t smem_optin_ = 0;
   int cur_path_ = DIC_COUNT_ROWS;
@@ -370,14 +371,14 @@ dic_status Miner::launch_phase(int phase) {
         uint32_t chunk = (win + bs_grid_ - 1) / bs_grid_;
         chunk = std::max<uint32_t>(256, (chunk + 3) & ~3u);
         chunk = std::min(chunk, bitslice_max_chunk(bs_tw_, kre, bs_l1p_, smem_optin_));
-        e = launch_slice_block(L_, bs_V_, bs_tw_, bs_l1p_, s_);
+        e = launch_slice_block(L_, bs_V_, bs_tw_, bs_l1p_, bs_V_words_, s_);
         ++launches_;
         if (e == cudaSuccess) {
           if (opt_.profile) {
             TRY(next_event(&a));
             CU(cudaEventRecord(a, s_));
           }
-          e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_grid_, s_);
+          e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_, bs_grid_, s_);
         }
         path_launches_[DIC_COUNT_BITSLICE]++;
       } else {
@@ -482,6 +483,13 @@ dic_status Miner::grow_trace(uint32_t need) {
   drop(L_.trace); drop(L_.cohort_start); drop(L_.cohort_birth);
   L_ = N;
   return DIC_OK;
+}
+
+static dic_status device_error(uint32_t code) {
+  if (code == DIC_INTERNAL_BOUNDS)
+    return fail(DIC_ECUDA, "internal error: a kernel's bounds check caught an index outside its buffer");
+  if (code == DIC_ECAPACITY) return fail(DIC_ECAPACITY, "trace capacity exceeded");
+  return fail((dic_status)code, "device reported status %u", code);
 }
 
 static bool canon_less(const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) {
@@ -623,7 +631,8 @@ dic_status Miner::run(dic_result **out) {
       if (bs_ok_) {
         const uint64_t blockmax = std::min<uint64_t>(M_, n);
         const uint64_t ntiles = ((blockmax + 31) / 32 + bs_tw_ - 1) / bs_tw_;
-        TRY(alloc(&bs_V_, (size_t)ntiles * bs_l1p_ * (bs_tw_ + 1)));
+        bs_V_words_ = (uint64_t)ntiles * bitslice_tile_words(bs_tw_, bs_l1p_);
+        TRY(alloc(&bs_V_, bs_V_words_));
         bs_grid_ = sm_count();
       }
     }
@@ -640,8 +649,7 @@ dic_status Miner::run(dic_result **out) {
       cur_path_ = count_path_for_stop();
       for (uint32_t i = 0; i < chunk; ++i) TRY(launch_stop_from(PH_COUNT));
       TRY(sync_ctrl());
-      if (h_ctrl_->error)
-        return fail((dic_status)h_ctrl_->error, "device reported status %u", h_ctrl_->error);
+      if (h_ctrl_->error) return device_error(h_ctrl_->error);
       while (h_ctrl_->stall) {
         const uint32_t st = h_ctrl_->stall;
         int phase = PH_COUNT;
@@ -665,8 +673,7 @@ dic_status Miner::run(dic_result **out) {
         CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
         TRY(launch_stop_from(phase));
         TRY(sync_ctrl());
-        if (h_ctrl_->error)
-          return fail((dic_status)h_ctrl_->error, "device reported status %u", h_ctrl_->error);
+        if (h_ctrl_->error) return device_error(h_ctrl_->error);
       }
       if (h_ctrl_->done) break;
       chunk = std::min(chunk * 2, chunk_max);

@@ -21,6 +21,9 @@ enum Stall : uint32_t { ST_NONE = 0, ST_WIDTH = 1, ST_HASH = 2, ST_CAND = 3, ST_
 enum Phase : int { PH_COUNT = 0, PH_PROMOTE = 1, PH_HASH = 2, PH_GEN = 3 };
 
 constexpr int TRACE_COLS = 9;
+// Ctrl.error value recorded by a kernel whose own bounds check caught an
+// index outside a buffer (an internal sizing error); the access is skipped.
+constexpr uint32_t DIC_INTERNAL_BOUNDS = 100;
 // Ranks kept per candidate record for the BITSLICE count path; itemsets with
 // more items are counted by the ROWS path.
 constexpr int KRMAX = 16;
@@ -119,9 +122,10 @@ cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, ui
 // j = row +j); stride = TW+4 (TW = 8, 16) or TW (TW = 4), the extra words
 // being padding. l1p = l1 rounded up to a multiple of 4.
 size_t bitslice_tile_words(int tw, uint32_t l1p);
-cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, cudaStream_t s);
+cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, uint64_t vwords,
+                               cudaStream_t s);
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
-                                  uint32_t chunk, int grid, cudaStream_t s);
+                                  uint32_t chunk, uint64_t vwords, int grid, cudaStream_t s);
 // Largest candidate chunk whose bitslice shared-memory footprint fits.
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit);
 size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk);

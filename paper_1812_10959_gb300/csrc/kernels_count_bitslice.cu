@@ -38,7 +38,7 @@ __host__ __device__ constexpr uint32_t bs_stride(int tw) { return tw == 4 ? 4u :
 
 // ------------------------------------------------------------ transpose
 __global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t *__restrict__ V, int tw,
-                                                     uint32_t l1p) {
+                                                     uint32_t l1p, uint64_t vwords) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   uint32_t stop;
@@ -69,12 +69,18 @@ __global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t *__rest
     const uint32_t t = w / tw, wi = w % tw;
     const uint32_t r0 = j * 64 + lane, r1 = r0 + 32;
     const uint32_t st = bs_stride(tw);
-    if (r0 < l1p) V[((uint64_t)t * l1p + r0) * st + wi] = lo;
-    if (r1 < l1p) V[((uint64_t)t * l1p + r1) * st + wi] = hi;
+    const uint64_t i0 = ((uint64_t)t * l1p + r0) * st + wi, i1 = ((uint64_t)t * l1p + r1) * st + wi;
+    if (i0 >= vwords || (r1 < l1p && i1 >= vwords)) {  // internal sizing error: record, skip
+      C->error = DIC_INTERNAL_BOUNDS;
+      continue;
+    }
+    if (r0 < l1p) V[i0] = lo;
+    if (r1 < l1p) V[i1] = hi;
   }
 }
 
-cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, cudaStream_t s) {
+cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, uint64_t vwords,
+                               cudaStream_t s) {
   const uint64_t blockmax = L.M < L.n ? L.M : L.n;
   const uint64_t nw32 = (blockmax + 31) / 32;
   const uint64_t items = ((nw32 + tw - 1) / tw) * tw * L.wc;
@@ -84,7 +90,7 @@ cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, cud
   uint64_t want = (items + 7) / 8;
   int grid = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
   if (grid < 1) grid = 1;
-  k_slice_block<<<grid, 256, 0, s>>>(L, V, tw, l1p);
+  k_slice_block<<<grid, 256, 0, s>>>(L, V, tw, l1p, vwords);
   return cudaGetLastError();
 }
 
@@ -121,7 +127,8 @@ uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit) {
 template <int TW, int KRE>
 __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
                                                                const uint32_t *__restrict__ V,
-                                                               uint32_t l1p, uint32_t chunk) {
+                                                               uint32_t l1p, uint32_t chunk,
+                                                               uint64_t vwords) {
   extern __shared__ __align__(16) uint32_t sm[];
   constexpr uint32_t ST = bs_stride(TW);
   constexpr int NV = TW / 4;  // 128-bit loads per rank and tile
@@ -149,6 +156,10 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
   const uint32_t nw32 = (uint32_t)((last - first + 31) / 32);
   const uint32_t ntiles = (nw32 + TW - 1) / TW;
+  if ((uint64_t)ntiles * tile_words > vwords) {  // internal sizing error: record, skip
+    if (threadIdx.x == 0) C->error = DIC_INTERNAL_BOUNDS;
+    return;
+  }
   const uint32_t head = C->head, tail = C->tail;
   const uint32_t ncand = tail - head;
   const uint32_t nchunks = (ncand + chunk - 1) / chunk;
@@ -219,33 +230,35 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
 }
 
 template <int TW, int KRE>
-static cudaError_t go(Lattice L, const uint32_t *V, uint32_t l1p, uint32_t chunk, int grid,
-                      cudaStream_t s) {
+static cudaError_t go(Lattice L, const uint32_t *V, uint32_t l1p, uint32_t chunk, uint64_t vw,
+                      int grid, cudaStream_t s) {
   const size_t smem = bitslice_smem(TW, KRE, l1p, chunk);
   cudaError_t e = cudaFuncSetAttribute(k_count_bitslice<TW, KRE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_count_bitslice<TW, KRE><<<grid, BS_THREADS, smem, s>>>(L, V, l1p, chunk);
+  k_count_bitslice<TW, KRE><<<grid, BS_THREADS, smem, s>>>(L, V, l1p, chunk, vw);
   return cudaGetLastError();
 }
 
 template <int TW>
 static cudaError_t go_k(Lattice L, const uint32_t *V, int kre, uint32_t l1p, uint32_t chunk,
-                        int grid, cudaStream_t s) {
+                        uint64_t vw, int grid, cudaStream_t s) {
   switch (kre) {
-    case 2: return go<TW, 2>(L, V, l1p, chunk, grid, s);
-    case 4: return go<TW, 4>(L, V, l1p, chunk, grid, s);
-    case 8: return go<TW, 8>(L, V, l1p, chunk, grid, s);
-    default: return go<TW, 16>(L, V, l1p, chunk, grid, s);
+    case 2: return go<TW, 2>(L, V, l1p, chunk, vw, grid, s);
+    case 4: return go<TW, 4>(L, V, l1p, chunk, vw, grid, s);
+    case 8: return go<TW, 8>(L, V, l1p, chunk, vw, grid, s);
+    default: return go<TW, 16>(L, V, l1p, chunk, vw, grid, s);
   }
 }
 
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
-                                  uint32_t chunk, int grid, cudaStream_t s) {
+                                  uint32_t chunk, uint64_t vwords, int grid, cudaStream_t s) {
+  if (tw != 16 && tw != 8 && tw != 4) return cudaErrorInvalidValue;
+  if (bitslice_tile_words(tw, l1p) % 4) return cudaErrorInvalidValue;
   switch (tw) {
-    case 16: return go_k<16>(L, V, kre, l1p, chunk, grid, s);
-    case 8: return go_k<8>(L, V, kre, l1p, chunk, grid, s);
-    default: return go_k<4>(L, V, kre, l1p, chunk, grid, s);
+    case 16: return go_k<16>(L, V, kre, l1p, chunk, vwords, grid, s);
+    case 8: return go_k<8>(L, V, kre, l1p, chunk, vwords, grid, s);
+    default: return go_k<4>(L, V, kre, l1p, chunk, vwords, grid, s);
   }
 }
 

@@ -197,3 +197,13 @@ def test_paths_agree_on_wide_frequent_items(dic):
     for X, _ in big:
         for j in range(len(X)):
             assert X[:j] + X[j + 1:] in gd
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_growth_inside_the_first_group_of_stops(dic, path):
+    """The candidate store overflows and the box set grows within the first
+    stops enqueued together (and the window outgrows the first tile)."""
+    rp, it = synth.planted(seed=5, n=3000, m=70, n_patterns=60, pat_len_mean=4.0,
+                           tx_len_mean=9.0)
+    res, ref = check(dic, rp, it, 3000, 70, 60, 700, path)
+    assert len(res.itemsets()) == 1693
