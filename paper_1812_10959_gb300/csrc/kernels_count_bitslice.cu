@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t *__rest
     const uint32_t r0 = j * 64 + lane, r1 = r0 + 32;
     const uint32_t st = bs_stride(tw);
     const uint64_t i0 = ((uint64_t)t * l1p + r0) * st + wi, i1 = ((uint64_t)t * l1p + r1) * st + wi;
-    if (i0 >= vwords || (r1 < l1p && i1 >= vwords)) {  // internal sizing error: record, skip
+    if ((r0 < l1p && i0 >= vwords) || (r1 < l1p && i1 >= vwords)) {  // internal sizing error
       C->error = DIC_INTERNAL_BOUNDS;
       continue;
     }
