@@ -184,6 +184,38 @@ dic_status dic_result_trace(const dic_result *r, uint64_t *rows);
 dic_status dic_result_stats(const dic_result *r, dic_stats *out);
 void dic_result_free(dic_result *r);
 
+/* ------------------------------------------------ allocation-free count */
+
+/* Size of the scratch array of dic_count_support_noalloc, in 32-bit words
+ * (4 MiB), and the largest item count it accepts. */
+#define DIC_NOALLOC_SCRATCH_WORDS (1u << 20)
+#define DIC_NOALLOC_MAX_ITEMS 4096u
+
+/* Support counting for callers that must not allocate device memory (code
+ * running under a fixed, pre-reserved memory budget, threads that may not
+ * enter the CUDA allocator, runtimes that own all device memory). The paper
+ * has no counterpart: it is a service of this library, not a step of DIC.
+ *
+ * supp[c] = number of rows t in [0, n) of dev_words (device bitmaps, n*W
+ * words row-major, W = ceil(m/64), the dic_load_db layout) such that
+ * (row_t AND masks[c]) == masks[c], for c < ncand; masks is a DEVICE array
+ * of ncand*W words, supp a DEVICE array of ncand counters (cleared, then
+ * written). All work is enqueued on `stream` (NULL = legacy default stream);
+ * the call returns before it completes.
+ *
+ * Calls no cudaMalloc/cudaFree and no allocating library routine: its only
+ * working memory is one file-scope device array of
+ * DIC_NOALLOC_SCRATCH_WORDS words that every device which loads the library
+ * holds until the process exits. The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture on the device. All calls share the array: calls whose
+ * GPU work overlaps (other streams or threads on the same device) race and
+ * return wrong counts, so order them on one stream.
+ * DIC_EINVAL: m == 0, m > DIC_NOALLOC_MAX_ITEMS, n >= 2^31, a NULL buffer. */
+dic_status dic_count_support_noalloc(const uint64_t *dev_words, uint64_t n, uint32_t m,
+                                     const uint64_t *dev_masks, uint32_t ncand,
+                                     uint32_t *dev_supp, void *stream);
+
 /* ---------------------------------------------------------------- misc */
 
 /* ceil(frac * n) as an integer support count, at least 1 (the fraction of

@@ -38,6 +38,8 @@ static dic_status fail(dic_status s, const char *fmt, ...) {
   return s;
 }
 
+void dic::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 #define CU(call)                                                                        \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \

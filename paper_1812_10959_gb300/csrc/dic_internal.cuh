@@ -94,6 +94,9 @@ __host__ __device__ inline void block_of(uint32_t g, uint32_t stop_max, uint64_t
   *last = l < n ? l : n;
 }
 
+// Set the thread-local text returned by dic_last_error().
+void set_last_error(const char *msg);
+
 // ---- kernel launchers (kernels_*.cu) ----
 cudaError_t launch_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_t m,
                               uint32_t *cnt, cudaStream_t s);
