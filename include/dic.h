@@ -98,7 +98,10 @@ typedef struct {
   double firstpass_ms;      /* first-pass kernel time (profile=1 only)     */
   double mine_ms;           /* wall time of the mining call (host clock)   */
   uint32_t path_launches[4];/* count launches per dic_count_path           */
-  uint32_t reserved[8];
+  uint64_t count_ops;       /* algorithmic integer ops of the count kernels:
+                               ROWS h+2 per test (h = touched 32-bit
+                               halves), BITSLICE k+1 per 32-row word      */
+  uint32_t reserved[6];
 } dic_stats;
 
 /* Columns of one trace row (one per iteration of Algorithm 2's loop). */

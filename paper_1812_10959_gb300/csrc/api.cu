@@ -681,6 +681,7 @@ dic_status Miner::run(dic_result **out) {
       chunk = std::min(chunk * 2, chunk_max);
     }
     tests = h_ctrl_->tests;
+    res->stats.count_ops = h_ctrl_->work;
     const uint32_t tail = h_ctrl_->tail;
     res->stats.candidates = tail;
 

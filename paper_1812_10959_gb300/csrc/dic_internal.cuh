@@ -49,7 +49,14 @@ struct Ctrl {
   uint32_t n_trace;
   uint32_t blocks_done;  // ticket of the generate kernel's last-block step
   unsigned long long tests;  // candidate-transaction tests so far
+  unsigned long long work;   // algorithmic integer ops of the count kernels
 };
+
+// Add a per-thread amount to a 64-bit counter with one atomic per warp.
+__device__ __forceinline__ void warp_add_u64(unsigned long long *dst, unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
 
 // Everything a stop's kernels touch, passed by value.
 struct Lattice {

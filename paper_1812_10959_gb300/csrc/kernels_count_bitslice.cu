@@ -217,13 +217,17 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
       }
       __syncthreads();  // the buffer of tile t may be overwritten next
     }
+    unsigned long long work = 0;
     for (uint32_t i = tid; i < cn; i += BS_THREADS) {
       if (!kk[i]) continue;
       const uint32_t c = c0 + i;
       const uint32_t s = L.csupp[c] + cnt[i];
       L.csupp[c] = s;
       settle_record(L, C, c, s, g, true, pruned, solid);
+      // algorithmic work: k-1 AND + POPC + ADD per 32-row word
+      work += (unsigned long long)(kk[i] + 1) * nw32;
     }
+    warp_add_u64(&C->work, work);
   }
   if (pruned) atomicAdd(&C->n_pruned, pruned);
   if (solid) atomicAdd(&C->n_solid, solid);

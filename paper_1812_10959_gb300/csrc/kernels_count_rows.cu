@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(ROWS_THREADS) k_count_rows(Lattice L, uint32_t
       }
     }
     if (live && cnt) atomicAdd(&L.csupp[c], cnt);
+    // algorithmic work: one LOP3 per touched half + compare + add, per test
+    warp_add_u64(&C->work, live ? (unsigned long long)(nw + 2) * (r1 > r0 ? r1 - r0 : 0) : 0ull);
   }
 }
 
@@ -163,6 +165,8 @@ __global__ void __launch_bounds__(ROWS_THREADS) k_count_rows_dense(Lattice L, ui
       }
     }
     if (live && cnt) atomicAdd(&L.csupp[c], cnt);
+    warp_add_u64(&C->work,
+                 live ? (unsigned long long)(2 * wc + 2) * (r1 > r0 ? r1 - r0 : 0) : 0ull);
   }
 }
 
