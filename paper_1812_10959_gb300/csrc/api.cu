@@ -368,11 +368,11 @@ dic_status Miner::launch_phase(int phase) {
     case PH_COUNT: {
       cudaEvent_t a = nullptr, b = nullptr;
       if (cur_path_ == DIC_COUNT_BITSLICE) {
+        // shared memory for the largest chunk that fits; the kernel sizes its
+        // chunk from the live window
         const int kre = kr_bucket(h_ctrl_->max_k);
-        const uint32_t win = h_ctrl_->tail - h_ctrl_->head;
-        uint32_t chunk = (win + bs_grid_ - 1) / bs_grid_;
-        chunk = std::max<uint32_t>(256, (chunk + 3) & ~3u);
-        chunk = std::min(chunk, bitslice_max_chunk(bs_tw_, kre, bs_l1p_, smem_optin_));
+        const uint32_t chunk = std::min<uint32_t>(
+            bitslice_max_chunk(bs_tw_, kre, bs_l1p_, smem_optin_), 1u << 20);
         e = launch_slice_block(L_, bs_V_, bs_tw_, bs_l1p_, bs_V_words_, s_);
         ++launches_;
         if (e == cudaSuccess) {

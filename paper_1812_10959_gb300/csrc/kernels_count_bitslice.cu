@@ -32,7 +32,7 @@
 
 namespace dic {
 
-constexpr int BS_THREADS = 512;
+constexpr int BS_THREADS = 1024;
 
 __host__ __device__ constexpr uint32_t bs_stride(int tw) { return tw == 4 ? 4u : (uint32_t)tw + 4u; }
 
@@ -127,7 +127,7 @@ uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit) {
 template <int TW, int KRE>
 __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
                                                                const uint32_t *__restrict__ V,
-                                                               uint32_t l1p, uint32_t chunk,
+                                                               uint32_t l1p, uint32_t chunk_cap,
                                                                uint64_t vwords) {
   extern __shared__ __align__(16) uint32_t sm[];
   constexpr uint32_t ST = bs_stride(TW);
@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   uint32_t *S0 = sm;
   uint32_t *S1 = sm + tile_words;
   uint16_t *rk = reinterpret_cast<uint16_t *>(sm + 2 * tile_words);
-  uint32_t *cnt = reinterpret_cast<uint32_t *>(rk + (size_t)chunk * KRE);
-  uint8_t *kk = reinterpret_cast<uint8_t *>(cnt + chunk);
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(rk + (size_t)chunk_cap * KRE);
+  uint8_t *kk = reinterpret_cast<uint8_t *>(cnt + chunk_cap);
 
   const uint32_t g = C->step;
   uint32_t stop;
@@ -162,6 +162,11 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   }
   const uint32_t head = C->head, tail = C->tail;
   const uint32_t ncand = tail - head;
+  // balance the live window over the grid; shared memory holds chunk_cap
+  uint32_t chunk = (ncand + gridDim.x - 1) / gridDim.x;
+  chunk = (chunk + 3) & ~3u;
+  if (chunk < 4) chunk = 4;
+  if (chunk > chunk_cap) chunk = chunk_cap;
   const uint32_t nchunks = (ncand + chunk - 1) / chunk;
   const uint32_t tid = threadIdx.x;
   uint32_t pruned = 0, solid = 0;
