@@ -311,6 +311,7 @@ class Miner {
   int bs_grid_ = 0;
   size_t smem_optin_ = 0;
   int cur_path_ = DIC_COUNT_ROWS;
+  bool next_v_ready_ = false;  // the enqueued work builds V for the next count
   int grid_ = 0;
   uint32_t launches_ = 0;
   uint32_t path_launches_[4] = {0, 0, 0, 0};
@@ -370,11 +371,14 @@ dic_status Miner::launch_phase(int phase) {
       if (cur_path_ == DIC_COUNT_BITSLICE) {
         // shared memory for the largest chunk that fits; the kernel sizes its
         // chunk from the live window
-        const int kre = kr_bucket(h_ctrl_->max_k);
+        const int kre = kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4));
         const uint32_t chunk = std::min<uint32_t>(
             bitslice_max_chunk(bs_tw_, kre, bs_l1p_, smem_optin_), 1u << 20);
-        e = launch_slice_block(L_, bs_V_, bs_tw_, bs_l1p_, bs_V_words_, s_);
-        ++launches_;
+        if (!next_v_ready_) {
+          e = launch_slice_block(L_, s_);
+          ++launches_;
+        }
+        next_v_ready_ = false;
         if (e == cudaSuccess) {
           if (opt_.profile) {
             TRY(next_event(&a));
@@ -399,7 +403,10 @@ dic_status Miner::launch_phase(int phase) {
     }
     case PH_PROMOTE: e = launch_promote(L_, grid_, s_); break;
     case PH_HASH: e = launch_hash_insert(L_, grid_, s_); break;
-    case PH_GEN: e = launch_generate_finish(L_, grid_, s_); break;
+    case PH_GEN:
+      e = launch_generate_finish(L_, grid_, cur_path_ == DIC_COUNT_BITSLICE, s_);
+      next_v_ready_ = cur_path_ == DIC_COUNT_BITSLICE;
+      break;
   }
   ++launches_;
   if (e != cudaSuccess) return fail(DIC_ECUDA, "kernel launch (phase %d): %s", phase,
@@ -635,14 +642,23 @@ dic_status Miner::run(dic_result **out) {
         const uint64_t ntiles = ((blockmax + 31) / 32 + bs_tw_ - 1) / bs_tw_;
         bs_V_words_ = (uint64_t)ntiles * bitslice_tile_words(bs_tw_, bs_l1p_);
         TRY(alloc(&bs_V_, bs_V_words_));
+        L_.V = bs_V_;
+        L_.vwords = bs_V_words_;
+        L_.tw = (uint32_t)bs_tw_;
+        L_.l1p = bs_l1p_;
         bs_grid_ = sm_count();
       }
     }
 
     // ---- the stop loop of Algorithm 2
-    uint32_t chunk = opt_.steps_per_sync ? opt_.steps_per_sync : 4;
-    const uint32_t chunk_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
+    // stops enqueued per group: those the newest cohort still needs (more
+    // may follow if new cohorts appear), at most 64 between host checks
+    const uint32_t group_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
     for (;;) {
+      const uint64_t end = (uint64_t)h_ctrl_->last_birth + L_.stop_max + 1;
+      const uint64_t need = end > h_ctrl_->step ? end - h_ctrl_->step : 1;
+      const uint32_t chunk =
+          (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(need, group_max));
       TRY(grow_trace(h_ctrl_->n_trace + chunk + 2));
       if ((uint64_t)(h_ctrl_->hash_used + h_ctrl_->n_live) * 2 > L_.hcap)
         TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live));
@@ -670,6 +686,7 @@ dic_status Miner::run(dic_result **out) {
         } else {
           return fail(DIC_ECUDA, "unknown stall code %u", st);
         }
+        if (phase == PH_COUNT) next_v_ready_ = false;
         h_ctrl_->stall = ST_NONE;
         h_ctrl_->blocks_done = 0;
         CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
@@ -678,7 +695,6 @@ dic_status Miner::run(dic_result **out) {
         if (h_ctrl_->error) return device_error(h_ctrl_->error);
       }
       if (h_ctrl_->done) break;
-      chunk = std::min(chunk * 2, chunk_max);
     }
     tests = h_ctrl_->tests;
     res->stats.count_ops = h_ctrl_->work;

@@ -48,6 +48,8 @@ struct Ctrl {
   uint32_t max_k;      // largest itemset size ever placed in DASHED
   uint32_t n_trace;
   uint32_t blocks_done;  // ticket of the generate kernel's last-block step
+  uint32_t last_birth;   // creation stop of the newest cohort
+  uint32_t pad1;
   unsigned long long tests;  // candidate-transaction tests so far
   unsigned long long work;   // algorithmic integer ops of the count kernels
 };
@@ -89,6 +91,11 @@ struct Lattice {
   uint32_t minsup;
   uint32_t wc;         // words per compact row / mask
   uint32_t l1;         // frequent items (compact ranks 0..l1-1)
+  // BITSLICE column buffer (nullptr when that path is not set up)
+  uint32_t *V;
+  uint64_t vwords;
+  uint32_t tw;
+  uint32_t l1p;
 };
 
 // Block [first, last) of global stop g (1-based), with rewind (Algorithm 2).
@@ -119,7 +126,9 @@ cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s);
 cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s);
 // MAKECANDIDATES followed (in the last block to finish) by the end-of-stop
 // bookkeeping: trace row, cohort, CHECKFULLPASS, loop test.
-cudaError_t launch_generate_finish(Lattice L, int grid, cudaStream_t s);
+// With slice_next, the same launch also builds the BITSLICE columns of the
+// next stop's block (the count of this stop has finished reading them).
+cudaError_t launch_generate_finish(Lattice L, int grid, bool slice_next, cudaStream_t s);
 cudaError_t launch_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap, cudaStream_t s);
 cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
                                  uint32_t *out_count, cudaStream_t s);
@@ -132,8 +141,8 @@ cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, ui
 // j = row +j); stride = TW+4 (TW = 8, 16) or TW (TW = 4), the extra words
 // being padding. l1p = l1 rounded up to a multiple of 4.
 size_t bitslice_tile_words(int tw, uint32_t l1p);
-cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, uint64_t vwords,
-                               cudaStream_t s);
+// Columns of the block of stop g (g = Ctrl.step when g == 0).
+cudaError_t launch_slice_block(Lattice L, cudaStream_t s);
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
                                   uint32_t chunk, uint64_t vwords, int grid, cudaStream_t s);
 // Largest candidate chunk whose bitslice shared-memory footprint fits.

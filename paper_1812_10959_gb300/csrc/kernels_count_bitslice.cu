@@ -34,63 +34,27 @@ namespace dic {
 
 constexpr int BS_THREADS = 1024;
 
-__host__ __device__ constexpr uint32_t bs_stride(int tw) { return tw == 4 ? 4u : (uint32_t)tw + 4u; }
-
 // ------------------------------------------------------------ transpose
-__global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t *__restrict__ V, int tw,
-                                                     uint32_t l1p, uint64_t vwords) {
+// Standalone form (first stop of a run, or a resumed stop); later stops get
+// their columns from the previous stop's generate kernel.
+__global__ void __launch_bounds__(256) k_slice_block(Lattice L) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
-  uint32_t stop;
-  uint64_t first, last;
-  block_of(C->step, L.stop_max, L.M, L.n, &stop, &first, &last);
-  const uint32_t nw32 = (uint32_t)((last - first + 31) / 32);
-  const uint32_t ntiles = (nw32 + tw - 1) / tw;
-  const uint32_t wc = L.wc;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t items = (uint64_t)ntiles * tw * wc;
-  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
-       it += nwarps) {
-    const uint32_t w = (uint32_t)(it / wc), j = (uint32_t)(it % wc);
-    const uint64_t row = first + 32ull * w + lane;
-    const uint64_t x = (w < nw32 && row < last) ? __ldg(L.rows + row * wc + j) : 0ull;
-    uint32_t lo = 0, hi = 0;
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> b) & 1u);
-      if ((int)lane == b) lo = v;
-    }
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> (b + 32)) & 1u);
-      if ((int)lane == b) hi = v;
-    }
-    const uint32_t t = w / tw, wi = w % tw;
-    const uint32_t r0 = j * 64 + lane, r1 = r0 + 32;
-    const uint32_t st = bs_stride(tw);
-    const uint64_t i0 = ((uint64_t)t * l1p + r0) * st + wi, i1 = ((uint64_t)t * l1p + r1) * st + wi;
-    if ((r0 < l1p && i0 >= vwords) || (r1 < l1p && i1 >= vwords)) {  // internal sizing error
-      C->error = DIC_INTERNAL_BOUNDS;
-      continue;
-    }
-    if (r0 < l1p) V[i0] = lo;
-    if (r1 < l1p) V[i1] = hi;
-  }
+  slice_block_warps(L, C->step, (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                    (uint64_t)gridDim.x * (blockDim.x >> 5));
 }
 
-cudaError_t launch_slice_block(Lattice L, uint32_t *V, int tw, uint32_t l1p, uint64_t vwords,
-                               cudaStream_t s) {
+cudaError_t launch_slice_block(Lattice L, cudaStream_t s) {
   const uint64_t blockmax = L.M < L.n ? L.M : L.n;
   const uint64_t nw32 = (blockmax + 31) / 32;
-  const uint64_t items = ((nw32 + tw - 1) / tw) * tw * L.wc;
+  const uint64_t items = ((nw32 + L.tw - 1) / L.tw) * L.tw * L.wc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   uint64_t want = (items + 7) / 8;
   int grid = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
   if (grid < 1) grid = 1;
-  k_slice_block<<<grid, 256, 0, s>>>(L, V, tw, l1p, vwords);
+  k_slice_block<<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 

@@ -302,6 +302,7 @@ __device__ void finish_stop(const Lattice &L, Ctrl *C) {
     L.cohort_start[C->n_cohorts] = C->tail;
     L.cohort_birth[C->n_cohorts] = g;
     C->n_cohorts += 1;
+    C->last_birth = g;
   }
   C->tail += C->n_gen;
   C->hash_used += C->n_newbox;
@@ -316,9 +317,13 @@ __device__ void finish_stop(const Lattice &L, Ctrl *C) {
   if (C->n_live == 0) C->done = 1;
 }
 
-__global__ void __launch_bounds__(256) k_generate_finish(Lattice L) {
+__global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_next) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
+  if (slice_next)  // the columns of stop g+1 (count of stop g is complete)
+    slice_block_warps(L, C->step + 1,
+                      (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                      (uint64_t)gridDim.x * (blockDim.x >> 5));
   const uint32_t P = C->n_newbox;
   const uint32_t g = C->step, base = C->tail, l1 = L.l1, wc = L.wc;
   const uint64_t total = (uint64_t)P * l1;
@@ -381,8 +386,8 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L) {
   }
 }
 
-cudaError_t launch_generate_finish(Lattice L, int grid, cudaStream_t s) {
-  k_generate_finish<<<grid, 256, 0, s>>>(L);
+cudaError_t launch_generate_finish(Lattice L, int grid, bool slice_next, cudaStream_t s) {
+  k_generate_finish<<<grid, 256, 0, s>>>(L, slice_next ? 1 : 0);
   return cudaGetLastError();
 }
 

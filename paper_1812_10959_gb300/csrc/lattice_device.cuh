@@ -100,4 +100,51 @@ __device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_
   if (age == L.stop_max) ++solid;
 }
 
+// BITSLICE column stride of a tile row (words): TW + 4 for TW = 8, 16 and TW
+// for TW = 4, so rows start on 16-byte boundaries and eight threads reading
+// consecutive ranks with 128-bit loads hit distinct banks.
+__host__ __device__ constexpr uint32_t bs_stride(int tw) { return tw == 4 ? 4u : (uint32_t)tw + 4u; }
+
+// Transpose the block of stop g into L.V (see dic_internal.cuh): warp `wid`
+// of `nwarps` handles (32-row word w, mask word j) items; bit j' of the
+// result is row first+32w+j'. Out-of-range rows read as 0. An index outside
+// V (an internal sizing error) is recorded in Ctrl.error and skipped.
+__device__ __forceinline__ void slice_block_warps(const Lattice &L, uint32_t g, uint64_t wid,
+                                                  uint64_t nwarps) {
+  uint32_t stop;
+  uint64_t first, last;
+  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
+  const uint32_t tw = L.tw, l1p = L.l1p, st = bs_stride((int)tw);
+  const uint32_t nw32 = (uint32_t)((last - first + 31) / 32);
+  const uint32_t ntiles = (nw32 + tw - 1) / tw;
+  const uint32_t wc = L.wc;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t items = (uint64_t)ntiles * tw * wc;
+  for (uint64_t it = wid; it < items; it += nwarps) {
+    const uint32_t w = (uint32_t)(it / wc), j = (uint32_t)(it % wc);
+    const uint64_t row = first + 32ull * w + lane;
+    const uint64_t x = (w < nw32 && row < last) ? __ldg(L.rows + row * wc + j) : 0ull;
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> b) & 1u);
+      if ((int)lane == b) lo = v;
+    }
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> (b + 32)) & 1u);
+      if ((int)lane == b) hi = v;
+    }
+    const uint32_t t = w / tw, wi = w % tw;
+    const uint32_t r0 = j * 64 + lane, r1 = r0 + 32;
+    const uint64_t i0 = ((uint64_t)t * l1p + r0) * st + wi, i1 = ((uint64_t)t * l1p + r1) * st + wi;
+    if ((r0 < l1p && i0 >= L.vwords) || (r1 < l1p && i1 >= L.vwords)) {
+      L.ctrl->error = DIC_INTERNAL_BOUNDS;
+      continue;
+    }
+    if (r0 < l1p) L.V[i0] = lo;
+    if (r1 < l1p) L.V[i1] = hi;
+  }
+}
+
 }  // namespace dic
