@@ -53,7 +53,7 @@ def _load():
         pres = ctypes.POINTER(vp)
         for name in ("oracle_dic", "oracle_dic_classic"):
             f = getattr(lib, name)
-            f.argtypes = [vp, vp, u64, u32, u32, u64, u64, pres]
+            f.argtypes = [vp, vp, u64, u32, u32, u64, u64, ctypes.c_int, pres]
             f.restype = ctypes.c_int
         for name in ("oracle_apriori", "oracle_bruteforce"):
             f = getattr(lib, name)
@@ -126,17 +126,21 @@ def _run(name, row_ptr, items, n, m, *args) -> OracleResult:
     return _result(h)
 
 
-def dic(row_ptr, items, n: int, m: int, minsup: int, M: int, max_stops: int = 0) -> OracleResult:
+def dic(row_ptr, items, n: int, m: int, minsup: int, M: int, max_stops: int = 0,
+        superset_loop: bool = True) -> OracleResult:
     """ParallelDIC (Algorithm 2): first pass, then COUNT / PRUNE /
     MAKECANDIDATES / CHECKFULLPASS per block of M rows with rewind.
-    max_stops > 0 ends after that many stops (timing samples only)."""
-    return _run("oracle_dic", row_ptr, items, n, m, minsup, M, max_stops)
+    max_stops > 0 ends after that many stops (timing samples only);
+    superset_loop=False skips Algorithm 4's superset loop (quadratic; the
+    pinned runs show it never changes anything)."""
+    return _run("oracle_dic", row_ptr, items, n, m, minsup, M, max_stops, int(superset_loop))
 
 
 def dic_classic(row_ptr, items, n: int, m: int, minsup: int, M: int,
-                max_stops: int = 0) -> OracleResult:
+                max_stops: int = 0, superset_loop: bool = True) -> OracleResult:
     """Serial DIC of Algorithm 1 (every 1-itemset starts as a dashed circle)."""
-    return _run("oracle_dic_classic", row_ptr, items, n, m, minsup, M, max_stops)
+    return _run("oracle_dic_classic", row_ptr, items, n, m, minsup, M, max_stops,
+                int(superset_loop))
 
 
 def apriori(row_ptr, items, n: int, m: int, minsup: int) -> OracleResult:

@@ -119,7 +119,7 @@ std::vector<Mask> pack_all(const uint64_t *row_ptr, const uint32_t *items, uint6
 void dic_loop(const std::vector<Mask> &B, uint64_t n, uint32_t m, uint32_t minsup, uint64_t M,
               std::vector<Itemset> &SOLID, std::vector<Itemset> &DASHED,
               std::map<Mask, uint64_t> &boxes, std::set<Mask> &ever, Result *r,
-              uint64_t max_stops) {
+              uint64_t max_stops, bool superset_loop) {
   const uint32_t W = words_for(m);
   const uint64_t stop_max = (n + M - 1) / M;
   uint64_t stop = 0, step = 0;
@@ -157,7 +157,7 @@ void dic_loop(const std::vector<Mask> &B, uint64_t n, uint32_t m, uint32_t minsu
         if (supp_max < minsup) {
           I.shape = NIL;
           ++row[TR_PRUNED];
-          for (size_t b = 0; b < DASHED.size(); ++b) {
+          for (size_t b = 0; superset_loop && b < DASHED.size(); ++b) {
             Itemset &J = DASHED[b];
             if (J.shape != CIRCLE) continue;
             if (contains(J.mask, I.mask)) {  // I.mask AND J.mask = I.mask
@@ -260,9 +260,12 @@ int oracle_pack(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint
 
 // ParallelDIC (Algorithm 2), serial.
 // max_stops > 0 ends the loop after that many stops (a bounded timing sample;
-// the itemsets are then incomplete). 0 runs to completion.
+// the itemsets are then incomplete). 0 runs to completion. superset_loop = 0
+// skips the superset loop of Algorithm 4 (quadratic in |DASHED|; it never
+// changes anything, which the pinned runs check by running it).
 int oracle_dic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
-               uint32_t minsup, uint64_t M, uint64_t max_stops, oracle_result **out) {
+               uint32_t minsup, uint64_t M, uint64_t max_stops, int superset_loop,
+               oracle_result **out) {
   *out = nullptr;
   if (m == 0 || minsup == 0 || M == 0) return -1;
   Result *r = new Result();
@@ -301,7 +304,7 @@ int oracle_dic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint3
       ever.insert(J.mask);
       DASHED.push_back(J);
     }
-  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r, max_stops);
+  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r, max_stops, superset_loop != 0);
   collect(SOLID, r);
   *out = r;
   return 0;
@@ -309,7 +312,8 @@ int oracle_dic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint3
 
 // Serial DIC of Algorithm 1: Dashed Circle starts with all 1-itemsets.
 int oracle_dic_classic(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
-                       uint32_t minsup, uint64_t M, uint64_t max_stops, oracle_result **out) {
+                       uint32_t minsup, uint64_t M, uint64_t max_stops, int superset_loop,
+                       oracle_result **out) {
   *out = nullptr;
   if (m == 0 || minsup == 0 || M == 0) return -1;
   Result *r = new Result();
@@ -327,7 +331,7 @@ int oracle_dic_classic(const uint64_t *row_ptr, const uint32_t *items, uint64_t 
     DASHED.push_back(I);
   }
   std::map<Mask, uint64_t> boxes;
-  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r, max_stops);
+  dic_loop(B, n, m, minsup, M, SOLID, DASHED, boxes, ever, r, max_stops, superset_loop != 0);
   collect(SOLID, r);
   *out = r;
   return 0;

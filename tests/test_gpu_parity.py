@@ -207,3 +207,57 @@ def test_growth_inside_the_first_group_of_stops(dic, path):
                            tx_len_mean=9.0)
     res, ref = check(dic, rp, it, 3000, 70, 60, 700, path)
     assert len(res.itemsets()) == 1693
+
+
+@pytest.fixture(scope="module")
+def dense_small():
+    return synth.dense_zipf(n=2000)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_dense_reduced_rows_full_oracle(dic, dense_small, path):
+    """Dense recipe (4,096 items, ~400 per row, minsup 20%) on 2,000 rows:
+    exact itemsets and trace against the full oracle run."""
+    db = dense_small
+    h = dic.load_db_csr(db.row_ptr, db.items, db.n, db.m)
+    res = dic.mine(h, db.minsup, 400, path=path)
+    h.free()
+    ref = oracle.dic(db.row_ptr, db.items, db.n, db.m, db.minsup, 400, superset_loop=False)
+    assert res.itemsets() == ref.itemsets
+    assert res.trace.tolist() == ref.trace.tolist()
+    assert res.stats["tests"] == ref.tests
+    assert res.stats["l1"] > 400
+
+
+def test_dense_full_size(dic):
+    """Dense recipe at its full size (200,000 rows), in the launch
+    configuration bench.py uses: every 1-itemset exact, every reported
+    itemset's support equal to the oracle's, the itemsets downward closed,
+    and a seeded sample of the pair negative border infrequent; the ROWS path
+    agrees."""
+    db = synth.dense_zipf()
+    h = dic.load_db_csr(db.row_ptr, db.items, db.n, db.m)
+    res = dic.mine(h, db.minsup, db.M, path="auto")
+    got = res.itemsets()
+    assert got == dic.mine(h, db.minsup, db.M, path="rows").itemsets()
+    h.free()
+    freq = np.bincount(db.items, minlength=db.m)
+    assert [x for x in got if len(x[0]) == 1] == [((i,), int(freq[i])) for i in range(db.m)
+                                                  if freq[i] >= db.minsup]
+    big = [x for x in got if len(x[0]) >= 2]
+    assert len(big) > 100
+    sup = oracle.support(db.row_ptr, db.items, db.n, db.m, [s for s, _ in big])
+    assert [int(v) for v in sup] == [v for _, v in big]
+    gd = dict(got)
+    for X, _ in big:
+        for j in range(len(X)):
+            assert X[:j] + X[j + 1:] in gd
+    l1 = [s[0] for s, _ in got if len(s) == 1]
+    rng = np.random.default_rng(3)
+    border = set()
+    while len(border) < 3000:
+        a, b = sorted(rng.choice(l1, 2, replace=False).tolist())
+        if (a, b) not in gd:
+            border.add((a, b))
+    bs = oracle.support(db.row_ptr, db.items, db.n, db.m, sorted(border))
+    assert (bs < db.minsup).all()
