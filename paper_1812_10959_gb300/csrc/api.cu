@@ -251,6 +251,34 @@ class Miner {
   ~Miner() { release(); }
 
   dic_status run(dic_result **out);
+  // run() in phases, for the batched driver: begin() enqueues the first pass;
+  // after a stream synchronisation prepare() builds the lattice; loop() runs
+  // the remaining stops alone; collect() returns the result.
+  dic_status begin();
+  dic_status prepare();
+  dic_status loop();
+  dic_status collect(dic_result **out);
+  // Use a loop-state record owned by the caller (device and pinned host
+  // copies); call before begin().
+  void use_external_ctrl(Ctrl *dev, Ctrl *host) { ext_ctrl_ = dev; h_ctrl_ = host; }
+  bool has_loop() const { return has_loop_; }
+  Lattice &lattice() { return L_; }
+  Ctrl *host_ctrl() { return h_ctrl_; }
+  bool bitslice_ready() const { return bs_ok_; }
+  uint32_t l1p() const { return bs_l1p_; }
+  int tile_words_per_rank() const { return bs_tw_; }
+  uint64_t stop_max() const { return stop_max64_; }
+  // Recover a stop that stalled (grow what it needs, re-run it from the
+  // stalled phase with this query's own kernels); no-op without a stall.
+  dic_status recover();
+  // Grow what the next `stops` stops may need before they are enqueued.
+  dic_status reserve(uint32_t stops);
+  void set_forced_tw(int tw) { forced_tw_ = tw; }
+  // Rebuild the BITSLICE column buffer for another tile width (the batched
+  // count uses one width for all queries). False if it does not fit.
+  dic_status set_tile_width(int tw, bool *ok);
+  uint32_t launches() const { return launches_; }
+  void add_launches(uint32_t k) { launches_ += k; }
 
  private:
   template <class T>
@@ -276,7 +304,10 @@ class Miner {
     for (cudaEvent_t ev : ev_pool_) cudaEventDestroy(ev);
     ev_pool_.clear();
     ev_used_ = 0;
-    if (h_ctrl_) { cudaFreeHost(h_ctrl_); h_ctrl_ = nullptr; }
+    if (h_ctrl_ && own_h_ctrl_) { cudaFreeHost(h_ctrl_); h_ctrl_ = nullptr; }
+    if (h_cnt1_) { cudaFreeHost(h_cnt1_); h_cnt1_ = nullptr; }
+    if (fa_) { cudaEventDestroy(fa_); fa_ = nullptr; }
+    if (fb_) { cudaEventDestroy(fb_); fb_ = nullptr; }
   }
 
   dic_status grow_candidates(uint32_t need);
@@ -316,6 +347,19 @@ class Miner {
   uint32_t launches_ = 0;
   uint32_t path_launches_[4] = {0, 0, 0, 0};
   uint64_t candidates_cap_limit_ = 0xFFFFFFF0ull;
+  // phase state
+  std::chrono::steady_clock::time_point t0_;
+  std::unique_ptr<dic_result> res_;
+  uint64_t n_ = 0, stop_max64_ = 0, tests_ = 0;
+  uint32_t *h_cnt1_ = nullptr;
+  cudaEvent_t fa_ = nullptr, fb_ = nullptr;
+  std::vector<uint32_t> l1items_;
+  std::vector<std::vector<uint32_t>> sets_;
+  std::vector<uint32_t> supps_;
+  bool has_loop_ = false;
+  Ctrl *ext_ctrl_ = nullptr;
+  bool own_h_ctrl_ = false;
+  int forced_tw_ = 0;
 };
 
 // Count path for the next stops: BITSLICE whenever the block's columns fit in
@@ -506,57 +550,59 @@ static bool canon_less(const std::vector<uint32_t> &a, const std::vector<uint32_
   return a < b;
 }
 
-dic_status Miner::run(dic_result **out) {
-  auto t0 = std::chrono::steady_clock::now();
-  const uint64_t n = db_->n;
-  const uint32_t m = db_->m, W = db_->W;
-  std::unique_ptr<dic_result> res(new dic_result());
-  res->W = W;
-  res->stats.words = W;
+// ---- phase 1: first pass launched, its counts copied to pinned memory
+dic_status Miner::begin() {
+  t0_ = std::chrono::steady_clock::now();
+  n_ = db_->n;
+  res_.reset(new dic_result());
+  res_->W = db_->W;
+  res_->stats.words = db_->W;
   grid_ = sm_count() * 4;
-  if (n == 0) {
-    *out = res.release();
-    return DIC_OK;
+  if (n_ == 0) return DIC_OK;
+  if (M_ > n_) M_ = n_;
+  stop_max64_ = (n_ + M_ - 1) / M_;
+  if (!h_ctrl_) {
+    CU(cudaMallocHost((void **)&h_ctrl_, sizeof(Ctrl)));
+    own_h_ctrl_ = true;
   }
-  if (M_ > n) M_ = n;
-  const uint64_t stop_max64 = (n + M_ - 1) / M_;
-  CU(cudaMallocHost((void **)&h_ctrl_, sizeof(Ctrl)));
-
-  // ---- FIRSTPASS: supports of all 1-itemsets over all n rows
+  CU(cudaMallocHost((void **)&h_cnt1_, (size_t)db_->m * 4));
   uint32_t *d_cnt1 = nullptr;
-  TRY(alloc(&d_cnt1, m));
-  cudaEvent_t fa = nullptr, fb = nullptr;
+  TRY(alloc(&d_cnt1, db_->m));
   if (opt_.profile) {
-    CU(cudaEventCreate(&fa));
-    CU(cudaEventCreate(&fb));
-    CU(cudaEventRecord(fa, s_));
+    CU(cudaEventCreate(&fa_));
+    CU(cudaEventCreate(&fb_));
+    CU(cudaEventRecord(fa_, s_));
   }
-  CU(launch_item_count(db_->words, n, W, m, d_cnt1, s_));
+  CU(launch_item_count(db_->words, n_, db_->W, db_->m, d_cnt1, s_));
   ++launches_;
-  if (opt_.profile) CU(cudaEventRecord(fb, s_));
-  std::vector<uint32_t> cnt1(m);
-  CU(cudaMemcpyAsync(cnt1.data(), d_cnt1, (size_t)m * 4, cudaMemcpyDeviceToHost, s_));
-  CU(cudaStreamSynchronize(s_));
+  if (opt_.profile) CU(cudaEventRecord(fb_, s_));
+  CU(cudaMemcpyAsync(h_cnt1_, d_cnt1, (size_t)db_->m * 4, cudaMemcpyDeviceToHost, s_));
+  return DIC_OK;
+}
+
+// ---- phase 2 (stream synchronised since begin): L1, compaction, lattice,
+// pair join. Sets has_loop_ when there are candidate pairs.
+dic_status Miner::prepare() {
+  has_loop_ = false;
+  if (n_ == 0) return DIC_OK;
+  const uint64_t n = n_;
+  const uint32_t m = db_->m, W = db_->W;
+  const uint64_t stop_max64 = stop_max64_;
   if (opt_.profile) {
     float ms = 0;
-    cudaEventElapsedTime(&ms, fa, fb);
-    res->stats.firstpass_ms = ms;
-    cudaEventDestroy(fa);
-    cudaEventDestroy(fb);
+    cudaEventElapsedTime(&ms, fa_, fb_);
+    res_->stats.firstpass_ms = ms;
   }
-  std::vector<uint32_t> l1items;
+  const uint32_t *cnt1 = h_cnt1_;
   for (uint32_t i = 0; i < m; ++i)
-    if (cnt1[i] >= minsup_) l1items.push_back(i);
+    if (cnt1[i] >= minsup_) l1items_.push_back(i);
+  const std::vector<uint32_t> &l1items = l1items_;
   const uint32_t l1 = (uint32_t)l1items.size();
-  res->stats.l1 = l1;
+  res_->stats.l1 = l1;
   const uint32_t wc = std::max<uint32_t>(1, (l1 + 63) / 64);
-  res->stats.words_compact = wc;
-  uint64_t tests = (uint64_t)m * n;
-
-  std::vector<std::vector<uint32_t>> sets;
-  std::vector<uint32_t> supps;
-  for (uint32_t i : l1items) { sets.push_back({i}); supps.push_back(cnt1[i]); }
-
+  res_->stats.words_compact = wc;
+  tests_ = (uint64_t)m * n;
+  for (uint32_t i : l1items) { sets_.push_back({i}); supps_.push_back(cnt1[i]); }
   const uint64_t npairs = (uint64_t)l1 * (l1 - (l1 ? 1 : 0)) / 2;
   if (npairs > 0) {
     if (npairs > candidates_cap_limit_ ||
@@ -604,7 +650,7 @@ dic_status Miner::run(dic_result **out) {
     TRY(alloc(&L_.cohort_start, (size_t)L_.tcap + 2));
     TRY(alloc(&L_.cohort_birth, (size_t)L_.tcap + 2, true));
     CU(cudaMemsetAsync(L_.cohort_start, 0, ((size_t)L_.tcap + 2) * 4, s_));
-    TRY(alloc(&L_.ctrl, 1));
+    if (!ext_ctrl_) TRY(alloc(&L_.ctrl, 1)); else L_.ctrl = ext_ctrl_;
     Ctrl c{};
     c.step = 1;
     c.head = 0;
@@ -612,7 +658,7 @@ dic_status Miner::run(dic_result **out) {
     c.n_live = (uint32_t)npairs;
     c.n_cohorts = 1;
     c.max_k = 2;
-    c.tests = tests;
+    c.tests = tests_;
     *h_ctrl_ = c;
     CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
     CU(launch_pair_join(L_, npairs, s_));
@@ -630,6 +676,7 @@ dic_status Miner::run(dic_result **out) {
       bs_ok_ = false;
       if (l1 <= 65535 && opt_.count_path != DIC_COUNT_ROWS) {
         for (int tw : {16, 8, 4}) {
+          if (forced_tw_ && tw != forced_tw_) continue;
           if (bitslice_max_chunk(tw, 16, bs_l1p_, smem_optin_) >= 1024) {
             bs_tw_ = tw;
             bs_ok_ = true;
@@ -650,52 +697,111 @@ dic_status Miner::run(dic_result **out) {
       }
     }
 
-    // ---- the stop loop of Algorithm 2
-    // stops enqueued per group: those the newest cohort still needs (more
-    // may follow if new cohorts appear), at most 64 between host checks
-    const uint32_t group_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
-    for (;;) {
-      const uint64_t end = (uint64_t)h_ctrl_->last_birth + L_.stop_max + 1;
-      const uint64_t need = end > h_ctrl_->step ? end - h_ctrl_->step : 1;
-      const uint32_t chunk =
-          (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(need, group_max));
-      TRY(grow_trace(h_ctrl_->n_trace + chunk + 2));
-      if ((uint64_t)(h_ctrl_->hash_used + h_ctrl_->n_live) * 2 > L_.hcap)
-        TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live));
-      int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
-      nw_ = bucket ? (uint32_t)bucket : 0;
+    has_loop_ = true;
+  }
+  return DIC_OK;
+}
+
+// ---- phase 3: the stop loop of Algorithm 2 for this query alone
+// Stops the newest cohort still needs (more may follow if cohorts appear).
+static uint32_t stops_needed(const Ctrl &c, uint32_t stop_max, uint32_t cap) {
+  const uint64_t end = (uint64_t)c.last_birth + stop_max + 1;
+  const uint64_t need = end > c.step ? end - c.step : 1;
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(need, cap));
+}
+
+dic_status Miner::reserve(uint32_t stops) {
+  TRY(grow_trace(h_ctrl_->n_trace + stops + 2));
+  if ((uint64_t)(h_ctrl_->hash_used + h_ctrl_->n_live) * 2 > L_.hcap)
+    TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live));
+  return DIC_OK;
+}
+
+dic_status Miner::set_tile_width(int tw, bool *ok) {
+  *ok = false;
+  if (!bs_ok_) return DIC_OK;
+  if (tw == bs_tw_) { *ok = true; return DIC_OK; }
+  if (bitslice_max_chunk(tw, 16, bs_l1p_, smem_optin_) < 1024) return DIC_OK;
+  const uint64_t blockmax = std::min<uint64_t>(M_, n_);
+  const uint64_t ntiles = ((blockmax + 31) / 32 + tw - 1) / tw;
+  drop(bs_V_);
+  bs_tw_ = tw;
+  bs_V_words_ = (uint64_t)ntiles * bitslice_tile_words(bs_tw_, bs_l1p_);
+  TRY(alloc(&bs_V_, bs_V_words_));
+  L_.V = bs_V_;
+  L_.vwords = bs_V_words_;
+  L_.tw = (uint32_t)bs_tw_;
+  next_v_ready_ = false;
+  *ok = true;
+  return DIC_OK;
+}
+
+dic_status Miner::recover() {
+  const uint32_t wc = L_.wc;
+  if (h_ctrl_->error) return device_error(h_ctrl_->error);
+  if (h_ctrl_->stall) {
+    int b = rows_width_bucket(h_ctrl_->max_k, wc);
+    nw_ = b ? (uint32_t)b : 0;
+    cur_path_ = count_path_for_stop();
+  }
+  while (h_ctrl_->stall) {
+    const uint32_t st = h_ctrl_->stall;
+    int phase = PH_COUNT;
+    if (st == ST_WIDTH) {
+      int b = rows_width_bucket(h_ctrl_->max_k, wc);
+      nw_ = b ? (uint32_t)b : 0;
       cur_path_ = count_path_for_stop();
-      for (uint32_t i = 0; i < chunk; ++i) TRY(launch_stop_from(PH_COUNT));
-      TRY(sync_ctrl());
-      if (h_ctrl_->error) return device_error(h_ctrl_->error);
-      while (h_ctrl_->stall) {
-        const uint32_t st = h_ctrl_->stall;
-        int phase = PH_COUNT;
-        if (st == ST_WIDTH) {
-          int b = rows_width_bucket(h_ctrl_->max_k, wc);
-          nw_ = b ? (uint32_t)b : 0;
-          cur_path_ = count_path_for_stop();
-          phase = PH_COUNT;
-        } else if (st == ST_HASH || st == ST_HASH_COUNT) {
-          TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live + h_ctrl_->n_newbox));
-          phase = st == ST_HASH ? PH_HASH : PH_COUNT;
-        } else if (st == ST_CAND) {
-          TRY(grow_candidates(h_ctrl_->tail + h_ctrl_->n_gen));
-          h_ctrl_->n_gen = 0;
-          phase = PH_GEN;
-        } else {
-          return fail(DIC_ECUDA, "unknown stall code %u", st);
-        }
-        if (phase == PH_COUNT) next_v_ready_ = false;
-        h_ctrl_->stall = ST_NONE;
-        h_ctrl_->blocks_done = 0;
-        CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
-        TRY(launch_stop_from(phase));
-        TRY(sync_ctrl());
-        if (h_ctrl_->error) return device_error(h_ctrl_->error);
-      }
-      if (h_ctrl_->done) break;
+      phase = PH_COUNT;
+    } else if (st == ST_HASH || st == ST_HASH_COUNT) {
+      TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live + h_ctrl_->n_newbox));
+      phase = st == ST_HASH ? PH_HASH : PH_COUNT;
+    } else if (st == ST_CAND) {
+      TRY(grow_candidates(h_ctrl_->tail + h_ctrl_->n_gen));
+      h_ctrl_->n_gen = 0;
+      phase = PH_GEN;
+    } else {
+      return fail(DIC_ECUDA, "unknown stall code %u", st);
     }
+    if (phase == PH_COUNT) next_v_ready_ = false;
+    h_ctrl_->stall = ST_NONE;
+    h_ctrl_->blocks_done = 0;
+    CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
+    TRY(launch_stop_from(phase));
+    TRY(sync_ctrl());
+    if (h_ctrl_->error) return device_error(h_ctrl_->error);
+  }
+  return DIC_OK;
+}
+
+dic_status Miner::loop() {
+  if (!has_loop_) return DIC_OK;
+  const uint32_t wc = L_.wc;
+  // stops enqueued per group: those the newest cohort still needs, at most
+  // 64 between host checks
+  const uint32_t group_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
+  while (!h_ctrl_->done) {
+    const uint32_t group = stops_needed(*h_ctrl_, L_.stop_max, group_max);
+    TRY(reserve(group));
+    int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
+    nw_ = bucket ? (uint32_t)bucket : 0;
+    cur_path_ = count_path_for_stop();
+    for (uint32_t i = 0; i < group; ++i) TRY(launch_stop_from(PH_COUNT));
+    TRY(sync_ctrl());
+    TRY(recover());
+  }
+  return DIC_OK;
+}
+
+// ---- phase 4: SOLID boxes to the host, canonical order
+dic_status Miner::collect(dic_result **out) {
+  const uint32_t W = db_->W;
+  std::unique_ptr<dic_result> res(std::move(res_));
+  std::vector<std::vector<uint32_t>> &sets = sets_;
+  std::vector<uint32_t> &supps = supps_;
+  const std::vector<uint32_t> &l1items = l1items_;
+  uint64_t tests = tests_;
+  if (has_loop_) {
+    const uint32_t wc = L_.wc;
     tests = h_ctrl_->tests;
     res->stats.count_ops = h_ctrl_->work;
     const uint32_t tail = h_ctrl_->tail;
@@ -745,7 +851,6 @@ dic_status Miner::run(dic_result **out) {
   } else {
     res->stats.candidates = 0;
   }
-
   // ---- canonical order, original item space
   std::vector<uint32_t> order(sets.size());
   for (uint32_t i = 0; i < order.size(); ++i) order[i] = i;
@@ -772,9 +877,18 @@ dic_status Miner::run(dic_result **out) {
   cudaError_t e = cudaStreamSynchronize(s_);
   if (e != cudaSuccess) return fail(DIC_ECUDA, "finalise: %s", cudaGetErrorString(e));
   res->stats.mine_ms =
-      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_).count();
   *out = res.release();
   return DIC_OK;
+}
+
+
+dic_status Miner::run(dic_result **out) {
+  TRY(begin());
+  CU(cudaStreamSynchronize(s_));
+  TRY(prepare());
+  TRY(loop());
+  return collect(out);
 }
 
 }  // namespace
@@ -819,19 +933,228 @@ extern "C" dic_status dic_mine(const dic_db *db, uint32_t minsup_count, uint64_t
   return dic_mine_ex(db, minsup_count, M, nullptr, nullptr, out);
 }
 
+
+// ------------------------------------------------------------ batch driver
+// Mines many queries together: every query keeps its own lattice; a round
+// advances every active query by one stop and each phase of a round is one
+// launch for all of them (kernels_batch.cu). Queries whose BITSLICE columns
+// do not fit the common tile width, or whose itemsets outgrow the ranks the
+// batched count handles, finish alone afterwards ("solo").
+namespace {
+
+class BatchMiner {
+ public:
+  BatchMiner(const dic_db *const *dbs, const uint32_t *minsup, const uint64_t *M, uint32_t Q,
+             const dic_options &opt, cudaStream_t s)
+      : dbs_(dbs), minsup_(minsup), M_(M), Q_(Q), opt_(opt), s_(s) {}
+  ~BatchMiner() {
+    ms_.clear();
+    for (void *p : bufs_) cudaFreeAsync(p, s_);
+    cudaStreamSynchronize(s_);
+    if (h_ctrls_) cudaFreeHost(h_ctrls_);
+    if (h_Ls_) cudaFreeHost(h_Ls_);
+  }
+  dic_status run(dic_result **out);
+  uint32_t batch_launches() const { return launches_; }
+
+ private:
+  template <class T>
+  dic_status alloc(T **p, size_t count) {
+    cudaError_t e = cudaMallocAsync((void **)p, std::max<size_t>(count * sizeof(T), 16), s_);
+    if (e != cudaSuccess) return fail(DIC_ENOMEM, "batch allocation: %s", cudaGetErrorString(e));
+    bufs_.push_back(*p);
+    return DIC_OK;
+  }
+  dic_status upload_lattices();
+  dic_status sync_ctrls();
+
+  const dic_db *const *dbs_;
+  const uint32_t *minsup_;
+  const uint64_t *M_;
+  uint32_t Q_;
+  dic_options opt_;
+  cudaStream_t s_;
+  std::vector<void *> bufs_;
+  std::vector<std::unique_ptr<Miner>> ms_;
+  Ctrl *d_ctrls_ = nullptr, *h_ctrls_ = nullptr;
+  Lattice *d_Ls_ = nullptr, *h_Ls_ = nullptr;
+  uint32_t launches_ = 0;
+};
+
+dic_status BatchMiner::upload_lattices() {
+  for (uint32_t q = 0; q < Q_; ++q) {
+    h_Ls_[q] = ms_[q]->has_loop() ? ms_[q]->lattice() : Lattice{};
+    h_Ls_[q].ctrl = d_ctrls_ + q;
+  }
+  CU(cudaMemcpyAsync(d_Ls_, h_Ls_, (size_t)Q_ * sizeof(Lattice), cudaMemcpyHostToDevice, s_));
+  return DIC_OK;
+}
+
+dic_status BatchMiner::sync_ctrls() {
+  CU(cudaMemcpyAsync(h_ctrls_, d_ctrls_, (size_t)Q_ * sizeof(Ctrl), cudaMemcpyDeviceToHost, s_));
+  CU(cudaStreamSynchronize(s_));
+  return DIC_OK;
+}
+
+dic_status BatchMiner::run(dic_result **out) {
+  const uint32_t Q = Q_;
+  CU(cudaMallocHost((void **)&h_ctrls_, (size_t)Q * sizeof(Ctrl)));
+  CU(cudaMallocHost((void **)&h_Ls_, (size_t)Q * sizeof(Lattice)));
+  TRY(alloc(&d_ctrls_, Q));
+  TRY(alloc(&d_Ls_, Q));
+  uint32_t *d_items = nullptr, *d_chunk = nullptr;
+  uint64_t *d_gen = nullptr, *d_slice = nullptr;
+  TRY(alloc(&d_items, (size_t)Q + 1));
+  TRY(alloc(&d_chunk, 1));
+  TRY(alloc(&d_gen, (size_t)Q + 1));
+  TRY(alloc(&d_slice, (size_t)Q + 1));
+  // every loop-state record starts as "done" (queries without candidate
+  // pairs keep it); prepare() initialises the others
+  for (uint32_t q = 0; q < Q; ++q) {
+    h_ctrls_[q] = Ctrl{};
+    h_ctrls_[q].done = 1;
+  }
+  CU(cudaMemcpyAsync(d_ctrls_, h_ctrls_, (size_t)Q * sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
+  for (uint32_t q = 0; q < Q; ++q) {
+    ms_.emplace_back(new Miner(dbs_[q], minsup_[q], M_[q], opt_, s_));
+    ms_[q]->use_external_ctrl(d_ctrls_ + q, h_ctrls_ + q);
+    TRY(ms_[q]->begin());
+  }
+  CU(cudaStreamSynchronize(s_));
+  int tw = 16;
+  for (uint32_t q = 0; q < Q; ++q) {
+    TRY(ms_[q]->prepare());
+    if (ms_[q]->has_loop() && ms_[q]->bitslice_ready())
+      tw = std::min(tw, ms_[q]->tile_words_per_rank());
+  }
+  // one tile width for the batch; queries that cannot use it go solo
+  std::vector<bool> solo(Q, false);
+  uint32_t max_l1p = 4;
+  for (uint32_t q = 0; q < Q; ++q) {
+    if (!ms_[q]->has_loop()) continue;
+    bool ok = false;
+    TRY(ms_[q]->set_tile_width(tw, &ok));
+    solo[q] = !ok;
+    if (ok) max_l1p = std::max(max_l1p, ms_[q]->l1p());
+    h_ctrls_[q].solo = solo[q] ? 1 : 0;
+  }
+  int dev = 0, optin = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  CU(cudaMemcpyAsync(d_ctrls_, h_ctrls_, (size_t)Q * sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
+  TRY(upload_lattices());
+  const int grid = sms, gen_grid = sms * 4;
+  // bit columns of every query's first stop, then the first plan
+  CU(launch_batch_plan_gen(d_Ls_, Q, 0, d_gen, d_slice, s_));
+  CU(launch_batch_gen(d_Ls_, Q, 0, d_gen, d_slice, gen_grid, s_));
+  launches_ += 2;
+  const uint32_t group_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
+  for (;;) {
+    uint32_t max_k = 2, group = 0;
+    for (uint32_t q = 0; q < Q; ++q) {
+      const Ctrl &c = h_ctrls_[q];
+      if (c.done || solo[q]) continue;
+      max_k = std::max(max_k, c.max_k);
+      group = std::max(group, stops_needed(c, ms_[q]->lattice().stop_max, group_max));
+    }
+    if (group == 0) break;
+    if (max_k > (uint32_t)KRMAX) {  // these queries continue alone
+      for (uint32_t q = 0; q < Q; ++q)
+        if (!h_ctrls_[q].done && !solo[q] && h_ctrls_[q].max_k > (uint32_t)KRMAX) {
+          solo[q] = true;
+          h_ctrls_[q].solo = 1;
+          CU(cudaMemcpyAsync(d_ctrls_ + q, h_ctrls_ + q, sizeof(Ctrl), cudaMemcpyHostToDevice,
+                             s_));
+        }
+      continue;
+    }
+    const int kre = kr_bucket(std::max<uint32_t>(max_k, 4));
+    for (uint32_t q = 0; q < Q; ++q)
+      if (!h_ctrls_[q].done && !solo[q]) TRY(ms_[q]->reserve(group));
+    TRY(upload_lattices());
+    const uint32_t chunk_cap = bitslice_max_chunk(tw, kre, max_l1p, (size_t)optin);
+    const uint32_t smem = (uint32_t)bitslice_smem(tw, kre, max_l1p, chunk_cap);
+    CU(launch_batch_plan(d_Ls_, Q, false, grid, chunk_cap, d_items, d_chunk, s_));
+    ++launches_;
+    for (uint32_t r = 0; r < group; ++r) {
+      CU(launch_batch_count(d_Ls_, Q, tw, kre, d_items, d_chunk, smem, grid, s_));
+      CU(launch_batch_plan_gen(d_Ls_, Q, 1, d_gen, d_slice, s_));
+      CU(launch_batch_gen(d_Ls_, Q, 1, d_gen, d_slice, gen_grid, s_));
+      CU(launch_batch_plan(d_Ls_, Q, true, grid, chunk_cap, d_items, d_chunk, s_));
+      launches_ += 4;
+    }
+    TRY(sync_ctrls());
+    bool changed = false;
+    for (uint32_t q = 0; q < Q; ++q) {
+      if (solo[q] || !ms_[q]->has_loop()) continue;
+      if (h_ctrls_[q].error) return device_error(h_ctrls_[q].error);
+      if (h_ctrls_[q].stall) {
+        TRY(ms_[q]->recover());
+        changed = true;
+      }
+    }
+    (void)changed;
+  }
+  // queries that left the batch finish alone
+  for (uint32_t q = 0; q < Q; ++q)
+    if (solo[q] && ms_[q]->has_loop()) {
+      h_ctrls_[q].solo = 0;
+      TRY(ms_[q]->loop());
+    }
+  for (uint32_t q = 0; q < Q; ++q) {
+    if (q == 0) ms_[q]->add_launches(launches_);
+    TRY(ms_[q]->collect(&out[q]));
+  }
+  return DIC_OK;
+}
+
+}  // namespace
+
 extern "C" dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *minsup,
                                      const uint64_t *M, uint32_t count, const dic_options *opt,
                                      dic_result **out) {
   if (!out || (count && (!dbs || !minsup || !M))) return fail(DIC_EINVAL, "NULL argument");
   for (uint32_t i = 0; i < count; ++i) out[i] = nullptr;
+  if (count == 0) return DIC_OK;
   for (uint32_t i = 0; i < count; ++i) {
-    dic_status st = dic_mine_ex(dbs[i], minsup[i], M[i], opt, nullptr, &out[i]);
-    if (st != DIC_OK) {
-      for (uint32_t j = 0; j <= i; ++j) { dic_result_free(out[j]); out[j] = nullptr; }
-      return st;
-    }
+    if (!dbs[i]) return fail(DIC_EINVAL, "dbs[%u] is NULL", i);
+    if (minsup[i] == 0) return fail(DIC_EINVAL, "minsup[%u] must be >= 1", i);
+    if (M[i] == 0) return fail(DIC_EINVAL, "M[%u] must be >= 1", i);
+    if (dbs[i]->device != dbs[0]->device) return fail(DIC_EINVAL, "databases on different devices");
   }
-  return DIC_OK;
+  dic_options o;
+  dic_options_init(&o);
+  if (opt) std::memcpy(&o, opt, std::min<size_t>(sizeof o, opt->struct_size ? opt->struct_size : sizeof o));
+  if (o.count_path == DIC_COUNT_ROWS) {  // plain per-query GPU DIC, one after another
+    for (uint32_t i = 0; i < count; ++i) {
+      dic_status st = dic_mine_ex(dbs[i], minsup[i], M[i], &o, nullptr, &out[i]);
+      if (st != DIC_OK) {
+        for (uint32_t j = 0; j <= i; ++j) { dic_result_free(out[j]); out[j] = nullptr; }
+        return st;
+      }
+    }
+    return DIC_OK;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != dbs[0]->device) cudaSetDevice(dbs[0]->device);
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(DIC_ECUDA, "stream creation failed");
+  for (uint32_t i = 0; i < count; ++i) const_cast<dic_db *>(dbs[i])->busy.fetch_add(1);
+  dic_status st;
+  {
+    BatchMiner bm(dbs, minsup, M, count, o, s);
+    st = bm.run(out);
+    if (st != DIC_OK)
+      for (uint32_t j = 0; j < count; ++j) { dic_result_free(out[j]); out[j] = nullptr; }
+  }
+  cudaStreamSynchronize(s);
+  for (uint32_t i = 0; i < count; ++i) const_cast<dic_db *>(dbs[i])->busy.fetch_sub(1);
+  cudaStreamDestroy(s);
+  if (prev != dbs[0]->device) cudaSetDevice(prev);
+  return st;
 }
 
 // ----------------------------------------------------------------- results

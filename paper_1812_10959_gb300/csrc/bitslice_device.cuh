@@ -1,0 +1,138 @@
+// BITSLICE count body shared by the single-query and the batched kernels.
+#pragma once
+#include <cstdint>
+
+#include "dic_internal.cuh"
+#include "lattice_device.cuh"
+
+namespace dic {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// Checks a count launch makes before changing anything for a query: every
+// dashed itemset fits KRE ranks, and the box set has room for every live
+// record to be promoted. Reads only values no count kernel changes, so all
+// CTAs of a launch decide alike. `report` lets one thread raise the stall.
+template <int KRE>
+__device__ __forceinline__ bool bs_checks(const Lattice &L, Ctrl *C, bool report) {
+  if (C->max_k > (uint32_t)KRE) {
+    if (report && threadIdx.x == 0) C->stall = ST_WIDTH;
+    return false;
+  }
+  if ((uint64_t)(C->hash_used + C->n_live) * 2 > L.hcap) {
+    if (report && threadIdx.x == 0) C->stall = ST_HASH_COUNT;
+    return false;
+  }
+  return true;
+}
+
+// 32-row words and tiles of stop g's block; false (error recorded) if they
+// would not fit the column buffer.
+template <int TW>
+__device__ __forceinline__ bool bs_block_tiles(const Lattice &L, Ctrl *C, uint32_t g,
+                                               uint32_t *nw32, uint32_t *ntiles) {
+  uint32_t stop;
+  uint64_t first, last;
+  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
+  *nw32 = (uint32_t)((last - first + 31) / 32);
+  *ntiles = (*nw32 + TW - 1) / TW;
+  if ((uint64_t)(*ntiles) * L.l1p * bs_stride(TW) > L.vwords || L.tw != (uint32_t)TW) {
+    if (threadIdx.x == 0) C->error = DIC_INTERNAL_BOUNDS;
+    return false;
+  }
+  return true;
+}
+
+// Count records [c0, c0+cn) of the window over the block of stop g and apply
+// PRUNE (Algorithm 4) to each. Tiles of L.V stream through a cp.async double
+// buffer; every thread ANDs its candidates' rank columns with 128-bit shared
+// loads and popcounts. The whole CTA must call this (it synchronises).
+template <int TW, int KRE, int NT>
+__device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32_t g, uint32_t c0,
+                                               uint32_t cn, uint32_t nw32, uint32_t ntiles,
+                                               uint32_t *sm, uint32_t chunk_cap,
+                                               uint32_t &pruned, uint32_t &solid) {
+  constexpr uint32_t ST = bs_stride(TW);
+  constexpr int NV = TW / 4;  // 128-bit loads per rank and tile
+  const uint32_t tile_words = L.l1p * ST;
+  const uint32_t *V = L.V;
+  uint32_t *S0 = sm;
+  uint32_t *S1 = sm + tile_words;
+  uint16_t *rk = reinterpret_cast<uint16_t *>(sm + 2 * tile_words);
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(rk + (size_t)chunk_cap * KRE);
+  uint8_t *kk = reinterpret_cast<uint8_t *>(cnt + chunk_cap);
+  const uint32_t tid = threadIdx.x;
+  __syncthreads();  // shared memory of the previous chunk is free
+  for (uint32_t o = tid * 4; o < tile_words; o += NT * 4) cp_async16(S0 + o, V + o);
+  cp_async_commit();
+  for (uint32_t i = tid; i < cn; i += NT) {
+    const uint32_t c = c0 + i;
+    const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
+    kk[i] = (uint8_t)k;
+    cnt[i] = 0;
+#pragma unroll
+    for (int q = 0; q < KRE; ++q)
+      rk[(size_t)i * KRE + q] = (uint32_t)q < k ? L.cranks[(uint64_t)c * KRMAX + q] : (uint16_t)0;
+  }
+  for (uint32_t t = 0; t < ntiles; ++t) {
+    if (t + 1 < ntiles) {
+      uint32_t *dst = ((t + 1) & 1) ? S1 : S0;
+      const uint32_t *src = V + (size_t)(t + 1) * tile_words;
+      for (uint32_t o = tid * 4; o < tile_words; o += NT * 4) cp_async16(dst + o, src + o);
+    }
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    const uint32_t *S = (t & 1) ? S1 : S0;
+    for (uint32_t i = tid; i < cn; i += NT) {
+      const uint32_t k = kk[i];
+      if (k == 0) continue;
+      const uint16_t *ri = rk + (size_t)i * KRE;
+      uint4 acc[NV];
+      {
+        const uint4 *p = reinterpret_cast<const uint4 *>(S + (uint32_t)ri[0] * ST);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = p[v];
+      }
+      for (uint32_t q = 1; q < k; ++q) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(S + (uint32_t)ri[q] * ST);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const uint4 x = p[v];
+          acc[v].x &= x.x; acc[v].y &= x.y; acc[v].z &= x.z; acc[v].w &= x.w;
+        }
+      }
+      uint32_t sum = 0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        sum += __popc(acc[v].x) + __popc(acc[v].y) + __popc(acc[v].z) + __popc(acc[v].w);
+      cnt[i] += sum;
+    }
+    __syncthreads();  // the buffer of tile t may be overwritten next
+  }
+  unsigned long long work = 0;
+  for (uint32_t i = tid; i < cn; i += NT) {
+    if (!kk[i]) continue;
+    const uint32_t c = c0 + i;
+    const uint32_t s = L.csupp[c] + cnt[i];
+    L.csupp[c] = s;
+    settle_record(L, C, c, s, g, true, pruned, solid);
+    // algorithmic work: k-1 AND + POPC + ADD per 32-row word
+    work += (unsigned long long)(kk[i] + 1) * nw32;
+  }
+  warp_add_u64(&C->work, work);
+}
+
+}  // namespace dic

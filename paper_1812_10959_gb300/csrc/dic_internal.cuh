@@ -49,7 +49,7 @@ struct Ctrl {
   uint32_t n_trace;
   uint32_t blocks_done;  // ticket of the generate kernel's last-block step
   uint32_t last_birth;   // creation stop of the newest cohort
-  uint32_t pad1;
+  uint32_t solo;         // 1: the batched kernels leave this query alone
   unsigned long long tests;  // candidate-transaction tests so far
   unsigned long long work;   // algorithmic integer ops of the count kernels
 };
@@ -145,6 +145,19 @@ size_t bitslice_tile_words(int tw, uint32_t l1p);
 cudaError_t launch_slice_block(Lattice L, cudaStream_t s);
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
                                   uint32_t chunk, uint64_t vwords, int grid, cudaStream_t s);
+// Batched rounds (kernels_batch.cu): one launch per phase for all queries.
+cudaError_t launch_batch_plan(const Lattice *Ls, uint32_t Q, bool finish, uint32_t grid,
+                              uint32_t chunk_cap, uint32_t *item_prefix, uint32_t *chunk,
+                              cudaStream_t s);
+cudaError_t launch_batch_count(const Lattice *Ls, uint32_t Q, int tw, int kre,
+                               const uint32_t *item_prefix, const uint32_t *chunk,
+                               uint32_t smem, int grid, cudaStream_t s);
+cudaError_t launch_batch_plan_gen(const Lattice *Ls, uint32_t Q, uint32_t slice_offset,
+                                  uint64_t *gen_prefix, uint64_t *slice_prefix, cudaStream_t s);
+cudaError_t launch_batch_gen(const Lattice *Ls, uint32_t Q, uint32_t slice_offset,
+                             const uint64_t *gen_prefix, const uint64_t *slice_prefix, int grid,
+                             cudaStream_t s);
+
 // Largest candidate chunk whose bitslice shared-memory footprint fits.
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit);
 size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk);

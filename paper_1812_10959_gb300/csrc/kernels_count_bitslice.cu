@@ -29,6 +29,7 @@
 
 #include "dic_internal.cuh"
 #include "lattice_device.cuh"
+#include "bitslice_device.cuh"
 
 namespace dic {
 
@@ -58,21 +59,6 @@ cudaError_t launch_slice_block(Lattice L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- count
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_1() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-}
-
 size_t bitslice_tile_words(int tw, uint32_t l1p) { return (size_t)l1p * bs_stride(tw); }
 
 size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk) {
@@ -94,36 +80,12 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
                                                                uint32_t l1p, uint32_t chunk_cap,
                                                                uint64_t vwords) {
   extern __shared__ __align__(16) uint32_t sm[];
-  constexpr uint32_t ST = bs_stride(TW);
-  constexpr int NV = TW / 4;  // 128-bit loads per rank and tile
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
-  if (C->max_k > (uint32_t)KRE) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) C->stall = ST_WIDTH;
-    return;
-  }
-  // room in the box set for every live record, checked before any change
-  if ((uint64_t)(C->hash_used + C->n_live) * 2 > L.hcap) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) C->stall = ST_HASH_COUNT;
-    return;
-  }
-  const uint32_t tile_words = l1p * ST;
-  uint32_t *S0 = sm;
-  uint32_t *S1 = sm + tile_words;
-  uint16_t *rk = reinterpret_cast<uint16_t *>(sm + 2 * tile_words);
-  uint32_t *cnt = reinterpret_cast<uint32_t *>(rk + (size_t)chunk_cap * KRE);
-  uint8_t *kk = reinterpret_cast<uint8_t *>(cnt + chunk_cap);
-
+  if (!bs_checks<KRE>(L, C, blockIdx.x == 0)) return;
   const uint32_t g = C->step;
-  uint32_t stop;
-  uint64_t first, last;
-  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
-  const uint32_t nw32 = (uint32_t)((last - first + 31) / 32);
-  const uint32_t ntiles = (nw32 + TW - 1) / TW;
-  if ((uint64_t)ntiles * tile_words > vwords) {  // internal sizing error: record, skip
-    if (threadIdx.x == 0) C->error = DIC_INTERNAL_BOUNDS;
-    return;
-  }
+  uint32_t nw32, ntiles;
+  if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
   const uint32_t head = C->head, tail = C->tail;
   const uint32_t ncand = tail - head;
   // balance the live window over the grid; shared memory holds chunk_cap
@@ -132,74 +94,16 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   if (chunk < 4) chunk = 4;
   if (chunk > chunk_cap) chunk = chunk_cap;
   const uint32_t nchunks = (ncand + chunk - 1) / chunk;
-  const uint32_t tid = threadIdx.x;
   uint32_t pruned = 0, solid = 0;
-
   for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const uint32_t c0 = head + ch * chunk;
     const uint32_t cn = (tail - c0) < chunk ? (tail - c0) : chunk;
-    __syncthreads();  // shared memory of the previous chunk is free
-    for (uint32_t o = tid * 4; o < tile_words; o += BS_THREADS * 4) cp_async16(S0 + o, V + o);
-    cp_async_commit();
-    for (uint32_t i = tid; i < cn; i += BS_THREADS) {
-      const uint32_t c = c0 + i;
-      const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
-      kk[i] = (uint8_t)k;
-      cnt[i] = 0;
-#pragma unroll
-      for (int q = 0; q < KRE; ++q)
-        rk[(size_t)i * KRE + q] = (uint32_t)q < k ? L.cranks[(uint64_t)c * KRMAX + q] : (uint16_t)0;
-    }
-    for (uint32_t t = 0; t < ntiles; ++t) {
-      if (t + 1 < ntiles) {
-        uint32_t *dst = ((t + 1) & 1) ? S1 : S0;
-        const uint32_t *src = V + (size_t)(t + 1) * tile_words;
-        for (uint32_t o = tid * 4; o < tile_words; o += BS_THREADS * 4) cp_async16(dst + o, src + o);
-      }
-      cp_async_commit();
-      cp_async_wait_1();
-      __syncthreads();
-      const uint32_t *S = (t & 1) ? S1 : S0;
-      for (uint32_t i = tid; i < cn; i += BS_THREADS) {
-        const uint32_t k = kk[i];
-        if (k == 0) continue;
-        const uint16_t *ri = rk + (size_t)i * KRE;
-        uint4 acc[NV];
-        {
-          const uint4 *p = reinterpret_cast<const uint4 *>(S + (uint32_t)ri[0] * ST);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) acc[v] = p[v];
-        }
-        for (uint32_t q = 1; q < k; ++q) {
-          const uint4 *p = reinterpret_cast<const uint4 *>(S + (uint32_t)ri[q] * ST);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const uint4 x = p[v];
-            acc[v].x &= x.x; acc[v].y &= x.y; acc[v].z &= x.z; acc[v].w &= x.w;
-          }
-        }
-        uint32_t sum = 0;
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-          sum += __popc(acc[v].x) + __popc(acc[v].y) + __popc(acc[v].z) + __popc(acc[v].w);
-        cnt[i] += sum;
-      }
-      __syncthreads();  // the buffer of tile t may be overwritten next
-    }
-    unsigned long long work = 0;
-    for (uint32_t i = tid; i < cn; i += BS_THREADS) {
-      if (!kk[i]) continue;
-      const uint32_t c = c0 + i;
-      const uint32_t s = L.csupp[c] + cnt[i];
-      L.csupp[c] = s;
-      settle_record(L, C, c, s, g, true, pruned, solid);
-      // algorithmic work: k-1 AND + POPC + ADD per 32-row word
-      work += (unsigned long long)(kk[i] + 1) * nw32;
-    }
-    warp_add_u64(&C->work, work);
+    bs_count_chunk<TW, KRE, BS_THREADS>(L, C, g, c0, cn, nw32, ntiles, sm, chunk_cap, pruned,
+                                        solid);
   }
   if (pruned) atomicAdd(&C->n_pruned, pruned);
   if (solid) atomicAdd(&C->n_solid, solid);
+  (void)V; (void)l1p; (void)vwords;
 }
 
 template <int TW, int KRE>

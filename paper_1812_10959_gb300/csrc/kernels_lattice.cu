@@ -283,40 +283,6 @@ cudaError_t launch_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap, cudaS
 // The last block to finish then closes the stop: trace row, test count,
 // the new cohort, CHECKFULLPASS (cohorts whose full pass is complete leave
 // the window [head, tail)), |DASHED| and the loop test of Algorithm 2.
-__device__ void finish_stop(const Lattice &L, Ctrl *C) {
-  const uint32_t g = C->step;
-  uint32_t stop;
-  uint64_t first, last;
-  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
-  if (C->n_trace >= L.tcap) {
-    C->error = 4;  // DIC_ECAPACITY
-    C->done = 1;
-    return;
-  }
-  unsigned long long *row = L.trace + (uint64_t)C->n_trace * TRACE_COLS;
-  row[0] = g; row[1] = stop; row[2] = first; row[3] = last;
-  row[4] = C->n_live; row[5] = C->n_newbox; row[6] = C->n_pruned; row[7] = C->n_gen;
-  row[8] = C->n_solid;
-  C->tests += (unsigned long long)C->n_live * (last - first);
-  if (C->n_gen) {
-    L.cohort_start[C->n_cohorts] = C->tail;
-    L.cohort_birth[C->n_cohorts] = g;
-    C->n_cohorts += 1;
-    C->last_birth = g;
-  }
-  C->tail += C->n_gen;
-  C->hash_used += C->n_newbox;
-  C->n_live = C->n_live - C->n_pruned - C->n_solid + C->n_gen;
-  uint32_t ch = C->cohort_head;
-  while (ch < C->n_cohorts && L.cohort_birth[ch] + L.stop_max <= g) ++ch;
-  C->cohort_head = ch;
-  C->head = ch < C->n_cohorts ? L.cohort_start[ch] : C->tail;
-  C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->n_gen = 0;
-  C->n_trace += 1;
-  C->step = g + 1;
-  if (C->n_live == 0) C->done = 1;
-}
-
 __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_next) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
@@ -329,47 +295,7 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_ne
   const uint64_t total = (uint64_t)P * l1;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
-    const uint32_t p = (uint32_t)(w / l1), r = (uint32_t)(w % l1);
-    const uint64_t *A = L.cmask + (uint64_t)L.newbox[p] * wc;
-    const uint32_t wr = r >> 6;
-    const uint64_t br = 1ull << (r & 63);
-    const uint64_t Awr = A[wr];
-    if (Awr & br) continue;
-    const uint64_t sumC = L.newhash[p] - hterm(Awr, wr) + hterm(Awr | br, wr);
-    bool ok = true;
-    uint32_t k = 0;
-    for (uint32_t i = 0; i < wc && ok; ++i) {
-      uint64_t x = A[i];
-      const uint64_t Ci = i == wr ? (A[i] | br) : A[i];
-      while (x) {
-        const uint32_t b = (uint32_t)(__ffsll((long long)x) - 1);
-        x &= x - 1;
-        ++k;
-        const uint64_t bj = 1ull << b;
-        const uint64_t sumS = sumC - hterm(Ci, i) + hterm(Ci & ~bj, i);
-        const uint32_t v = box_lookup(L, A, wr, br, i, bj, sumS);
-        if (v == 0 || (i * 64 + b < r && v == g + 1)) { ok = false; break; }
-      }
-    }
-    if (!ok) continue;
-    const uint32_t pos = base + atomicAdd(&C->n_gen, 1u);
-    if (pos >= L.cap) {
-      C->stall = ST_CAND;
-      continue;
-    }
-    uint32_t q = 0;
-    uint16_t *rk = L.cranks + (uint64_t)pos * KRMAX;
-    for (uint32_t i = 0; i < wc; ++i) {
-      const uint64_t x = i == wr ? (A[i] | br) : A[i];
-      L.cmask[(uint64_t)pos * wc + i] = x;
-      for (uint64_t y = x; y && q < KRMAX; y &= y - 1)
-        rk[q++] = (uint16_t)(i * 64 + __ffsll((long long)y) - 1);
-    }
-    L.csupp[pos] = 0;
-    L.cbirth[pos] = g;
-    L.cshape[pos] = SH_CIRCLE;
-    L.ck[pos] = (uint8_t)(k + 1 < 255 ? k + 1 : 255);
-    atomicMax(&C->max_k, k + 1);
+    gen_candidate(L, C, (uint32_t)(w / l1), (uint32_t)(w % l1), g, base);
   }
   // last block closes the stop
   __shared__ bool last;
