@@ -24,10 +24,10 @@ def mixed_queries():
     rng = np.random.default_rng(42)
     for i in range(14):
         m = int(rng.choice([20, 64, 100, 130, 300]))
-        n = int(rng.integers(50, 2500))
+        n = int(rng.integers(300, 2500))
         rp, it = synth.planted(100 + i, n, m, 2 * m, float(rng.uniform(2, 6)),
-                               float(rng.uniform(5, 20)))
-        minsup = max(2, int(n * rng.uniform(0.01, 0.05)))
+                               min(float(rng.uniform(4, 14)), m / 6))
+        minsup = max(6, int(n * rng.uniform(0.02, 0.05)))
         M = int(rng.integers(1, n + 10))
         qs.append((rp, it, n, m, minsup, M))
     qs.append(to_csr([]) + (0, 8, 1, 3))                 # empty database
