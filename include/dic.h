@@ -170,6 +170,40 @@ dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint64_t M,
 dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *minsup, const uint64_t *M,
                           uint32_t count, const dic_options *opt, dic_result **out);
 
+/* -------------------------------------------------------------- serving */
+
+/* A request server with continuous batching. Queries submitted from any
+ * thread wait in arrival order; at every group boundary (a few stops) the
+ * server admits waiting queries while a slot is free and their estimated
+ * device footprint fits `hbm_budget_bytes`; all admitted queries advance one
+ * stop of Algorithm 2 per round through launches shared by all of them, and
+ * a query that finishes frees its slot and memory immediately. Results are
+ * exactly those of dic_mine. The databases must outlive their queries. */
+typedef struct dic_server dic_server;
+typedef struct {
+  uint64_t submitted, completed;
+  uint64_t rounds;          /* batched rounds run                           */
+  uint32_t peak_slots;      /* most queries advanced together               */
+  uint32_t reserved0;
+  uint64_t peak_bytes;      /* largest estimated footprint admitted at once */
+  double p50_ms, p99_ms, mean_ms;  /* submit-to-result latency              */
+  double qps;               /* completed / (last completion - first submit) */
+  uint32_t reserved[8];
+} dic_server_metrics;
+
+dic_status dic_server_create(uint64_t hbm_budget_bytes, uint32_t max_slots,
+                             const dic_options *opt, dic_server **out);
+/* Enqueue a query; *ticket identifies it for dic_server_wait. */
+dic_status dic_server_submit(dic_server *srv, const dic_db *db, uint32_t minsup_count, uint64_t M,
+                             uint64_t *ticket);
+/* Wait for a ticket (timeout_ms < 0: no limit; DIC_ETIMEOUT otherwise) and
+ * take its result (or the query's error). A ticket can be waited once. */
+dic_status dic_server_wait(dic_server *srv, uint64_t ticket, int64_t timeout_ms,
+                           dic_result **out);
+dic_status dic_server_stats(dic_server *srv, dic_server_metrics *out);
+/* Finish every submitted query, then stop the worker and free everything. */
+dic_status dic_server_destroy(dic_server *srv);
+
 /* ------------------------------------------------------------- results */
 
 /* Number of frequent itemsets (1-itemsets included). */

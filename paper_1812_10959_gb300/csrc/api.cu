@@ -10,6 +10,11 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1155,6 +1160,368 @@ extern "C" dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *m
   cudaStreamDestroy(s);
   if (prev != dbs[0]->device) cudaSetDevice(prev);
   return st;
+}
+
+
+// ------------------------------------------------------------- request server
+// Continuous batching of mining queries. A worker thread owns a stream and a
+// table of slots; requests wait in arrival order and are admitted at every
+// group boundary while a slot is free and their estimated device footprint
+// fits the HBM budget. Admitted queries run their first pass and setup, then
+// join the active slots, which all advance one stop per round through the
+// batched kernels (one launch per phase for every slot); a query that
+// finishes completes its ticket and frees its slot and memory at once.
+namespace {
+
+struct ServerRequest {
+  uint64_t ticket = 0;
+  const dic_db *db = nullptr;
+  uint32_t minsup = 0;
+  uint64_t M = 0;
+  uint64_t est_bytes = 0;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  dic_result *result = nullptr;
+  dic_status status = DIC_OK;
+  std::string error;
+  bool done = false;
+};
+
+// Upper bound of a query's device footprint before its first pass (all m
+// items taken as frequent).
+uint64_t estimate_bytes(const dic_db *db, uint64_t M) {
+  const uint64_t m = db->m, W = db->W, n = db->n;
+  const uint64_t pairs = m * (m - 1) / 2;
+  const uint64_t cap = pairs + pairs / 8 + 4096;
+  const uint64_t record = W * 8 + 4 + 4 + 1 + 1 + 2 * KRMAX + 4 + 4 + 8;
+  uint64_t hcap = 4096;
+  while (hcap < pairs * 4) hcap *= 2;
+  const uint64_t block = std::min<uint64_t>(M, n ? n : 1);
+  const uint64_t vbytes = ((block + 31) / 32 / 16 + 1) * 16 * ((m + 3) & ~3ull) * 20 * 4;
+  return n * W * 8 + cap * record + hcap * 4 + vbytes + (1u << 20);
+}
+
+}  // namespace
+
+struct dic_server {
+  uint64_t budget = 0;
+  uint32_t max_slots = 0;
+  dic_options opt{};
+  int device = 0;
+  int tw = 16;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<ServerRequest>> pending;
+  std::unordered_map<uint64_t, std::shared_ptr<ServerRequest>> tickets;
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+  std::thread worker;
+  // statistics (under mu)
+  std::vector<double> lat_ms;
+  uint64_t submitted = 0, completed = 0, rejected = 0, rounds = 0;
+  uint32_t peak_slots = 0;
+  uint64_t used_bytes = 0, peak_bytes = 0;
+  bool have_first = false;
+  std::chrono::steady_clock::time_point t_first, t_last;
+  std::string fatal;
+  // worker-owned device state
+  cudaStream_t s = nullptr;
+  Ctrl *d_ctrls = nullptr, *h_ctrls = nullptr;
+  Lattice *d_Ls = nullptr, *h_Ls = nullptr;
+  uint32_t *d_items = nullptr, *d_chunk = nullptr;
+  uint64_t *d_gen = nullptr, *d_slice = nullptr;
+  std::vector<std::unique_ptr<Miner>> miner;
+  std::vector<std::shared_ptr<ServerRequest>> req;
+};
+
+namespace {
+
+void server_complete(dic_server *sv, uint32_t slot, dic_status st) {
+  std::shared_ptr<ServerRequest> r = sv->req[slot];
+  dic_result *res = nullptr;
+  if (st == DIC_OK) st = sv->miner[slot]->collect(&res);
+  std::string err = st == DIC_OK ? std::string() : std::string(dic_last_error());
+  sv->miner[slot].reset();  // buffers released on the stream
+  sv->req[slot].reset();
+  sv->h_ctrls[slot] = Ctrl{};
+  sv->h_ctrls[slot].done = 1;
+  cudaMemcpyAsync(sv->d_ctrls + slot, sv->h_ctrls + slot, sizeof(Ctrl), cudaMemcpyHostToDevice,
+                  sv->s);
+  const_cast<dic_db *>(r->db)->busy.fetch_sub(1);
+  std::lock_guard<std::mutex> lk(sv->mu);
+  r->done = true;
+  r->status = st;
+  r->error = err;
+  r->result = res;
+  r->t_done = std::chrono::steady_clock::now();
+  sv->used_bytes -= r->est_bytes;
+  sv->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+  ++sv->completed;
+  sv->t_last = r->t_done;
+  sv->cv_done.notify_all();
+}
+
+dic_status server_upload(dic_server *sv) {
+  for (uint32_t q = 0; q < sv->max_slots; ++q) {
+    sv->h_Ls[q] = sv->miner[q] && sv->miner[q]->has_loop() ? sv->miner[q]->lattice() : Lattice{};
+    sv->h_Ls[q].ctrl = sv->d_ctrls + q;
+  }
+  CU(cudaMemcpyAsync(sv->d_Ls, sv->h_Ls, (size_t)sv->max_slots * sizeof(Lattice),
+                     cudaMemcpyHostToDevice, sv->s));
+  return DIC_OK;
+}
+
+// One pass of the worker: admit, set up, run a group of rounds, retire.
+dic_status server_step(dic_server *sv, const std::vector<std::shared_ptr<ServerRequest>> &adm,
+                       const std::vector<uint32_t> &slots) {
+  const uint32_t Q = sv->max_slots;
+  // setup of newly admitted queries: first passes together, one sync
+  for (size_t i = 0; i < adm.size(); ++i) {
+    const uint32_t q = slots[i];
+    sv->req[q] = adm[i];
+    sv->miner[q].reset(new Miner(adm[i]->db, adm[i]->minsup, adm[i]->M, sv->opt, sv->s));
+    sv->miner[q]->use_external_ctrl(sv->d_ctrls + q, sv->h_ctrls + q);
+    dic_status st = sv->miner[q]->begin();
+    if (st != DIC_OK) { server_complete(sv, q, st); continue; }
+  }
+  if (!adm.empty()) CU(cudaStreamSynchronize(sv->s));
+  for (size_t i = 0; i < adm.size(); ++i) {
+    const uint32_t q = slots[i];
+    if (!sv->miner[q]) continue;
+    dic_status st = sv->miner[q]->prepare();
+    if (st != DIC_OK || !sv->miner[q]->has_loop()) { server_complete(sv, q, st); continue; }
+    bool ok = false;
+    st = sv->miner[q]->set_tile_width(sv->tw, &ok);
+    if (st == DIC_OK && !ok) st = sv->miner[q]->loop();  // cannot join the batch
+    if (st != DIC_OK || !ok) { server_complete(sv, q, st); continue; }
+  }
+  uint32_t max_k = 2, group = 0, max_l1p = 4, active = 0;
+  const uint32_t group_cap = sv->opt.steps_per_sync ? sv->opt.steps_per_sync : 8;
+  for (uint32_t q = 0; q < Q; ++q) {
+    if (!sv->miner[q]) continue;
+    const Ctrl &c = sv->h_ctrls[q];
+    if (c.done) { server_complete(sv, q, DIC_OK); continue; }
+    if (c.max_k > (uint32_t)KRMAX) {  // outgrew the batched count: finish alone
+      server_complete(sv, q, sv->miner[q]->loop());
+      continue;
+    }
+    ++active;
+    max_k = std::max(max_k, c.max_k);
+    max_l1p = std::max(max_l1p, sv->miner[q]->l1p());
+    group = std::max(group, stops_needed(c, sv->miner[q]->lattice().stop_max, group_cap));
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->peak_slots = std::max(sv->peak_slots, active);
+  }
+  if (active == 0) return DIC_OK;
+  for (uint32_t q = 0; q < Q; ++q)
+    if (sv->miner[q]) TRY(sv->miner[q]->reserve(group));
+  TRY(server_upload(sv));
+  int dev = 0, optin = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int kre = kr_bucket(std::max<uint32_t>(max_k, 4));
+  const uint32_t chunk_cap = bitslice_max_chunk(sv->tw, kre, max_l1p, (size_t)optin);
+  const uint32_t smem = (uint32_t)bitslice_smem(sv->tw, kre, max_l1p, chunk_cap);
+  // bit columns of every active query's current stop (cheap; covers the
+  // newly admitted and any recovered query), then the plan
+  CU(launch_batch_plan_gen(sv->d_Ls, Q, 0, sv->d_gen, sv->d_slice, sv->s));
+  CU(launch_batch_gen(sv->d_Ls, Q, 0, sv->d_gen, sv->d_slice, sms * 4, sv->s));
+  CU(launch_batch_plan(sv->d_Ls, Q, false, sms, chunk_cap, sv->d_items, sv->d_chunk, sv->s));
+  for (uint32_t r = 0; r < group; ++r) {
+    CU(launch_batch_count(sv->d_Ls, Q, sv->tw, kre, sv->d_items, sv->d_chunk, smem, sms, sv->s));
+    CU(launch_batch_plan_gen(sv->d_Ls, Q, 1, sv->d_gen, sv->d_slice, sv->s));
+    CU(launch_batch_gen(sv->d_Ls, Q, 1, sv->d_gen, sv->d_slice, sms * 4, sv->s));
+    CU(launch_batch_plan(sv->d_Ls, Q, true, sms, chunk_cap, sv->d_items, sv->d_chunk, sv->s));
+  }
+  CU(cudaMemcpyAsync(sv->h_ctrls, sv->d_ctrls, (size_t)Q * sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                     sv->s));
+  CU(cudaStreamSynchronize(sv->s));
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->rounds += group;
+  }
+  for (uint32_t q = 0; q < Q; ++q) {
+    if (!sv->miner[q]) continue;
+    const Ctrl &c = sv->h_ctrls[q];
+    if (c.error || c.stall) {
+      dic_status st = sv->miner[q]->recover();
+      if (st != DIC_OK) { server_complete(sv, q, st); continue; }
+    }
+    if (sv->h_ctrls[q].done) server_complete(sv, q, DIC_OK);
+  }
+  return DIC_OK;
+}
+
+void server_main(dic_server *sv) {
+  cudaSetDevice(sv->device);
+  const uint32_t Q = sv->max_slots;
+  for (;;) {
+    std::vector<std::shared_ptr<ServerRequest>> adm;
+    std::vector<uint32_t> slots;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      bool any_active = false;
+      for (uint32_t q = 0; q < Q; ++q) any_active |= (bool)sv->miner[q];
+      if (!any_active)
+        sv->cv_work.wait(lk, [&] { return sv->stopping || !sv->pending.empty(); });
+      if (sv->stopping && sv->pending.empty() && !any_active) return;
+      std::vector<uint32_t> free_slots;
+      for (uint32_t q = 0; q < Q; ++q)
+        if (!sv->miner[q]) free_slots.push_back(q);
+      size_t f = 0;
+      while (!sv->pending.empty() && f < free_slots.size()) {
+        std::shared_ptr<ServerRequest> r = sv->pending.front();
+        const bool alone = !any_active && adm.empty();
+        if (sv->used_bytes + r->est_bytes > sv->budget && !alone) break;  // wait for memory
+        sv->pending.pop_front();
+        sv->used_bytes += r->est_bytes;
+        sv->peak_bytes = std::max(sv->peak_bytes, sv->used_bytes);
+        adm.push_back(r);
+        slots.push_back(free_slots[f++]);
+      }
+    }
+    dic_status st = server_step(sv, adm, slots);
+    if (st != DIC_OK) {  // device failure: fail every query in flight
+      std::string err = dic_last_error();
+      for (uint32_t q = 0; q < Q; ++q)
+        if (sv->miner[q]) server_complete(sv, q, st);
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->fatal = err;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" dic_status dic_server_create(uint64_t hbm_budget_bytes, uint32_t max_slots,
+                                        const dic_options *opt, dic_server **out) {
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_slots == 0 || max_slots > 65536) return fail(DIC_EINVAL, "max_slots must be 1..65536");
+  if (hbm_budget_bytes == 0) return fail(DIC_EINVAL, "hbm budget must be > 0");
+  std::unique_ptr<dic_server> sv(new (std::nothrow) dic_server());
+  if (!sv) return fail(DIC_ENOMEM, "host allocation");
+  sv->budget = hbm_budget_bytes;
+  sv->max_slots = max_slots;
+  dic_options_init(&sv->opt);
+  if (opt) std::memcpy(&sv->opt, opt, std::min<size_t>(sizeof sv->opt, opt->struct_size ? opt->struct_size : sizeof sv->opt));
+  cudaGetDevice(&sv->device);
+  init_pool(sv->device);
+  CU(cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking));
+  CU(cudaMallocHost((void **)&sv->h_ctrls, (size_t)max_slots * sizeof(Ctrl)));
+  CU(cudaMallocHost((void **)&sv->h_Ls, (size_t)max_slots * sizeof(Lattice)));
+  CU(cudaMalloc(&sv->d_ctrls, (size_t)max_slots * sizeof(Ctrl)));
+  CU(cudaMalloc(&sv->d_Ls, (size_t)max_slots * sizeof(Lattice)));
+  CU(cudaMalloc(&sv->d_items, ((size_t)max_slots + 1) * 4));
+  CU(cudaMalloc(&sv->d_chunk, 16));
+  CU(cudaMalloc(&sv->d_gen, ((size_t)max_slots + 1) * 8));
+  CU(cudaMalloc(&sv->d_slice, ((size_t)max_slots + 1) * 8));
+  for (uint32_t q = 0; q < max_slots; ++q) {
+    sv->h_ctrls[q] = Ctrl{};
+    sv->h_ctrls[q].done = 1;
+  }
+  CU(cudaMemcpy(sv->d_ctrls, sv->h_ctrls, (size_t)max_slots * sizeof(Ctrl),
+                cudaMemcpyHostToDevice));
+  sv->miner.resize(max_slots);
+  sv->req.resize(max_slots);
+  dic_server *p = sv.release();
+  p->worker = std::thread(server_main, p);
+  *out = p;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_server_submit(dic_server *sv, const dic_db *db, uint32_t minsup_count,
+                                        uint64_t M, uint64_t *ticket) {
+  if (!sv || !db || !ticket) return fail(DIC_EINVAL, "NULL argument");
+  if (minsup_count == 0 || M == 0) return fail(DIC_EINVAL, "minsup_count and M must be >= 1");
+  if (db->device != sv->device) return fail(DIC_EINVAL, "database on another device");
+  std::shared_ptr<ServerRequest> r(new ServerRequest());
+  r->db = db;
+  r->minsup = minsup_count;
+  r->M = M;
+  r->est_bytes = estimate_bytes(db, M);
+  r->t_submit = std::chrono::steady_clock::now();
+  const_cast<dic_db *>(db)->busy.fetch_add(1);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stopping) {
+      const_cast<dic_db *>(db)->busy.fetch_sub(1);
+      return fail(DIC_EBUSY, "server is shutting down");
+    }
+    r->ticket = sv->next_ticket++;
+    sv->tickets[r->ticket] = r;
+    sv->pending.push_back(r);
+    ++sv->submitted;
+    if (!sv->have_first) { sv->have_first = true; sv->t_first = r->t_submit; }
+  }
+  sv->cv_work.notify_one();
+  *ticket = r->ticket;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_server_wait(dic_server *sv, uint64_t ticket, int64_t timeout_ms,
+                                      dic_result **out) {
+  if (!sv || !out) return fail(DIC_EINVAL, "NULL argument");
+  *out = nullptr;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->tickets.find(ticket);
+  if (it == sv->tickets.end()) return fail(DIC_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  std::shared_ptr<ServerRequest> r = it->second;
+  auto ready = [&] { return r->done; };
+  if (timeout_ms < 0) sv->cv_done.wait(lk, ready);
+  else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+    return fail(DIC_ETIMEOUT, "ticket %llu not finished", (unsigned long long)ticket);
+  sv->tickets.erase(ticket);
+  if (r->status != DIC_OK) return fail(r->status, "%s", r->error.c_str());
+  *out = r->result;
+  r->result = nullptr;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_server_stats(dic_server *sv, dic_server_metrics *out) {
+  if (!sv || !out) return fail(DIC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  std::memset(out, 0, sizeof *out);
+  out->submitted = sv->submitted;
+  out->completed = sv->completed;
+  out->rounds = sv->rounds;
+  out->peak_slots = sv->peak_slots;
+  out->peak_bytes = sv->peak_bytes;
+  std::vector<double> v = sv->lat_ms;
+  if (!v.empty()) {
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) { return v[std::min<size_t>(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    double sum = 0;
+    for (double x : v) sum += x;
+    out->mean_ms = sum / v.size();
+  }
+  if (sv->completed && sv->have_first) {
+    const double secs = std::chrono::duration<double>(sv->t_last - sv->t_first).count();
+    out->qps = secs > 0 ? sv->completed / secs : 0;
+  }
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_server_destroy(dic_server *sv) {
+  if (!sv) return DIC_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stopping = true;
+  }
+  sv->cv_work.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  for (auto &kv : sv->tickets) dic_result_free(kv.second->result);
+  cudaStreamSynchronize(sv->s);
+  cudaFree(sv->d_ctrls); cudaFree(sv->d_Ls); cudaFree(sv->d_items); cudaFree(sv->d_chunk);
+  cudaFree(sv->d_gen); cudaFree(sv->d_slice);
+  cudaFreeHost(sv->h_ctrls); cudaFreeHost(sv->h_Ls);
+  cudaStreamDestroy(sv->s);
+  delete sv;
+  return DIC_OK;
 }
 
 // ----------------------------------------------------------------- results

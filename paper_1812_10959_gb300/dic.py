@@ -48,6 +48,18 @@ class Stats(ctypes.Structure):
         return d
 
 
+class ServerMetrics(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("peak_slots", ctypes.c_uint32),
+                ("reserved0", ctypes.c_uint32), ("peak_bytes", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("qps", ctypes.c_double),
+                ("reserved", ctypes.c_uint32 * 8)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libdic.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -77,6 +89,11 @@ def _load():
         "dic_status_str": ([i32], ctypes.c_char_p),
         "dic_last_error": ([], ctypes.c_char_p),
         "dic_abi_version": ([], u32),
+        "dic_server_create": ([u64, u32, ctypes.POINTER(Options), pvp], i32),
+        "dic_server_submit": ([vp, vp, u32, u64, ctypes.POINTER(u64)], i32),
+        "dic_server_wait": ([vp, u64, ctypes.c_int64, pvp], i32),
+        "dic_server_stats": ([vp, ctypes.POINTER(ServerMetrics)], i32),
+        "dic_server_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -249,3 +266,43 @@ def mine_batch(dbs, minsups, Ms, path: str = "auto", profile: bool = False):
 
 def minsup_count(n: int, frac: float) -> int:
     return _lib.dic_minsup_count(n, frac)
+
+
+class Server:
+    """Continuous-batching request server (dic_server_*): submit queries from
+    any thread, wait for their results by ticket."""
+
+    def __init__(self, hbm_budget_bytes: int = 120 << 30, max_slots: int = 64,
+                 path: str = "auto", steps_per_sync: int = 0):
+        o = options(path, steps_per_sync)
+        h = ctypes.c_void_p()
+        _check(_lib.dic_server_create(hbm_budget_bytes, max_slots, ctypes.byref(o),
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, db: Database, minsup: int, M: int) -> int:
+        t = ctypes.c_uint64()
+        _check(_lib.dic_server_submit(self._h, db.handle, minsup, M, ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> Result:
+        h = ctypes.c_void_p()
+        _check(_lib.dic_server_wait(self._h, ticket, timeout_ms, ctypes.byref(h)))
+        return _result(h)
+
+    def stats(self) -> dict:
+        m = ServerMetrics()
+        _check(_lib.dic_server_stats(self._h, ctypes.byref(m)))
+        return m.as_dict()
+
+    def close(self):
+        if self._h:
+            _check(_lib.dic_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib.dic_server_destroy(self._h)
+        except Exception:
+            pass
