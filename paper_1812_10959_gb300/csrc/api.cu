@@ -333,6 +333,7 @@ class Miner {
   std::vector<void *> bufs_;
   std::vector<cudaEvent_t> ev_pool_;   // profiling events, reused every group
   size_t ev_used_ = 0;
+  std::vector<std::pair<size_t, size_t>> gram_events_;  // (start, end) pool indices
   double count_ms_ = 0;
   uint64_t count_timed_ = 0;
   Lattice L_{};
@@ -348,6 +349,14 @@ class Miner {
   size_t smem_optin_ = 0;
   int cur_path_ = DIC_COUNT_ROWS;
   bool next_v_ready_ = false;  // the enqueued work builds V for the next count
+  // TENSOR path (pair cohort on tcgen05)
+  bool tc_ok_ = false;
+  uint8_t *tc_X_ = nullptr;
+  uint64_t tc_xbytes_ = 0;
+  uint32_t tc_nkc_max_ = 0, tc_nsplit_ = 1;
+  uint32_t pred_step_ = 1;     // stop number the next enqueued count runs at
+  double gram_ms_ = 0;
+  uint64_t gram_timed_ = 0;
   int grid_ = 0;
   uint32_t launches_ = 0;
   uint32_t path_launches_[4] = {0, 0, 0, 0};
@@ -372,7 +381,7 @@ class Miner {
 int Miner::count_path_for_stop() const {
   if (opt_.count_path == DIC_COUNT_ROWS) return DIC_COUNT_ROWS;
   if (!bs_ok_ || h_ctrl_->max_k > (uint32_t)KRMAX) return DIC_COUNT_ROWS;
-  return DIC_COUNT_BITSLICE;
+  return tc_ok_ ? DIC_COUNT_TENSOR : DIC_COUNT_BITSLICE;
 }
 
 static int kr_bucket(uint32_t max_k) {
@@ -395,11 +404,24 @@ dic_status Miner::next_event(cudaEvent_t *ev) {
 // Sum the count-kernel event pairs recorded since the last group (the
 // stream has been synchronised).
 dic_status Miner::harvest_events() {
-  for (size_t i = 0; i + 1 < ev_used_; i += 2) {
+  std::vector<bool> is_gram(ev_used_, false);
+  for (auto &ge : gram_events_) {
     float ms = 0;
-    CU(cudaEventElapsedTime(&ms, ev_pool_[i], ev_pool_[i + 1]));
+    CU(cudaEventElapsedTime(&ms, ev_pool_[ge.first], ev_pool_[ge.second]));
+    gram_ms_ += ms;
+    ++gram_timed_;
+    is_gram[ge.first] = is_gram[ge.second] = true;
+  }
+  gram_events_.clear();
+  size_t first = SIZE_MAX;
+  for (size_t i = 0; i < ev_used_; ++i) {
+    if (is_gram[i]) continue;
+    if (first == SIZE_MAX) { first = i; continue; }
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, ev_pool_[first], ev_pool_[i]));
     count_ms_ += ms;
     ++count_timed_;
+    first = SIZE_MAX;
   }
   ev_used_ = 0;
   return DIC_OK;
@@ -417,7 +439,7 @@ dic_status Miner::launch_phase(int phase) {
   switch (phase) {
     case PH_COUNT: {
       cudaEvent_t a = nullptr, b = nullptr;
-      if (cur_path_ == DIC_COUNT_BITSLICE) {
+      if (cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR) {
         // shared memory for the largest chunk that fits; the kernel sizes its
         // chunk from the live window
         const int kre = kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4));
@@ -428,6 +450,24 @@ dic_status Miner::launch_phase(int phase) {
           ++launches_;
         }
         next_v_ready_ = false;
+        if (e == cudaSuccess && cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max) {
+          // the pair cohort on the tensor cores (it is in DASHED up to stop_max)
+          cudaEvent_t ga = nullptr, gb = nullptr;
+          if (opt_.profile) {
+            TRY(next_event(&ga));
+            CU(cudaEventRecord(ga, s_));
+          }
+          e = launch_gram_operand(L_, tc_X_, tc_nkc_max_, tc_xbytes_, (uint32_t)kre, s_);
+          if (e == cudaSuccess)
+            e = launch_gram_pairs(L_, tc_X_, tc_nkc_max_, tc_nsplit_, (uint32_t)kre, s_);
+          launches_ += 2;
+          path_launches_[DIC_COUNT_TENSOR]++;
+          if (opt_.profile && e == cudaSuccess) {
+            TRY(next_event(&gb));
+            CU(cudaEventRecord(gb, s_));
+            gram_events_.push_back({ev_used_ - 2, ev_used_ - 1});
+          }
+        }
         if (e == cudaSuccess) {
           if (opt_.profile) {
             TRY(next_event(&a));
@@ -452,10 +492,13 @@ dic_status Miner::launch_phase(int phase) {
     }
     case PH_PROMOTE: e = launch_promote(L_, grid_, s_); break;
     case PH_HASH: e = launch_hash_insert(L_, grid_, s_); break;
-    case PH_GEN:
-      e = launch_generate_finish(L_, grid_, cur_path_ == DIC_COUNT_BITSLICE, s_);
-      next_v_ready_ = cur_path_ == DIC_COUNT_BITSLICE;
+    case PH_GEN: {
+      const bool slice = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
+      e = launch_generate_finish(L_, grid_, slice, s_);
+      next_v_ready_ = slice;
+      ++pred_step_;
       break;
+    }
   }
   ++launches_;
   if (e != cudaSuccess) return fail(DIC_ECUDA, "kernel launch (phase %d): %s", phase,
@@ -701,6 +744,25 @@ dic_status Miner::prepare() {
         bs_grid_ = sm_count();
       }
     }
+    // ---- TENSOR path for the pair cohort: needs the BITSLICE path for the
+    // rest, a block below 2^24 rows (exact fp32 sums), and enough pairs to
+    // fill a tile (AUTO) or an explicit request
+    {
+      const uint64_t blockmax = std::min<uint64_t>(M_, n);
+      const bool want = opt_.count_path == DIC_COUNT_TENSOR ||
+                        (opt_.count_path == DIC_COUNT_AUTO && l1 >= 256 && blockmax >= 2048);
+      tc_ok_ = false;
+      if (want && bs_ok_ && blockmax < (1ull << 24) && npairs <= 0xFFFFFFF0ull) {
+        tc_nkc_max_ = gram_chunks(blockmax);
+        tc_xbytes_ = gram_operand_bytes(l1, blockmax);
+        TRY(alloc(&tc_X_, tc_xbytes_, true));
+        const uint32_t nt = gram_tiles(l1), ntp = nt * (nt + 1) / 2;
+        const uint32_t sms = (uint32_t)sm_count();
+        tc_nsplit_ = std::max<uint32_t>(1, std::min<uint32_t>(tc_nkc_max_, (sms + ntp - 1) / ntp));
+        L_.pair_end = (uint32_t)npairs;
+        tc_ok_ = true;
+      }
+    }
 
     has_loop_ = true;
   }
@@ -724,6 +786,9 @@ dic_status Miner::reserve(uint32_t stops) {
 
 dic_status Miner::set_tile_width(int tw, bool *ok) {
   *ok = false;
+  // the batched kernels count every record themselves
+  tc_ok_ = false;
+  L_.pair_end = 0;
   if (!bs_ok_) return DIC_OK;
   if (tw == bs_tw_) { *ok = true; return DIC_OK; }
   if (bitslice_max_chunk(tw, 16, bs_l1p_, smem_optin_) < 1024) return DIC_OK;
@@ -768,6 +833,7 @@ dic_status Miner::recover() {
       return fail(DIC_ECUDA, "unknown stall code %u", st);
     }
     if (phase == PH_COUNT) next_v_ready_ = false;
+    pred_step_ = h_ctrl_->step;
     h_ctrl_->stall = ST_NONE;
     h_ctrl_->blocks_done = 0;
     CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
@@ -790,6 +856,7 @@ dic_status Miner::loop() {
     int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
     nw_ = bucket ? (uint32_t)bucket : 0;
     cur_path_ = count_path_for_stop();
+    pred_step_ = h_ctrl_->step;
     for (uint32_t i = 0; i < group; ++i) TRY(launch_stop_from(PH_COUNT));
     TRY(sync_ctrl());
     TRY(recover());
@@ -877,6 +944,8 @@ dic_status Miner::collect(dic_result **out) {
   if (opt_.profile) {
     res->stats.count_ms = count_ms_;
     res->stats.count_launches = count_timed_;
+    res->stats.gram_ms = gram_ms_;
+    res->stats.gram_launches = gram_timed_;
   }
   release();
   cudaError_t e = cudaStreamSynchronize(s_);

@@ -21,6 +21,9 @@ __device__ __forceinline__ void cp_async_wait_1() {
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
+// Marker in the per-chunk size array for a record counted elsewhere.
+constexpr uint8_t KSKIP = 255;
+
 // Checks a count launch makes before changing anything for a query: every
 // dashed itemset fits KRE ranks, and the box set has room for every live
 // record to be promoted. Reads only values no count kernel changes, so all
@@ -74,19 +77,25 @@ __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32
   uint32_t *cnt = reinterpret_cast<uint32_t *>(rk + (size_t)chunk_cap * KRE);
   uint8_t *kk = reinterpret_cast<uint8_t *>(cnt + chunk_cap);
   const uint32_t tid = threadIdx.x;
+  // records below `skip` (the pair cohort while the tensor path counts it)
+  // already have this stop's count: only PRUNE is applied to them
+  const uint32_t skip = (L.pair_end && g <= L.stop_max) ? L.pair_end : 0u;
+  const bool need_tiles = c0 + cn > skip;  // uniform over the CTA
   __syncthreads();  // shared memory of the previous chunk is free
-  for (uint32_t o = tid * 4; o < tile_words; o += NT * 4) cp_async16(S0 + o, V + o);
-  cp_async_commit();
+  if (need_tiles) {
+    for (uint32_t o = tid * 4; o < tile_words; o += NT * 4) cp_async16(S0 + o, V + o);
+    cp_async_commit();
+  }
   for (uint32_t i = tid; i < cn; i += NT) {
     const uint32_t c = c0 + i;
     const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
-    kk[i] = (uint8_t)k;
+    kk[i] = (uint8_t)(k && c < skip ? KSKIP : k);
     cnt[i] = 0;
 #pragma unroll
     for (int q = 0; q < KRE; ++q)
       rk[(size_t)i * KRE + q] = (uint32_t)q < k ? L.cranks[(uint64_t)c * KRMAX + q] : (uint16_t)0;
   }
-  for (uint32_t t = 0; t < ntiles; ++t) {
+  for (uint32_t t = 0; need_tiles && t < ntiles; ++t) {
     if (t + 1 < ntiles) {
       uint32_t *dst = ((t + 1) & 1) ? S1 : S0;
       const uint32_t *src = V + (size_t)(t + 1) * tile_words;
@@ -98,7 +107,7 @@ __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32
     const uint32_t *S = (t & 1) ? S1 : S0;
     for (uint32_t i = tid; i < cn; i += NT) {
       const uint32_t k = kk[i];
-      if (k == 0) continue;
+      if (k == 0 || k == KSKIP) continue;
       const uint16_t *ri = rk + (size_t)i * KRE;
       uint4 acc[NV];
       {
@@ -126,6 +135,10 @@ __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32
   for (uint32_t i = tid; i < cn; i += NT) {
     if (!kk[i]) continue;
     const uint32_t c = c0 + i;
+    if (kk[i] == KSKIP) {
+      settle_record(L, C, c, L.csupp[c], g, true, pruned, solid);
+      continue;
+    }
     const uint32_t s = L.csupp[c] + cnt[i];
     L.csupp[c] = s;
     settle_record(L, C, c, s, g, true, pruned, solid);

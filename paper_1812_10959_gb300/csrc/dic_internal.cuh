@@ -96,6 +96,10 @@ struct Lattice {
   uint64_t vwords;
   uint32_t tw;
   uint32_t l1p;
+  // records [0, pair_end) (the pair cohort) are counted by the tensor path
+  // while it is live; 0 when that path is off
+  uint32_t pair_end;
+  uint32_t pad2;
 };
 
 // Block [first, last) of global stop g (1-based), with rewind (Algorithm 2).
@@ -157,6 +161,17 @@ cudaError_t launch_batch_plan_gen(const Lattice *Ls, uint32_t Q, uint32_t slice_
 cudaError_t launch_batch_gen(const Lattice *Ls, uint32_t Q, uint32_t slice_offset,
                              const uint64_t *gen_prefix, const uint64_t *slice_prefix, int grid,
                              cudaStream_t s);
+
+// TENSOR path for the pair cohort (kernels_count_tensor.cu).
+uint32_t gram_tiles(uint32_t l1);
+uint32_t gram_chunks(uint64_t rows);
+uint64_t gram_operand_bytes(uint32_t l1, uint64_t block_rows);
+// Both do nothing when the BITSLICE count of the same stop (kre ranks) will
+// stall, so a re-run stop never counts its pairs twice.
+cudaError_t launch_gram_operand(Lattice L, uint8_t *X, uint32_t nkc_max, uint64_t xbytes,
+                                uint32_t kre, cudaStream_t s);
+cudaError_t launch_gram_pairs(Lattice L, const uint8_t *X, uint32_t nkc_max, uint32_t nsplit,
+                              uint32_t kre, cudaStream_t s);
 
 // Largest candidate chunk whose bitslice shared-memory footprint fits.
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit);

@@ -40,7 +40,8 @@ class Stats(ctypes.Structure):
                 ("count_ms", ctypes.c_double), ("count_launches", ctypes.c_uint64),
                 ("firstpass_ms", ctypes.c_double), ("mine_ms", ctypes.c_double),
                 ("path_launches", ctypes.c_uint32 * 4), ("count_ops", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("gram_ms", ctypes.c_double), ("gram_launches", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint32 * 2)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "path_launches")}

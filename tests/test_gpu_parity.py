@@ -12,7 +12,7 @@ from golden_io import hand_examples, to_csr
 from gpu_util import packbits_rows
 
 pytestmark = pytest.mark.gpu
-PATHS = ["rows", "bitslice", "auto"]
+PATHS = ["rows", "bitslice", "tensor", "auto"]
 
 
 @pytest.fixture(scope="module")
@@ -176,10 +176,12 @@ def test_paths_agree_on_wide_frequent_items(dic):
         rows.append(r)
     rp, it = to_csr(rows)
     db = dic.load_db_csr(rp, it, n, m)
-    out = {path: dic.mine(db, minsup, 700, path=path) for path in ("rows", "bitslice", "auto")}
+    out = {path: dic.mine(db, minsup, 700, path=path)
+           for path in ("rows", "bitslice", "tensor", "auto")}
     db.free()
     got = out["rows"].itemsets()
-    assert got == out["bitslice"].itemsets() == out["auto"].itemsets()
+    assert got == out["bitslice"].itemsets() == out["tensor"].itemsets() == out["auto"].itemsets()
+    assert out["tensor"].stats["path_launches"][3] > 0
     assert out["bitslice"].stats["l1"] > 1430
     assert out["bitslice"].stats["path_launches"][2] > 0
     P = oracle.pair_supports(rp, it, n, m)
@@ -240,6 +242,7 @@ def test_dense_full_size(dic):
     res = dic.mine(h, db.minsup, db.M, path="auto")
     got = res.itemsets()
     assert got == dic.mine(h, db.minsup, db.M, path="rows").itemsets()
+    assert got == dic.mine(h, db.minsup, db.M, path="tensor").itemsets()
     h.free()
     freq = np.bincount(db.items, minlength=db.m)
     assert [x for x in got if len(x[0]) == 1] == [((i,), int(freq[i])) for i in range(db.m)
