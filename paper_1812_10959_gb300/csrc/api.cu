@@ -758,7 +758,8 @@ dic_status Miner::prepare() {
         TRY(alloc(&tc_X_, tc_xbytes_, true));
         const uint32_t nt = gram_tiles(l1), ntp = nt * (nt + 1) / 2;
         const uint32_t sms = (uint32_t)sm_count();
-        tc_nsplit_ = std::max<uint32_t>(1, std::min<uint32_t>(tc_nkc_max_, (sms + ntp - 1) / ntp));
+        // one CTA per SM (the ring takes ~144 KiB): a single wave of splits
+        tc_nsplit_ = std::max<uint32_t>(1, std::min<uint32_t>(tc_nkc_max_, sms / ntp));
         L_.pair_end = (uint32_t)npairs;
         tc_ok_ = true;
       }

@@ -91,6 +91,7 @@ __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32
     const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
     kk[i] = (uint8_t)(k && c < skip ? KSKIP : k);
     cnt[i] = 0;
+    if (c < skip) continue;  // counted elsewhere: no ranks needed
 #pragma unroll
     for (int q = 0; q < KRE; ++q)
       rk[(size_t)i * KRE + q] = (uint32_t)q < k ? L.cranks[(uint64_t)c * KRMAX + q] : (uint16_t)0;
