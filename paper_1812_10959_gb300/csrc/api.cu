@@ -306,6 +306,11 @@ class Miner {
   void release() {
     for (void *p : bufs_) cudaFreeAsync(p, s_);
     bufs_.clear();
+    for (auto &sg : graphs_) {
+      if (sg.exec) cudaGraphExecDestroy(sg.exec);
+      if (sg.graph) cudaGraphDestroy(sg.graph);
+    }
+    graphs_.clear();
     for (cudaEvent_t ev : ev_pool_) cudaEventDestroy(ev);
     ev_pool_.clear();
     ev_used_ = 0;
@@ -357,6 +362,21 @@ class Miner {
   uint32_t pred_step_ = 1;     // stop number the next enqueued count runs at
   double gram_ms_ = 0;
   uint64_t gram_timed_ = 0;
+  // CUDA graphs: one captured stop per variant, replayed stop after stop
+  struct StopGraph {
+    int path = 0, kre = 0;
+    bool gram = false, slice = false, profile = false;
+    uint32_t nw = 0;
+    uint64_t version = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> ev_nodes;  // event records in recording order
+    uint32_t kernels = 0;
+    uint32_t path_counts[4] = {0, 0, 0, 0};
+  };
+  std::vector<StopGraph> graphs_;
+  uint64_t lat_version_ = 1;  // bumped whenever a buffer of the lattice changes
+  dic_status launch_stop();   // one stop: graph replay or direct launches
   int grid_ = 0;
   uint32_t launches_ = 0;
   uint32_t path_launches_[4] = {0, 0, 0, 0};
@@ -549,6 +569,7 @@ dic_status Miner::grow_candidates(uint32_t need) {
   drop(L_.cmask); drop(L_.csupp); drop(L_.cbirth); drop(L_.cshape); drop(L_.newbox);
   drop(L_.newhash); drop(L_.ck); drop(L_.cranks); drop(L_.cpromo);
   L_ = N;
+  ++lat_version_;
   return DIC_OK;
 }
 
@@ -564,6 +585,7 @@ dic_status Miner::grow_hash(uint64_t entries) {
   ++launches_;
   drop(L_.hslot);
   L_ = N;
+  ++lat_version_;
   return DIC_OK;
 }
 
@@ -583,6 +605,7 @@ dic_status Miner::grow_trace(uint32_t need) {
                      cudaMemcpyDeviceToDevice, s_));
   drop(L_.trace); drop(L_.cohort_start); drop(L_.cohort_birth);
   L_ = N;
+  ++lat_version_;
   return DIC_OK;
 }
 
@@ -803,6 +826,7 @@ dic_status Miner::set_tile_width(int tw, bool *ok) {
   L_.vwords = bs_V_words_;
   L_.tw = (uint32_t)bs_tw_;
   next_v_ready_ = false;
+  ++lat_version_;
   *ok = true;
   return DIC_OK;
 }
@@ -845,6 +869,106 @@ dic_status Miner::recover() {
   return DIC_OK;
 }
 
+dic_status Miner::launch_stop() {
+  if (!opt_.use_graph) return launch_stop_from(PH_COUNT);
+  const bool fast = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
+  StopGraph key;
+  key.path = cur_path_;
+  key.gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
+  key.slice = fast && !next_v_ready_;
+  key.kre = fast ? kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4)) : 0;
+  key.nw = cur_path_ == DIC_COUNT_ROWS ? nw_ : 0;
+  key.profile = opt_.profile != 0;
+  key.version = lat_version_;
+  StopGraph *sg = nullptr;
+  for (auto &g : graphs_)
+    if (g.path == key.path && g.gram == key.gram && g.slice == key.slice && g.kre == key.kre &&
+        g.nw == key.nw && g.profile == key.profile && g.version == key.version)
+      sg = &g;
+  const uint32_t pred0 = pred_step_;
+  if (!sg) {
+    // capture this stop's launches once (the host-side bookkeeping of the
+    // capture is undone; every replay applies it)
+    for (size_t i = 0; i < 4; ++i) {  // pool events used by the capture
+      cudaEvent_t e;
+      TRY(next_event(&e));
+    }
+    ev_used_ -= 4;
+    const size_t e0 = ev_used_, ng0 = gram_events_.size();
+    const uint32_t l0 = launches_;
+    uint32_t p0[4];
+    std::memcpy(p0, path_launches_, sizeof p0);
+    const bool v0 = next_v_ready_;
+    CU(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal));
+    dic_status st = launch_stop_from(PH_COUNT);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s_, &graph);
+    cudaError_t ie = cudaErrorUnknown;
+    if (st == DIC_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&key.exec, graph, 0);
+    if (st != DIC_OK || ce != cudaSuccess || ie != cudaSuccess) {
+      // capture not possible here: undo its bookkeeping, launch directly from now on
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      launches_ = l0;
+      std::memcpy(path_launches_, p0, sizeof p0);
+      ev_used_ = e0;
+      gram_events_.resize(ng0);
+      next_v_ready_ = v0;
+      pred_step_ = pred0;
+      opt_.use_graph = 0;
+      return launch_stop_from(PH_COUNT);
+    }
+    key.graph = graph;
+    key.kernels = launches_ - l0;
+    for (int i = 0; i < 4; ++i) key.path_counts[i] = path_launches_[i] - p0[i];
+    if (key.profile) {
+      size_t nn = 0;
+      CU(cudaGraphGetNodes(graph, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      CU(cudaGraphGetNodes(graph, nodes.data(), &nn));
+      std::vector<std::pair<size_t, cudaGraphNode_t>> evn;
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        CU(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        CU(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        for (size_t i = e0; i < ev_used_; ++i)
+          if (ev_pool_[i] == ev) evn.push_back({i, nd});
+      }
+      std::sort(evn.begin(), evn.end(),
+                [](const std::pair<size_t, cudaGraphNode_t> &a,
+                   const std::pair<size_t, cudaGraphNode_t> &b) { return a.first < b.first; });
+      for (auto &p : evn) key.ev_nodes.push_back(p.second);
+    }
+    launches_ = l0;
+    std::memcpy(path_launches_, p0, sizeof p0);
+    ev_used_ = e0;
+    gram_events_.resize(ng0);
+    next_v_ready_ = v0;
+    pred_step_ = pred0;
+    graphs_.push_back(key);
+    sg = &graphs_.back();
+  }
+  if (sg->profile) {
+    // fresh events for this replay, in recording order: (gram start, gram
+    // end,) count start, count end
+    const size_t base = ev_used_;
+    for (cudaGraphNode_t nd : sg->ev_nodes) {
+      cudaEvent_t e;
+      TRY(next_event(&e));
+      CU(cudaGraphExecEventRecordNodeSetEvent(sg->exec, nd, e));
+    }
+    if (sg->gram && sg->ev_nodes.size() == 4) gram_events_.push_back({base, base + 1});
+  }
+  CU(cudaGraphLaunch(sg->exec, s_));
+  launches_ += sg->kernels;
+  for (int i = 0; i < 4; ++i) path_launches_[i] += sg->path_counts[i];
+  next_v_ready_ = fast;
+  pred_step_ = pred0 + 1;
+  return DIC_OK;
+}
+
 dic_status Miner::loop() {
   if (!has_loop_) return DIC_OK;
   const uint32_t wc = L_.wc;
@@ -858,7 +982,7 @@ dic_status Miner::loop() {
     nw_ = bucket ? (uint32_t)bucket : 0;
     cur_path_ = count_path_for_stop();
     pred_step_ = h_ctrl_->step;
-    for (uint32_t i = 0; i < group; ++i) TRY(launch_stop_from(PH_COUNT));
+    for (uint32_t i = 0; i < group; ++i) TRY(launch_stop());
     TRY(sync_ctrl());
     TRY(recover());
   }

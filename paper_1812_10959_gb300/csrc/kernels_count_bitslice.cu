@@ -87,19 +87,28 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   uint32_t nw32, ntiles;
   if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
   const uint32_t head = C->head, tail = C->tail;
-  const uint32_t ncand = tail - head;
-  // balance the live window over the grid; shared memory holds chunk_cap
-  uint32_t chunk = (ncand + gridDim.x - 1) / gridDim.x;
-  chunk = (chunk + 3) & ~3u;
-  if (chunk < 4) chunk = 4;
-  if (chunk > chunk_cap) chunk = chunk_cap;
-  const uint32_t nchunks = (ncand + chunk - 1) / chunk;
+  // records below `skip` (the pair cohort while the tensor path counts it)
+  // only need PRUNE; the rest are counted. Each range is spread over the
+  // whole grid on its own, so the (few) counted records do not all land in
+  // the last chunks of the window.
+  const uint32_t skip = (L.pair_end && g <= L.stop_max) ? L.pair_end : 0u;
+  const uint32_t cbeg = skip > head ? (skip < tail ? skip : tail) : head;
   uint32_t pruned = 0, solid = 0;
-  for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const uint32_t c0 = head + ch * chunk;
-    const uint32_t cn = (tail - c0) < chunk ? (tail - c0) : chunk;
-    bs_count_chunk<TW, KRE, BS_THREADS>(L, C, g, c0, cn, nw32, ntiles, sm, chunk_cap, pruned,
-                                        solid);
+  for (int range = 0; range < 2; ++range) {
+    const uint32_t lo = range == 0 ? cbeg : head, hi = range == 0 ? tail : cbeg;
+    const uint32_t ncand = hi - lo;
+    if (ncand == 0) continue;
+    uint32_t chunk = (ncand + gridDim.x - 1) / gridDim.x;
+    chunk = (chunk + 3) & ~3u;
+    if (chunk < 4) chunk = 4;
+    if (chunk > chunk_cap) chunk = chunk_cap;
+    const uint32_t nchunks = (ncand + chunk - 1) / chunk;
+    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+      const uint32_t c0 = lo + ch * chunk;
+      const uint32_t cn = (hi - c0) < chunk ? (hi - c0) : chunk;
+      bs_count_chunk<TW, KRE, BS_THREADS>(L, C, g, c0, cn, nw32, ntiles, sm, chunk_cap, pruned,
+                                          solid);
+    }
   }
   if (pruned) atomicAdd(&C->n_pruned, pruned);
   if (solid) atomicAdd(&C->n_solid, solid);
