@@ -264,3 +264,18 @@ def test_dense_full_size(dic):
             border.add((a, b))
     bs = oracle.support(db.row_ptr, db.items, db.n, db.m, sorted(border))
     assert (bs < db.minsup).all()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_direct_launches_equal_graph_replays(dic, path):
+    """Stops replayed as captured CUDA graphs and stops launched one kernel
+    at a time give the same result and trace (and the oracle's)."""
+    db = synth.planted_small()
+    h = dic.load_db_csr(db.row_ptr, db.items, db.n, db.m)
+    a = dic.mine(h, db.minsup, db.M, path=path, use_graph=True, profile=True)
+    b = dic.mine(h, db.minsup, db.M, path=path, use_graph=False)
+    h.free()
+    ref = oracle.dic(db.row_ptr, db.items, db.n, db.m, db.minsup, db.M)
+    assert a.itemsets() == b.itemsets() == ref.itemsets
+    assert a.trace.tolist() == b.trace.tolist() == ref.trace.tolist()
+    assert a.stats["count_launches"] >= len(ref.trace)
