@@ -407,7 +407,7 @@ def main():
     count_ops = sum(s["count_ops"] for s in stats)
     avg_ms = count_ms / max(count_launches, 1)
     ops_per_launch = count_ops / max(count_launches, 1)
-    achieved = ops_per_launch / (avg_ms / 1e3) / 1e12
+    achieved = ops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
     pl = stats[0]["path_launches"]
     kernel = COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])]
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",

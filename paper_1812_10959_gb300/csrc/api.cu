@@ -323,6 +323,7 @@ class Miner {
   dic_status grow_candidates(uint32_t need);
   dic_status grow_hash(uint64_t entries);
   dic_status next_event(cudaEvent_t *ev);
+  dic_status record(cudaEvent_t ev);
   dic_status harvest_events();
   dic_status grow_trace(uint32_t need);
   dic_status launch_phase(int phase);
@@ -411,6 +412,18 @@ static int kr_bucket(uint32_t max_k) {
   return 16;
 }
 
+// Record a profiling event; inside a stream capture it must become an event
+// record node of the graph (a plain record would only add a dependency).
+dic_status Miner::record(cudaEvent_t ev) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(s_, &cs));
+  if (cs == cudaStreamCaptureStatusActive)
+    CU(cudaEventRecordWithFlags(ev, s_, cudaEventRecordExternal));
+  else
+    CU(cudaEventRecord(ev, s_));
+  return DIC_OK;
+}
+
 dic_status Miner::next_event(cudaEvent_t *ev) {
   if (ev_used_ == ev_pool_.size()) {
     cudaEvent_t e;
@@ -475,7 +488,7 @@ dic_status Miner::launch_phase(int phase) {
           cudaEvent_t ga = nullptr, gb = nullptr;
           if (opt_.profile) {
             TRY(next_event(&ga));
-            CU(cudaEventRecord(ga, s_));
+            TRY(record(ga));
           }
           e = launch_gram_operand(L_, tc_X_, tc_nkc_max_, tc_xbytes_, (uint32_t)kre, s_);
           if (e == cudaSuccess)
@@ -484,14 +497,14 @@ dic_status Miner::launch_phase(int phase) {
           path_launches_[DIC_COUNT_TENSOR]++;
           if (opt_.profile && e == cudaSuccess) {
             TRY(next_event(&gb));
-            CU(cudaEventRecord(gb, s_));
+            TRY(record(gb));
             gram_events_.push_back({ev_used_ - 2, ev_used_ - 1});
           }
         }
         if (e == cudaSuccess) {
           if (opt_.profile) {
             TRY(next_event(&a));
-            CU(cudaEventRecord(a, s_));
+            TRY(record(a));
           }
           e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_, bs_grid_, s_);
         }
@@ -499,14 +512,14 @@ dic_status Miner::launch_phase(int phase) {
       } else {
         if (opt_.profile) {
           TRY(next_event(&a));
-          CU(cudaEventRecord(a, s_));
+          TRY(record(a));
         }
         e = launch_count_rows(L_, (int)nw_, grid_, s_);
         path_launches_[DIC_COUNT_ROWS]++;
       }
       if (opt_.profile && e == cudaSuccess) {
         TRY(next_event(&b));
-        CU(cudaEventRecord(b, s_));
+        TRY(record(b));
       }
       break;
     }
