@@ -101,9 +101,9 @@ typedef struct {
   uint64_t count_ops;       /* algorithmic integer ops of the count kernels:
                                ROWS h+2 per test (h = touched 32-bit
                                halves), BITSLICE k+1 per 32-row word      */
-  double gram_ms;           /* TENSOR pair-cohort kernels (profile=1 only)  */
+  double gram_ms;           /* TENSOR pair-cohort GEMM (profile=1 only)     */
   uint64_t gram_launches;   /* stops whose pair cohort ran on tcgen05       */
-  uint32_t reserved[2];
+  double settle_ms;         /* PRUNE of the tensor-counted pairs (profile)  */
 } dic_stats;
 
 /* Columns of one trace row (one per iteration of Algorithm 2's loop). */

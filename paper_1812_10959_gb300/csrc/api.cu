@@ -339,7 +339,15 @@ class Miner {
   std::vector<void *> bufs_;
   std::vector<cudaEvent_t> ev_pool_;   // profiling events, reused every group
   size_t ev_used_ = 0;
-  std::vector<std::pair<size_t, size_t>> gram_events_;  // (start, end) pool indices
+  // profiled intervals: (start, end) pool indices and what they time
+  enum IvKind { IV_COUNT = 0, IV_GRAM = 1, IV_SETTLE = 2 };
+  struct Interval { size_t start, end; int kind; };
+  std::vector<Interval> intervals_;
+  size_t iv_start_ = 0;
+  int iv_kind_ = 0;
+  dic_status iv_open(int kind);
+  dic_status iv_close();
+  double settle_ms_ = 0;
   double count_ms_ = 0;
   uint64_t count_timed_ = 0;
   Lattice L_{};
@@ -372,6 +380,7 @@ class Miner {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaGraphNode_t> ev_nodes;  // event records in recording order
+    std::vector<Interval> ivs;              // intervals, relative to the first event
     uint32_t kernels = 0;
     uint32_t path_counts[4] = {0, 0, 0, 0};
   };
@@ -436,26 +445,32 @@ dic_status Miner::next_event(cudaEvent_t *ev) {
 
 // Sum the count-kernel event pairs recorded since the last group (the
 // stream has been synchronised).
+dic_status Miner::iv_open(int kind) {
+  cudaEvent_t e;
+  TRY(next_event(&e));
+  TRY(record(e));
+  iv_start_ = ev_used_ - 1;
+  iv_kind_ = kind;
+  return DIC_OK;
+}
+
+dic_status Miner::iv_close() {
+  cudaEvent_t e;
+  TRY(next_event(&e));
+  TRY(record(e));
+  intervals_.push_back({iv_start_, ev_used_ - 1, iv_kind_});
+  return DIC_OK;
+}
+
 dic_status Miner::harvest_events() {
-  std::vector<bool> is_gram(ev_used_, false);
-  for (auto &ge : gram_events_) {
+  for (const Interval &iv : intervals_) {
     float ms = 0;
-    CU(cudaEventElapsedTime(&ms, ev_pool_[ge.first], ev_pool_[ge.second]));
-    gram_ms_ += ms;
-    ++gram_timed_;
-    is_gram[ge.first] = is_gram[ge.second] = true;
+    CU(cudaEventElapsedTime(&ms, ev_pool_[iv.start], ev_pool_[iv.end]));
+    if (iv.kind == IV_COUNT) { count_ms_ += ms; ++count_timed_; }
+    else if (iv.kind == IV_GRAM) { gram_ms_ += ms; ++gram_timed_; }
+    else settle_ms_ += ms;
   }
-  gram_events_.clear();
-  size_t first = SIZE_MAX;
-  for (size_t i = 0; i < ev_used_; ++i) {
-    if (is_gram[i]) continue;
-    if (first == SIZE_MAX) { first = i; continue; }
-    float ms = 0;
-    CU(cudaEventElapsedTime(&ms, ev_pool_[first], ev_pool_[i]));
-    count_ms_ += ms;
-    ++count_timed_;
-    first = SIZE_MAX;
-  }
+  intervals_.clear();
   ev_used_ = 0;
   return DIC_OK;
 }
@@ -471,7 +486,7 @@ dic_status Miner::launch_phase(int phase) {
   cudaError_t e = cudaSuccess;
   switch (phase) {
     case PH_COUNT: {
-      cudaEvent_t a = nullptr, b = nullptr;
+      const bool prof = opt_.profile != 0;
       if (cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR) {
         // shared memory for the largest chunk that fits; the kernel sizes its
         // chunk from the live window
@@ -483,43 +498,35 @@ dic_status Miner::launch_phase(int phase) {
           ++launches_;
         }
         next_v_ready_ = false;
-        if (e == cudaSuccess && cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max) {
+        const bool gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
+        if (e == cudaSuccess && gram) {
           // the pair cohort on the tensor cores (it is in DASHED up to stop_max)
-          cudaEvent_t ga = nullptr, gb = nullptr;
-          if (opt_.profile) {
-            TRY(next_event(&ga));
-            TRY(record(ga));
-          }
           e = launch_gram_operand(L_, tc_X_, tc_nkc_max_, tc_xbytes_, (uint32_t)kre, s_);
+          if (prof) TRY(iv_open(IV_GRAM));
           if (e == cudaSuccess)
             e = launch_gram_pairs(L_, tc_X_, tc_nkc_max_, tc_nsplit_, (uint32_t)kre, s_);
+          if (prof) TRY(iv_close());
           launches_ += 2;
           path_launches_[DIC_COUNT_TENSOR]++;
-          if (opt_.profile && e == cudaSuccess) {
-            TRY(next_event(&gb));
-            TRY(record(gb));
-            gram_events_.push_back({ev_used_ - 2, ev_used_ - 1});
-          }
         }
         if (e == cudaSuccess) {
-          if (opt_.profile) {
-            TRY(next_event(&a));
-            TRY(record(a));
-          }
-          e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_, bs_grid_, s_);
+          if (prof) TRY(iv_open(IV_COUNT));
+          e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_,
+                                    bs_grid_, s_);
+          if (prof) TRY(iv_close());
+        }
+        if (e == cudaSuccess && gram) {
+          if (prof) TRY(iv_open(IV_SETTLE));
+          e = launch_settle_pairs(L_, grid_, s_);
+          if (prof) TRY(iv_close());
+          ++launches_;
         }
         path_launches_[DIC_COUNT_BITSLICE]++;
       } else {
-        if (opt_.profile) {
-          TRY(next_event(&a));
-          TRY(record(a));
-        }
+        if (prof) TRY(iv_open(IV_COUNT));
         e = launch_count_rows(L_, (int)nw_, grid_, s_);
+        if (prof) TRY(iv_close());
         path_launches_[DIC_COUNT_ROWS]++;
-      }
-      if (opt_.profile && e == cudaSuccess) {
-        TRY(next_event(&b));
-        TRY(record(b));
       }
       break;
     }
@@ -902,12 +909,12 @@ dic_status Miner::launch_stop() {
   if (!sg) {
     // capture this stop's launches once (the host-side bookkeeping of the
     // capture is undone; every replay applies it)
-    for (size_t i = 0; i < 4; ++i) {  // pool events used by the capture
+    for (size_t i = 0; i < 8; ++i) {  // pool events used by the capture
       cudaEvent_t e;
       TRY(next_event(&e));
     }
-    ev_used_ -= 4;
-    const size_t e0 = ev_used_, ng0 = gram_events_.size();
+    ev_used_ -= 8;
+    const size_t e0 = ev_used_, ni0 = intervals_.size();
     const uint32_t l0 = launches_;
     uint32_t p0[4];
     std::memcpy(p0, path_launches_, sizeof p0);
@@ -925,7 +932,7 @@ dic_status Miner::launch_stop() {
       launches_ = l0;
       std::memcpy(path_launches_, p0, sizeof p0);
       ev_used_ = e0;
-      gram_events_.resize(ng0);
+      intervals_.resize(ni0);
       next_v_ready_ = v0;
       pred_step_ = pred0;
       opt_.use_graph = 0;
@@ -953,11 +960,13 @@ dic_status Miner::launch_stop() {
                 [](const std::pair<size_t, cudaGraphNode_t> &a,
                    const std::pair<size_t, cudaGraphNode_t> &b) { return a.first < b.first; });
       for (auto &p : evn) key.ev_nodes.push_back(p.second);
+      for (size_t i = ni0; i < intervals_.size(); ++i)
+        key.ivs.push_back({intervals_[i].start - e0, intervals_[i].end - e0, intervals_[i].kind});
     }
     launches_ = l0;
     std::memcpy(path_launches_, p0, sizeof p0);
     ev_used_ = e0;
-    gram_events_.resize(ng0);
+    intervals_.resize(ni0);
     next_v_ready_ = v0;
     pred_step_ = pred0;
     graphs_.push_back(key);
@@ -972,7 +981,7 @@ dic_status Miner::launch_stop() {
       TRY(next_event(&e));
       CU(cudaGraphExecEventRecordNodeSetEvent(sg->exec, nd, e));
     }
-    if (sg->gram && sg->ev_nodes.size() == 4) gram_events_.push_back({base, base + 1});
+    for (const Interval &iv : sg->ivs) intervals_.push_back({base + iv.start, base + iv.end, iv.kind});
   }
   CU(cudaGraphLaunch(sg->exec, s_));
   launches_ += sg->kernels;
@@ -1084,6 +1093,7 @@ dic_status Miner::collect(dic_result **out) {
     res->stats.count_launches = count_timed_;
     res->stats.gram_ms = gram_ms_;
     res->stats.gram_launches = gram_timed_;
+    res->stats.settle_ms = settle_ms_;
   }
   release();
   cudaError_t e = cudaStreamSynchronize(s_);

@@ -58,6 +58,45 @@ __device__ __forceinline__ bool bs_block_tiles(const Lattice &L, Ctrl *C, uint32
   return true;
 }
 
+// Windows up to this many counted records use bs_count_direct.
+constexpr uint32_t BS_DIRECT_MAX = 24576;
+
+// Count records [lo, hi) with one warp per record: lane w reads word w of
+// each of the record's rank columns from L.V (tile t = w / TW), ANDs them and
+// popcounts; the warp sum is the record's count. Then PRUNE. Whole warps
+// must call this (grid-stride over records by warp).
+template <int TW>
+__device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint32_t g,
+                                                uint32_t lo, uint32_t hi, uint32_t nw32,
+                                                uint32_t &pruned, uint32_t &solid) {
+  constexpr uint32_t ST = bs_stride(TW);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long work = 0;
+  for (uint64_t c = lo + (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < hi;
+       c += nwarps) {
+    const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
+    if (k == 0) continue;  // uniform over the warp
+    const uint16_t *rk = L.cranks + c * KRMAX;
+    uint32_t cnt = 0;
+    for (uint32_t w = lane; w < nw32; w += 32) {
+      const uint64_t tbase = (uint64_t)(w / TW) * L.l1p;
+      const uint32_t wi = w % TW;
+      uint32_t acc = __ldg(L.V + (tbase + rk[0]) * ST + wi);
+      for (uint32_t q = 1; q < k; ++q) acc &= __ldg(L.V + (tbase + rk[q]) * ST + wi);
+      cnt += __popc(acc);
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) {
+      const uint32_t s = L.csupp[c] + cnt;
+      L.csupp[c] = s;
+      settle_record(L, C, (uint32_t)c, s, g, true, pruned, solid);
+      work += (unsigned long long)(k + 1) * nw32;
+    }
+  }
+  warp_add_u64(&C->work, work);
+}
+
 // Count records [c0, c0+cn) of the window over the block of stop g and apply
 // PRUNE (Algorithm 4) to each. Tiles of L.V stream through a cp.async double
 // buffer; every thread ANDs its candidates' rank columns with 128-bit shared

@@ -173,6 +173,9 @@ cudaError_t launch_gram_operand(Lattice L, uint8_t *X, uint32_t nkc_max, uint64_
 cudaError_t launch_gram_pairs(Lattice L, const uint8_t *X, uint32_t nkc_max, uint32_t nsplit,
                               uint32_t kre, cudaStream_t s);
 
+// PRUNE for the pair cohort counted by the tensor path (one thread per record).
+cudaError_t launch_settle_pairs(Lattice L, int grid, cudaStream_t s);
+
 // Largest candidate chunk whose bitslice shared-memory footprint fits.
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit);
 size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk);

@@ -88,16 +88,17 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
   const uint32_t head = C->head, tail = C->tail;
   // records below `skip` (the pair cohort while the tensor path counts it)
-  // only need PRUNE; the rest are counted. Each range is spread over the
-  // whole grid on its own, so the (few) counted records do not all land in
-  // the last chunks of the window.
+  // are settled by k_settle_range; this kernel counts [lo, tail)
   const uint32_t skip = (L.pair_end && g <= L.stop_max) ? L.pair_end : 0u;
-  const uint32_t cbeg = skip > head ? (skip < tail ? skip : tail) : head;
+  const uint32_t lo = skip > head ? (skip < tail ? skip : tail) : head;
+  const uint32_t ncand = tail - lo;
   uint32_t pruned = 0, solid = 0;
-  for (int range = 0; range < 2; ++range) {
-    const uint32_t lo = range == 0 ? cbeg : head, hi = range == 0 ? tail : cbeg;
-    const uint32_t ncand = hi - lo;
-    if (ncand == 0) continue;
+  if (ncand == 0) return;
+  if (ncand <= BS_DIRECT_MAX) {
+    // few candidates: no shared tiles; a warp per candidate ANDs its columns
+    // straight from the (L2-resident) column buffer
+    bs_count_direct<TW>(L, C, g, lo, tail, nw32, pruned, solid);
+  } else {
     uint32_t chunk = (ncand + gridDim.x - 1) / gridDim.x;
     chunk = (chunk + 3) & ~3u;
     if (chunk < 4) chunk = 4;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
     const uint32_t nchunks = (ncand + chunk - 1) / chunk;
     for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
       const uint32_t c0 = lo + ch * chunk;
-      const uint32_t cn = (hi - c0) < chunk ? (hi - c0) : chunk;
+      const uint32_t cn = (tail - c0) < chunk ? (tail - c0) : chunk;
       bs_count_chunk<TW, KRE, BS_THREADS>(L, C, g, c0, cn, nw32, ntiles, sm, chunk_cap, pruned,
                                           solid);
     }
@@ -113,6 +114,27 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   if (pruned) atomicAdd(&C->n_pruned, pruned);
   if (solid) atomicAdd(&C->n_solid, solid);
   (void)V; (void)l1p; (void)vwords;
+}
+
+// PRUNE (Algorithm 4) for the pair cohort after the tensor kernel has added
+// this stop's counts: one thread per record.
+__global__ void __launch_bounds__(256) k_settle_pairs(Lattice L) {
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  const uint32_t g = C->step;
+  if (!L.pair_end || g > L.stop_max) return;
+  const uint32_t head = C->head, end = L.pair_end < C->tail ? L.pair_end : C->tail;
+  uint32_t pruned = 0, solid = 0;
+  for (uint32_t c = head + blockIdx.x * blockDim.x + threadIdx.x; c < end;
+       c += gridDim.x * blockDim.x)
+    settle_record(L, C, c, L.csupp[c], g, true, pruned, solid);
+  if (pruned) atomicAdd(&C->n_pruned, pruned);
+  if (solid) atomicAdd(&C->n_solid, solid);
+}
+
+cudaError_t launch_settle_pairs(Lattice L, int grid, cudaStream_t s) {
+  k_settle_pairs<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
 }
 
 template <int TW, int KRE>

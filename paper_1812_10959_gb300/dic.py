@@ -41,7 +41,7 @@ class Stats(ctypes.Structure):
                 ("firstpass_ms", ctypes.c_double), ("mine_ms", ctypes.c_double),
                 ("path_launches", ctypes.c_uint32 * 4), ("count_ops", ctypes.c_uint64),
                 ("gram_ms", ctypes.c_double), ("gram_launches", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("settle_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "path_launches")}
