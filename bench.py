@@ -43,7 +43,14 @@ CPU_SAMPLE_M = 1_000
 # LOP3 per touched 32-bit half + compare + add per test; BITSLICE: k-1 AND +
 # POPC + ADD per 32-row word) in stats["count_ops"].
 ALU_PEAK_TOPS = 152 * 64 * 2.070e9 / 1e12
-COUNT_KERNELS = {1: "k_count_rows", 2: "k_count_bitslice", 3: "k_count_tensor"}
+COUNT_KERNELS = {1: "k_count_rows", 2: "k_count_bitslice", 3: "k_count_bitslice"}
+# fp8 (kind::f8f6f4) dense tensor peak = the measured bf16 peak x 2, the
+# nominal fp8:bf16 ratio (4.5 / 2.25 PFLOP/s)
+FP8_PER_BF16 = 2.0
+# timed kinds of the stop loop: stats key prefix -> profile name, kernels
+KINDS = {"count": "count", "gram": "gram", "settle": "settle", "gen": "gen"}
+KIND_KERNELS = {"gram": "k_gram_operand + k_gram_pairs", "settle": "k_settle_pairs",
+                "gen": "k_generate_finish"}
 
 
 def workload(name: str):
@@ -54,6 +61,48 @@ def workload(name: str):
     if name == "dense":
         return synth.dense_zipf()
     raise SystemExit(f"unknown workload {name}")
+
+
+def roofline_of(kind, stats, shares_ms, step_ms, db):
+    """Roofline object of the kernel kind `kind` from the profiled timed steps."""
+    pk = peaks()
+    tot_ms = sum(s[kind + "_ms"] for s in stats)
+    nkey = {"count": "count_launches", "gram": "gram_launches", "gen": "gen_launches"}
+    # one PRUNE-of-pairs launch per tensor-counted stop
+    nl = sum(s[nkey[kind]] if kind in nkey else s["path_launches"][3] for s in stats)
+    avg_ms = tot_ms / max(nl, 1)
+    st = stats[0]
+    common = {"avg_launch_ms": avg_ms, "launches_timed": nl, "share_of_step": tot_ms / step_ms,
+              "kind_ms_per_step": {k: v for k, v in shares_ms.items()}}
+    if kind == "gram":
+        flops = sum(s["gram_flops"] for s in stats) / max(nl, 1)
+        ach = flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+        peak = pk["bf16"] * FP8_PER_BF16
+        return dict(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    traffic=None, kernel=KIND_KERNELS[kind],
+                    peak_source=f"{pk['source']} bf16 burst x {FP8_PER_BF16} (fp8 e4m3)",
+                    flops_per_launch=flops, **common)
+    if kind == "count":
+        ops = sum(s["count_ops"] for s in stats) / max(nl, 1)
+        ach = ops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+        pl = st["path_launches"]
+        return dict(bound="alu", achieved=ach, peak=ALU_PEAK_TOPS, unit="Top/s",
+                    frac=ach / ALU_PEAK_TOPS, traffic=None,
+                    kernel=COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])],
+                    peak_source="derived: 152 SM x 64 INT32 lanes x 2070 MHz",
+                    ops_per_launch=ops, **common)
+    # gen / settle: memory-side kernels; algorithmic bytes per launch
+    wc, l1 = st["words_compact"], st["l1"]
+    if kind == "gen":
+        # the next block's compacted rows read and its bit columns written
+        byts = db.M * wc * 8 + db.M * l1 / 8
+    else:
+        # every pair record's counter, shape and birth read once
+        byts = l1 * (l1 - 1) / 2 * 9
+    ach = byts / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    return dict(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
+                frac=ach / pk["hbm_gbs"], traffic=None, kernel=KIND_KERNELS[kind],
+                peak_source=f"{pk['source']} copy bandwidth", bytes_per_launch=byts, **common)
 
 
 def peaks():
@@ -341,9 +390,13 @@ def main():
             dist.barrier()
 
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream)
+        for i in range(args.warmup):
+            # the last warm-up step times every kernel kind of the stop loop
+            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream,
+                           profile=(i == args.warmup - 1))
     ref_count = len(res.k)
+    shares_ms = {k: res.stats[k + "_ms"] for k in KINDS}
+    kind = max(shares_ms, key=lambda k: shares_ms[k])
     barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
@@ -356,7 +409,8 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream, profile=True)
+            # the dominant kernel kind is bracketed by events inside the step
+            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream, profile=kind)
             b.record(stream)
             evs.append((a, b))
             stats.append(res.stats)
@@ -400,21 +454,9 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_v = tests_step * args.steps * world / float(tt[0])
 
-    # ---- roofline of the dominant kernel (the count kernel), timed live with
-    # CUDA events on the mining stream around every count launch
-    count_ms = sum(s["count_ms"] for s in stats)
-    count_launches = sum(s["count_launches"] for s in stats)
-    count_ops = sum(s["count_ops"] for s in stats)
-    avg_ms = count_ms / max(count_launches, 1)
-    ops_per_launch = count_ops / max(count_launches, 1)
-    achieved = ops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
-    pl = stats[0]["path_launches"]
-    kernel = COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
-                "frac": achieved / ALU_PEAK_TOPS, "traffic": None, "kernel": kernel,
-                "peak_source": "derived: 152 SM x 64 INT32 lanes x 2070 MHz",
-                "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_ms,
-                "count_share_of_step": count_ms / sum(ms)}
+    # ---- roofline of the dominant kernel kind, timed live with CUDA events
+    # on the mining stream around each of its launches in the timed steps
+    roofline = roofline_of(kind, stats, shares_ms, sum(ms), db)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

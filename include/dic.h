@@ -69,6 +69,14 @@ typedef enum {
   DIC_COUNT_TENSOR = 3
 } dic_count_path;
 
+/* dic_options.profile bits: which kernels of the stop loop are bracketed by
+ * CUDA events (each timed kind adds two event records per stop). */
+#define DIC_PROFILE_COUNT  1u  /* COUNTSUPPORT: ROWS or BITSLICE count kernel  */
+#define DIC_PROFILE_GRAM   2u  /* TENSOR pair-cohort operand + GEMM            */
+#define DIC_PROFILE_SETTLE 4u  /* PRUNE of the tensor-counted pairs            */
+#define DIC_PROFILE_GEN    8u  /* MAKECANDIDATES + CHECKFULLPASS (+ slicing)   */
+#define DIC_PROFILE_ALL   15u
+
 /* Mining options. Initialise with dic_options_init(); unknown trailing
  * fields are ignored by older libraries (struct_size). */
 typedef struct {
@@ -76,7 +84,8 @@ typedef struct {
   uint32_t count_path;      /* dic_count_path                              */
   uint32_t steps_per_sync;  /* stops enqueued between host checks; 0=auto  */
   uint32_t use_graph;       /* 1: replay stop loops as CUDA graphs         */
-  uint32_t profile;         /* 1: time count kernels with CUDA events      */
+  uint32_t profile;         /* bitmask of DIC_PROFILE_*: kernels to time
+                               with CUDA events on the mining stream       */
   uint32_t max_candidates;  /* 0 = no limit; else DIC_ECAPACITY beyond it  */
   uint32_t reserved[10];
 } dic_options;
@@ -93,17 +102,24 @@ typedef struct {
   uint32_t words;           /* W = ceil(m/64)                              */
   uint32_t words_compact;   /* W' = ceil(l1/64)                            */
   uint32_t kernel_launches; /* kernels launched by this run                */
-  double count_ms;          /* summed count-kernel time (profile=1 only)   */
+  double count_ms;          /* summed count-kernel time (DIC_PROFILE_COUNT) */
   uint64_t count_launches;  /* count-kernel launches timed                 */
-  double firstpass_ms;      /* first-pass kernel time (profile=1 only)     */
+  double firstpass_ms;      /* first-pass kernel time (any profile bit)    */
   double mine_ms;           /* wall time of the mining call (host clock)   */
   uint32_t path_launches[4];/* count launches per dic_count_path           */
   uint64_t count_ops;       /* algorithmic integer ops of the count kernels:
                                ROWS h+2 per test (h = touched 32-bit
                                halves), BITSLICE k+1 per 32-row word      */
-  double gram_ms;           /* TENSOR pair-cohort GEMM (profile=1 only)     */
-  uint64_t gram_launches;   /* stops whose pair cohort ran on tcgen05       */
-  double settle_ms;         /* PRUNE of the tensor-counted pairs (profile)  */
+  double gram_ms;           /* TENSOR pair-cohort operand + GEMM
+                               (DIC_PROFILE_GRAM)                          */
+  uint64_t gram_launches;   /* pair-cohort GEMMs timed                     */
+  double settle_ms;         /* PRUNE of the tensor-counted pairs
+                               (DIC_PROFILE_SETTLE)                        */
+  double gen_ms;            /* generate/finish kernels (DIC_PROFILE_GEN)   */
+  uint64_t gen_launches;    /* generate/finish kernels timed               */
+  uint64_t gram_flops;      /* algorithmic tensor work: 2 * pairs * rows
+                               summed over the stops counted by the GEMM   */
+  uint64_t reserved[5];
 } dic_stats;
 
 /* Columns of one trace row (one per iteration of Algorithm 2's loop). */

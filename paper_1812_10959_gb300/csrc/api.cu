@@ -340,14 +340,16 @@ class Miner {
   std::vector<cudaEvent_t> ev_pool_;   // profiling events, reused every group
   size_t ev_used_ = 0;
   // profiled intervals: (start, end) pool indices and what they time
-  enum IvKind { IV_COUNT = 0, IV_GRAM = 1, IV_SETTLE = 2 };
+  enum IvKind { IV_COUNT = 0, IV_GRAM = 1, IV_SETTLE = 2, IV_GEN = 3 };
   struct Interval { size_t start, end; int kind; };
   std::vector<Interval> intervals_;
   size_t iv_start_ = 0;
   int iv_kind_ = 0;
   dic_status iv_open(int kind);
   dic_status iv_close();
-  double settle_ms_ = 0;
+  bool prof(uint32_t bit) const { return (opt_.profile & bit) != 0; }
+  double settle_ms_ = 0, gen_ms_ = 0;
+  uint64_t gen_timed_ = 0;
   double count_ms_ = 0;
   uint64_t count_timed_ = 0;
   Lattice L_{};
@@ -374,7 +376,8 @@ class Miner {
   // CUDA graphs: one captured stop per variant, replayed stop after stop
   struct StopGraph {
     int path = 0, kre = 0;
-    bool gram = false, slice = false, profile = false;
+    bool gram = false, slice = false;
+    uint32_t profile = 0;  // DIC_PROFILE_* bits captured as event nodes
     uint32_t nw = 0;
     uint64_t version = 0;
     cudaGraph_t graph = nullptr;
@@ -468,6 +471,7 @@ dic_status Miner::harvest_events() {
     CU(cudaEventElapsedTime(&ms, ev_pool_[iv.start], ev_pool_[iv.end]));
     if (iv.kind == IV_COUNT) { count_ms_ += ms; ++count_timed_; }
     else if (iv.kind == IV_GRAM) { gram_ms_ += ms; ++gram_timed_; }
+    else if (iv.kind == IV_GEN) { gen_ms_ += ms; ++gen_timed_; }
     else settle_ms_ += ms;
   }
   intervals_.clear();
@@ -486,7 +490,6 @@ dic_status Miner::launch_phase(int phase) {
   cudaError_t e = cudaSuccess;
   switch (phase) {
     case PH_COUNT: {
-      const bool prof = opt_.profile != 0;
       if (cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR) {
         // shared memory for the largest chunk that fits; the kernel sizes its
         // chunk from the live window
@@ -501,31 +504,31 @@ dic_status Miner::launch_phase(int phase) {
         const bool gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
         if (e == cudaSuccess && gram) {
           // the pair cohort on the tensor cores (it is in DASHED up to stop_max)
+          if (prof(DIC_PROFILE_GRAM)) TRY(iv_open(IV_GRAM));
           e = launch_gram_operand(L_, tc_X_, tc_nkc_max_, tc_xbytes_, (uint32_t)kre, s_);
-          if (prof) TRY(iv_open(IV_GRAM));
           if (e == cudaSuccess)
             e = launch_gram_pairs(L_, tc_X_, tc_nkc_max_, tc_nsplit_, (uint32_t)kre, s_);
-          if (prof) TRY(iv_close());
+          if (prof(DIC_PROFILE_GRAM)) TRY(iv_close());
           launches_ += 2;
           path_launches_[DIC_COUNT_TENSOR]++;
         }
         if (e == cudaSuccess) {
-          if (prof) TRY(iv_open(IV_COUNT));
+          if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT));
           e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_,
                                     bs_grid_, s_);
-          if (prof) TRY(iv_close());
+          if (prof(DIC_PROFILE_COUNT)) TRY(iv_close());
         }
         if (e == cudaSuccess && gram) {
-          if (prof) TRY(iv_open(IV_SETTLE));
+          if (prof(DIC_PROFILE_SETTLE)) TRY(iv_open(IV_SETTLE));
           e = launch_settle_pairs(L_, grid_, s_);
-          if (prof) TRY(iv_close());
+          if (prof(DIC_PROFILE_SETTLE)) TRY(iv_close());
           ++launches_;
         }
         path_launches_[DIC_COUNT_BITSLICE]++;
       } else {
-        if (prof) TRY(iv_open(IV_COUNT));
+        if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT));
         e = launch_count_rows(L_, (int)nw_, grid_, s_);
-        if (prof) TRY(iv_close());
+        if (prof(DIC_PROFILE_COUNT)) TRY(iv_close());
         path_launches_[DIC_COUNT_ROWS]++;
       }
       break;
@@ -534,7 +537,9 @@ dic_status Miner::launch_phase(int phase) {
     case PH_HASH: e = launch_hash_insert(L_, grid_, s_); break;
     case PH_GEN: {
       const bool slice = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
+      if (prof(DIC_PROFILE_GEN)) TRY(iv_open(IV_GEN));
       e = launch_generate_finish(L_, grid_, slice, s_);
+      if (prof(DIC_PROFILE_GEN)) TRY(iv_close());
       next_v_ready_ = slice;
       ++pred_step_;
       break;
@@ -898,7 +903,7 @@ dic_status Miner::launch_stop() {
   key.slice = fast && !next_v_ready_;
   key.kre = fast ? kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4)) : 0;
   key.nw = cur_path_ == DIC_COUNT_ROWS ? nw_ : 0;
-  key.profile = opt_.profile != 0;
+  key.profile = opt_.profile;
   key.version = lat_version_;
   StopGraph *sg = nullptr;
   for (auto &g : graphs_)
@@ -1023,6 +1028,7 @@ dic_status Miner::collect(dic_result **out) {
     const uint32_t wc = L_.wc;
     tests = h_ctrl_->tests;
     res->stats.count_ops = h_ctrl_->work;
+    res->stats.gram_flops = 2ull * ((uint64_t)L_.l1 * (L_.l1 - 1) / 2) * h_ctrl_->gram_rows;
     const uint32_t tail = h_ctrl_->tail;
     res->stats.candidates = tail;
 
@@ -1094,6 +1100,8 @@ dic_status Miner::collect(dic_result **out) {
     res->stats.gram_ms = gram_ms_;
     res->stats.gram_launches = gram_timed_;
     res->stats.settle_ms = settle_ms_;
+    res->stats.gen_ms = gen_ms_;
+    res->stats.gen_launches = gen_timed_;
   }
   release();
   cudaError_t e = cudaStreamSynchronize(s_);

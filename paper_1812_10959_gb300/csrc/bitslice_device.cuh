@@ -63,27 +63,38 @@ constexpr uint32_t BS_DIRECT_MAX = 24576;
 
 // Count records [lo, hi) with one warp per record: lane w reads word w of
 // each of the record's rank columns from L.V (tile t = w / TW), ANDs them and
-// popcounts; the warp sum is the record's count. Then PRUNE. Whole warps
-// must call this (grid-stride over records by warp).
-template <int TW>
+// popcounts; the warp sum is the record's count. Then PRUNE. The ranks are
+// held in registers and the rank loop is unrolled (predicated on q < k) so
+// that a lane's column loads, and those of its next words, are all in
+// flight together. Whole warps must call this
+// (grid-stride over records by warp).
+template <int TW, int KRE>
 __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint32_t g,
                                                 uint32_t lo, uint32_t hi, uint32_t nw32,
                                                 uint32_t &pruned, uint32_t &solid) {
   constexpr uint32_t ST = bs_stride(TW);
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint32_t *__restrict__ V = L.V;
+  const uint32_t l1p = L.l1p;
   unsigned long long work = 0;
   for (uint64_t c = lo + (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < hi;
        c += nwarps) {
     const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
     if (k == 0) continue;  // uniform over the warp
     const uint16_t *rk = L.cranks + c * KRMAX;
+    uint32_t r[KRE];
+#pragma unroll
+    for (int q = 0; q < KRE; ++q) r[q] = (uint32_t)q < k ? (uint32_t)rk[q] : 0u;
     uint32_t cnt = 0;
+#pragma unroll 4
     for (uint32_t w = lane; w < nw32; w += 32) {
-      const uint64_t tbase = (uint64_t)(w / TW) * L.l1p;
+      const uint32_t tb = (w / TW) * l1p;
       const uint32_t wi = w % TW;
-      uint32_t acc = __ldg(L.V + (tbase + rk[0]) * ST + wi);
-      for (uint32_t q = 1; q < k; ++q) acc &= __ldg(L.V + (tbase + rk[q]) * ST + wi);
+      uint32_t acc = __ldg(V + (uint64_t)(tb + r[0]) * ST + wi);
+#pragma unroll
+      for (int q = 1; q < KRE; ++q)
+        if ((uint32_t)q < k) acc &= __ldg(V + (uint64_t)(tb + r[q]) * ST + wi);
       cnt += __popc(acc);
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);

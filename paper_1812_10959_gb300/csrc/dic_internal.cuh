@@ -52,6 +52,7 @@ struct Ctrl {
   uint32_t solo;         // 1: the batched kernels leave this query alone
   unsigned long long tests;  // candidate-transaction tests so far
   unsigned long long work;   // algorithmic integer ops of the count kernels
+  unsigned long long gram_rows;  // block rows whose pair cohort the GEMM counted
 };
 
 // Add a per-thread amount to a 64-bit counter with one atomic per warp.

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   if (ncand <= BS_DIRECT_MAX) {
     // few candidates: no shared tiles; a warp per candidate ANDs its columns
     // straight from the (L2-resident) column buffer
-    bs_count_direct<TW>(L, C, g, lo, tail, nw32, pruned, solid);
+    bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid);
   } else {
     uint32_t chunk = (ncand + gridDim.x - 1) / gridDim.x;
     chunk = (chunk + 3) & ~3u;
@@ -125,9 +125,25 @@ __global__ void __launch_bounds__(256) k_settle_pairs(Lattice L) {
   if (!L.pair_end || g > L.stop_max) return;
   const uint32_t head = C->head, end = L.pair_end < C->tail ? L.pair_end : C->tail;
   uint32_t pruned = 0, solid = 0;
-  for (uint32_t c = head + blockIdx.x * blockDim.x + threadIdx.x; c < end;
-       c += gridDim.x * blockDim.x)
-    settle_record(L, C, c, L.csupp[c], g, true, pruned, solid);
+  // four records per thread, all loads issued before any is used
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t c = head + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < end;
+       c += 4 * stride) {
+    uint8_t sh[4];
+    uint32_t sp[4], bi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t cc = c + u * stride;
+      const bool in = cc < end;
+      sh[u] = in ? L.cshape[cc] : (uint8_t)SH_NIL;
+      sp[u] = in ? L.csupp[cc] : 0u;
+      bi[u] = in ? L.cbirth[cc] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      settle_loaded(L, C, (uint32_t)(c + u * stride), sh[u], bi[u], sp[u], g, true, pruned,
+                    solid);
+  }
   if (pruned) atomicAdd(&C->n_pruned, pruned);
   if (solid) atomicAdd(&C->n_solid, solid);
 }

@@ -17,8 +17,10 @@
 //                   of bulk copies (cp.async.bulk + mbarrier) feeds
 //                   tcgen05.mma.kind::f8f6f4 (M = N = 128, K = 32 per
 //                   instruction, fp32 accumulation in TMEM); tcgen05.ld
-//                   brings each thread one row of the 128x128 tile and the
-//                   counts of pairs a < b are added to their records.
+//                   brings each thread one row of the 128x128 tile; the
+//                   rows are turned through shared memory so that the
+//                   counts of pairs a < b are added to 32 consecutive
+//                   records per warp instruction.
 //
 // Exactness: every product is 0 or 1 and a tile's sum over one split is at
 // most its rows (< 2^24), so fp32 accumulation is exact.
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(256) k_gram_operand(Lattice L, uint8_t *__rest
   uint64_t first, last;
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
   const uint32_t nrows = (uint32_t)(last - first);
+  if (blockIdx.x == 0 && threadIdx.x == 0) C->gram_rows += nrows;
   const uint32_t nkc = (nrows + GK - 1) / GK;
   const uint32_t ngroups = nkc * (GK / 32);  // 32-row groups, incl. zero padding
   const uint32_t lane = threadIdx.x & 31;
@@ -81,17 +84,8 @@ __global__ void __launch_bounds__(256) k_gram_operand(Lattice L, uint8_t *__rest
     const uint32_t grp = (uint32_t)(it / L.wc), j = (uint32_t)(it % L.wc);
     const uint32_t t = grp * 32 + lane;
     const uint64_t x = t < nrows ? __ldg(L.rows + (first + t) * L.wc + j) : 0ull;
-    uint32_t lo = 0, hi = 0;
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> b) & 1u);
-      if ((int)lane == b) lo = v;
-    }
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> (b + 32)) & 1u);
-      if ((int)lane == b) hi = v;
-    }
+    const uint32_t lo = warp_transpose32((uint32_t)x);
+    const uint32_t hi = warp_transpose32((uint32_t)(x >> 32));
     // lane handles ranks r0 = 64j + lane and r1 = r0 + 32: 32 rows each
     const uint32_t kc = (grp * 32) / GK, k0 = (grp * 32) % GK;
 #pragma unroll
@@ -275,8 +269,12 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
   if (threadIdx.x == 0 && !ok) C->error = 5;  // DIC_ETIMEOUT
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
+    // Each warp stages its 32 x 32 sub-tiles through shared memory (the
+    // operand ring is idle once `done` has fired) so that a warp's adds go
+    // to 32 consecutive counters: lane q adds count (a, b0 + q) of row a.
     const uint64_t l1 = L.l1;
-    const uint64_t a = (uint64_t)ti * GT + warp * 32 + lane;
+    uint32_t *stage = reinterpret_cast<uint32_t *>(stage_a) + warp * (32 * 33);
+    const uint64_t a0 = (uint64_t)ti * GT + warp * 32;
     for (uint32_t c0 = 0; c0 < GT; c0 += 32) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((warp * 32u) << 16) + c0;
@@ -292,16 +290,18 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (a < l1) {
+      const uint64_t b = (uint64_t)tj * GT + c0 + lane;
+      if (a0 >= l1 || (uint64_t)tj * GT + c0 + 31 <= a0) continue;  // all b <= a (warp-uniform)
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const uint64_t b = (uint64_t)tj * GT + c0 + q;
-          if (b > a && b < l1) {
-            const uint32_t cnt = (uint32_t)__uint_as_float(v[q]);
-            if (cnt) atomicAdd(&L.csupp[gram_pair_index(a, b, l1)], cnt);
-          }
-        }
+      for (int q = 0; q < 32; ++q) stage[lane * 33 + q] = (uint32_t)__uint_as_float(v[q]);
+      __syncwarp();
+      const uint32_t rmax = l1 - a0 < 32 ? (uint32_t)(l1 - a0) : 32u;
+      for (uint32_t r = 0; r < rmax; ++r) {
+        const uint64_t a = a0 + r;
+        const uint32_t cnt = stage[r * 33 + lane];
+        if (b > a && b < l1 && cnt) atomicAdd(&L.csupp[gram_pair_index(a, b, l1)], cnt);
       }
+      __syncwarp();
     }
   } else if (threadIdx.x == 0) {
     // let the copies already issued land before the shared memory goes away

@@ -82,12 +82,12 @@ __device__ __forceinline__ void promote_record(const Lattice &L, Ctrl *C, uint32
 // bound s + M * (stop_max - stop) is below minsup is erased (stop = g -
 // birth, the blocks counted so far). Tallies records completing their full
 // pass (every live one is a box there). Returns nothing; updates tallies.
-__device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_t c, uint32_t s,
-                                              uint32_t g, bool insert, uint32_t &pruned,
-                                              uint32_t &solid) {
-  uint8_t sh = L.cshape[c];
+// This form takes the record's shape and birth stop already loaded.
+__device__ __forceinline__ void settle_loaded(const Lattice &L, Ctrl *C, uint32_t c, uint8_t sh,
+                                              uint32_t birth, uint32_t s, uint32_t g,
+                                              bool insert, uint32_t &pruned, uint32_t &solid) {
   if (sh == SH_NIL) return;
-  const uint32_t age = g - L.cbirth[c];
+  const uint32_t age = g - birth;
   if (sh == SH_CIRCLE) {
     if (s >= L.minsup) {
       promote_record(L, C, c, g, insert);
@@ -98,6 +98,14 @@ __device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_
     }
   }
   if (age == L.stop_max) ++solid;
+}
+
+__device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_t c, uint32_t s,
+                                              uint32_t g, bool insert, uint32_t &pruned,
+                                              uint32_t &solid) {
+  const uint8_t sh = L.cshape[c];
+  if (sh == SH_NIL) return;
+  settle_loaded(L, C, c, sh, L.cbirth[c], s, g, insert, pruned, solid);
 }
 
 // MAKECANDIDATES for one (record promoted at g, rank r) pair: C = A | r is
@@ -185,6 +193,22 @@ __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
 }
 
 
+// Transpose a 32x32 bit block held one row per lane (bit b of lane t's word
+// = element (t, b)) so that lane b ends with column b (bit t = element (t,
+// b)). Five exchange stages: at distance j, the j x j off-diagonal
+// sub-blocks of every 2j x 2j block swap places.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lo_masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const uint32_t j = 16u >> st, mlo = lo_masks[st];
+    const uint32_t v = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~mlo) | ((v >> j) & mlo)) : ((x & mlo) | ((v << j) & ~mlo));
+  }
+  return x;
+}
+
 // BITSLICE column stride of a tile row (words): TW + 4 for TW = 8, 16 and TW
 // for TW = 4, so rows start on 16-byte boundaries and eight threads reading
 // consecutive ranks with 128-bit loads hit distinct banks.
@@ -209,17 +233,9 @@ __device__ __forceinline__ void slice_block_warps(const Lattice &L, uint32_t g, 
     const uint32_t w = (uint32_t)(it / wc), j = (uint32_t)(it % wc);
     const uint64_t row = first + 32ull * w + lane;
     const uint64_t x = (w < nw32 && row < last) ? __ldg(L.rows + row * wc + j) : 0ull;
-    uint32_t lo = 0, hi = 0;
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> b) & 1u);
-      if ((int)lane == b) lo = v;
-    }
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const uint32_t v = __ballot_sync(0xffffffffu, (uint32_t)(x >> (b + 32)) & 1u);
-      if ((int)lane == b) hi = v;
-    }
+    // lane b gets the 32 rows' bits of ranks 64j+b (lo) and 64j+32+b (hi)
+    const uint32_t lo = warp_transpose32((uint32_t)x);
+    const uint32_t hi = warp_transpose32((uint32_t)(x >> 32));
     const uint32_t t = w / tw, wi = w % tw;
     const uint32_t r0 = j * 64 + lane, r1 = r0 + 32;
     const uint64_t i0 = ((uint64_t)t * l1p + r0) * st + wi, i1 = ((uint64_t)t * l1p + r1) * st + wi;

@@ -41,7 +41,9 @@ class Stats(ctypes.Structure):
                 ("firstpass_ms", ctypes.c_double), ("mine_ms", ctypes.c_double),
                 ("path_launches", ctypes.c_uint32 * 4), ("count_ops", ctypes.c_uint64),
                 ("gram_ms", ctypes.c_double), ("gram_launches", ctypes.c_uint64),
-                ("settle_ms", ctypes.c_double)]
+                ("settle_ms", ctypes.c_double), ("gen_ms", ctypes.c_double),
+                ("gen_launches", ctypes.c_uint64), ("gram_flops", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 5)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "path_launches")}
@@ -228,20 +230,38 @@ def _result(h) -> Result:
     return Result(W, masks[:cnt], k[:cnt], sp[:cnt], tr[:tl], st.as_dict())
 
 
+PROFILE_BITS = {"count": 1, "gram": 2, "settle": 4, "gen": 8}
+PROFILE_ALL = 15
+
+
+def profile_mask(profile) -> int:
+    """True -> every kind; False/None -> none; an int is the DIC_PROFILE_*
+    bitmask; a name or list of names from PROFILE_BITS selects kinds."""
+    if profile is True:
+        return PROFILE_ALL
+    if not profile:
+        return 0
+    if isinstance(profile, int):
+        return profile & PROFILE_ALL
+    if isinstance(profile, str):
+        profile = [profile]
+    return sum(PROFILE_BITS[k] for k in set(profile))
+
+
 def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
-            profile: bool = False, max_candidates: int = 0) -> Options:
+            profile=False, max_candidates: int = 0) -> Options:
     o = Options()
     _lib.dic_options_init(ctypes.byref(o))
     o.count_path = PATHS[path]
     o.steps_per_sync = steps_per_sync
     o.use_graph = 1 if use_graph else 0
-    o.profile = 1 if profile else 0
+    o.profile = profile_mask(profile)
     o.max_candidates = max_candidates
     return o
 
 
 def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
-         profile: bool = False, steps_per_sync: int = 0, use_graph: bool = True,
+         profile=False, steps_per_sync: int = 0, use_graph: bool = True,
          max_candidates: int = 0) -> Result:
     """All itemsets with support >= minsup (integer count), blocks of M rows."""
     o = options(path, steps_per_sync, use_graph, profile, max_candidates)
@@ -251,7 +271,7 @@ def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
     return _result(h)
 
 
-def mine_batch(dbs, minsups, Ms, path: str = "auto", profile: bool = False):
+def mine_batch(dbs, minsups, Ms, path: str = "auto", profile=False):
     """Mine several (db, minsup, M) queries together; returns a list of Result."""
     cnt = len(dbs)
     handles = (ctypes.c_void_p * max(cnt, 1))(*[d.handle.value for d in dbs])
