@@ -49,7 +49,7 @@ COUNT_KERNELS = {1: "k_count_rows", 2: "k_count_bitslice", 3: "k_count_bitslice"
 FP8_PER_BF16 = 2.0
 # timed kinds of the stop loop: stats key prefix -> profile name, kernels
 KINDS = {"count": "count", "gram": "gram", "settle": "settle", "gen": "gen"}
-KIND_KERNELS = {"gram": "k_gram_operand + k_gram_pairs", "settle": "k_settle_pairs",
+KIND_KERNELS = {"gram": "k_gram_pairs", "settle": "k_settle_pairs",
                 "gen": "k_generate_finish"}
 
 

@@ -56,8 +56,8 @@ void dic::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
 #define TRY(expr)                      \
   do {                                 \
-    dic_status s_ = (expr);            \
-    if (s_ != DIC_OK) return s_;       \
+    dic_status st_ = (expr);           \
+    if (st_ != DIC_OK) return st_;     \
   } while (0)
 
 // ---------------------------------------------------------------- objects
@@ -318,12 +318,15 @@ class Miner {
     if (h_cnt1_) { cudaFreeHost(h_cnt1_); h_cnt1_ = nullptr; }
     if (fa_) { cudaEventDestroy(fa_); fa_ = nullptr; }
     if (fb_) { cudaEventDestroy(fb_); fb_ = nullptr; }
+    if (ev_fork_) { cudaEventDestroy(ev_fork_); ev_fork_ = nullptr; }
+    if (ev_join_) { cudaEventDestroy(ev_join_); ev_join_ = nullptr; }
+    if (s2_) { cudaStreamDestroy(s2_); s2_ = nullptr; }
   }
 
   dic_status grow_candidates(uint32_t need);
   dic_status grow_hash(uint64_t entries);
   dic_status next_event(cudaEvent_t *ev);
-  dic_status record(cudaEvent_t ev);
+  dic_status record(cudaEvent_t ev, cudaStream_t st);
   dic_status harvest_events();
   dic_status grow_trace(uint32_t need);
   dic_status launch_phase(int phase);
@@ -345,8 +348,8 @@ class Miner {
   std::vector<Interval> intervals_;
   size_t iv_start_ = 0;
   int iv_kind_ = 0;
-  dic_status iv_open(int kind);
-  dic_status iv_close();
+  dic_status iv_open(int kind, cudaStream_t st);
+  dic_status iv_close(cudaStream_t st);
   bool prof(uint32_t bit) const { return (opt_.profile & bit) != 0; }
   double settle_ms_ = 0, gen_ms_ = 0;
   uint64_t gen_timed_ = 0;
@@ -367,9 +370,9 @@ class Miner {
   bool next_v_ready_ = false;  // the enqueued work builds V for the next count
   // TENSOR path (pair cohort on tcgen05)
   bool tc_ok_ = false;
-  uint8_t *tc_X_ = nullptr;
-  uint64_t tc_xbytes_ = 0;
   uint32_t tc_nkc_max_ = 0, tc_nsplit_ = 1;
+  cudaStream_t s2_ = nullptr;  // side stream of the pair-cohort kernels
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   uint32_t pred_step_ = 1;     // stop number the next enqueued count runs at
   double gram_ms_ = 0;
   uint64_t gram_timed_ = 0;
@@ -426,13 +429,13 @@ static int kr_bucket(uint32_t max_k) {
 
 // Record a profiling event; inside a stream capture it must become an event
 // record node of the graph (a plain record would only add a dependency).
-dic_status Miner::record(cudaEvent_t ev) {
+dic_status Miner::record(cudaEvent_t ev, cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  CU(cudaStreamIsCapturing(s_, &cs));
+  CU(cudaStreamIsCapturing(st, &cs));
   if (cs == cudaStreamCaptureStatusActive)
-    CU(cudaEventRecordWithFlags(ev, s_, cudaEventRecordExternal));
+    CU(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
   else
-    CU(cudaEventRecord(ev, s_));
+    CU(cudaEventRecord(ev, st));
   return DIC_OK;
 }
 
@@ -448,19 +451,19 @@ dic_status Miner::next_event(cudaEvent_t *ev) {
 
 // Sum the count-kernel event pairs recorded since the last group (the
 // stream has been synchronised).
-dic_status Miner::iv_open(int kind) {
+dic_status Miner::iv_open(int kind, cudaStream_t st) {
   cudaEvent_t e;
   TRY(next_event(&e));
-  TRY(record(e));
+  TRY(record(e, st));
   iv_start_ = ev_used_ - 1;
   iv_kind_ = kind;
   return DIC_OK;
 }
 
-dic_status Miner::iv_close() {
+dic_status Miner::iv_close(cudaStream_t st) {
   cudaEvent_t e;
   TRY(next_event(&e));
-  TRY(record(e));
+  TRY(record(e, st));
   intervals_.push_back({iv_start_, ev_used_ - 1, iv_kind_});
   return DIC_OK;
 }
@@ -503,32 +506,35 @@ dic_status Miner::launch_phase(int phase) {
         next_v_ready_ = false;
         const bool gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
         if (e == cudaSuccess && gram) {
-          // the pair cohort on the tensor cores (it is in DASHED up to stop_max)
-          if (prof(DIC_PROFILE_GRAM)) TRY(iv_open(IV_GRAM));
-          e = launch_gram_operand(L_, tc_X_, tc_nkc_max_, tc_xbytes_, (uint32_t)kre, s_);
-          if (e == cudaSuccess)
-            e = launch_gram_pairs(L_, tc_X_, tc_nkc_max_, tc_nsplit_, (uint32_t)kre, s_);
-          if (prof(DIC_PROFILE_GRAM)) TRY(iv_close());
+          // fork: the pair cohort (in DASHED up to stop_max) is counted on the
+          // tensor cores and pruned on the side stream while the rest of the
+          // window is counted here; generation waits for both
+          CU(cudaEventRecord(ev_fork_, s_));
+          CU(cudaStreamWaitEvent(s2_, ev_fork_, 0));
+          if (prof(DIC_PROFILE_GRAM)) TRY(iv_open(IV_GRAM, s2_));
+          e = launch_gram_pairs(L_, tc_nsplit_, (uint32_t)kre, s2_);
+          if (prof(DIC_PROFILE_GRAM)) TRY(iv_close(s2_));
+          if (e == cudaSuccess) {
+            if (prof(DIC_PROFILE_SETTLE)) TRY(iv_open(IV_SETTLE, s2_));
+            e = launch_settle_pairs(L_, grid_, (uint32_t)kre, s2_);
+            if (prof(DIC_PROFILE_SETTLE)) TRY(iv_close(s2_));
+          }
+          CU(cudaEventRecord(ev_join_, s2_));
           launches_ += 2;
           path_launches_[DIC_COUNT_TENSOR]++;
         }
         if (e == cudaSuccess) {
-          if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT));
+          if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT, s_));
           e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_,
                                     bs_grid_, s_);
-          if (prof(DIC_PROFILE_COUNT)) TRY(iv_close());
+          if (prof(DIC_PROFILE_COUNT)) TRY(iv_close(s_));
         }
-        if (e == cudaSuccess && gram) {
-          if (prof(DIC_PROFILE_SETTLE)) TRY(iv_open(IV_SETTLE));
-          e = launch_settle_pairs(L_, grid_, s_);
-          if (prof(DIC_PROFILE_SETTLE)) TRY(iv_close());
-          ++launches_;
-        }
+        if (gram) CU(cudaStreamWaitEvent(s_, ev_join_, 0));  // join
         path_launches_[DIC_COUNT_BITSLICE]++;
       } else {
-        if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT));
+        if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT, s_));
         e = launch_count_rows(L_, (int)nw_, grid_, s_);
-        if (prof(DIC_PROFILE_COUNT)) TRY(iv_close());
+        if (prof(DIC_PROFILE_COUNT)) TRY(iv_close(s_));
         path_launches_[DIC_COUNT_ROWS]++;
       }
       break;
@@ -537,9 +543,9 @@ dic_status Miner::launch_phase(int phase) {
     case PH_HASH: e = launch_hash_insert(L_, grid_, s_); break;
     case PH_GEN: {
       const bool slice = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
-      if (prof(DIC_PROFILE_GEN)) TRY(iv_open(IV_GEN));
+      if (prof(DIC_PROFILE_GEN)) TRY(iv_open(IV_GEN, s_));
       e = launch_generate_finish(L_, grid_, slice, s_);
-      if (prof(DIC_PROFILE_GEN)) TRY(iv_close());
+      if (prof(DIC_PROFILE_GEN)) TRY(iv_close(s_));
       next_v_ready_ = slice;
       ++pred_step_;
       break;
@@ -802,12 +808,13 @@ dic_status Miner::prepare() {
       tc_ok_ = false;
       if (want && bs_ok_ && blockmax < (1ull << 24) && npairs <= 0xFFFFFFF0ull) {
         tc_nkc_max_ = gram_chunks(blockmax);
-        tc_xbytes_ = gram_operand_bytes(l1, blockmax);
-        TRY(alloc(&tc_X_, tc_xbytes_, true));
         const uint32_t nt = gram_tiles(l1), ntp = nt * (nt + 1) / 2;
         const uint32_t sms = (uint32_t)sm_count();
-        // one CTA per SM (the ring takes ~144 KiB): a single wave of splits
+        // one CTA per SM (the ring takes 128 KiB): a single wave of splits
         tc_nsplit_ = std::max<uint32_t>(1, std::min<uint32_t>(tc_nkc_max_, sms / ntp));
+        if (!s2_) CU(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
+        if (!ev_fork_) CU(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+        if (!ev_join_) CU(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
         L_.pair_end = (uint32_t)npairs;
         tc_ok_ = true;
       }

@@ -103,6 +103,26 @@ struct Lattice {
   uint32_t pad2;
 };
 
+// The pair-cohort kernels of the TENSOR path (GEMM and its PRUNE, which run
+// beside the BITSLICE count of the same stop) make the same checks as that
+// count, which may stall on the kernel width or the box-set room before
+// changing anything; they do nothing when it will stall, so a stop re-run
+// after a stall never counts its pairs twice. Reads only values no kernel of
+// the stop changes.
+__device__ __forceinline__ bool gram_may_run(const Lattice &L, const Ctrl *C, uint32_t kre) {
+  if (C->stall || C->done) return false;
+  if (C->max_k > kre) return false;
+  if ((uint64_t)(C->hash_used + C->n_live) * 2 > L.hcap) return false;
+  return C->step <= L.stop_max && C->head == 0;  // the pair cohort is in DASHED
+}
+
+// Record index of pair {a, b} (ranks a < b < l1): the first-pass pair join
+// writes all pairs of frequent ranks as records 0 .. l1(l1-1)/2 - 1 in
+// lexicographic order, before any other record.
+__host__ __device__ __forceinline__ uint64_t pair_record(uint64_t a, uint64_t b, uint64_t l1) {
+  return a * (2 * l1 - a - 1) / 2 + (b - a - 1);
+}
+
 // Block [first, last) of global stop g (1-based), with rewind (Algorithm 2).
 __host__ __device__ inline void block_of(uint32_t g, uint32_t stop_max, uint64_t M, uint64_t n,
                                          uint32_t *stop, uint64_t *first, uint64_t *last) {
@@ -166,16 +186,13 @@ cudaError_t launch_batch_gen(const Lattice *Ls, uint32_t Q, uint32_t slice_offse
 // TENSOR path for the pair cohort (kernels_count_tensor.cu).
 uint32_t gram_tiles(uint32_t l1);
 uint32_t gram_chunks(uint64_t rows);
-uint64_t gram_operand_bytes(uint32_t l1, uint64_t block_rows);
-// Both do nothing when the BITSLICE count of the same stop (kre ranks) will
-// stall, so a re-run stop never counts its pairs twice.
-cudaError_t launch_gram_operand(Lattice L, uint8_t *X, uint32_t nkc_max, uint64_t xbytes,
-                                uint32_t kre, cudaStream_t s);
-cudaError_t launch_gram_pairs(Lattice L, const uint8_t *X, uint32_t nkc_max, uint32_t nsplit,
-                              uint32_t kre, cudaStream_t s);
+// Reads the stop's bit columns L.V (so it needs L.tw in {4, 8, 16}); does
+// nothing when the BITSLICE count of the same stop (kre ranks) will stall,
+// so a re-run stop never counts its pairs twice.
+cudaError_t launch_gram_pairs(Lattice L, uint32_t nsplit, uint32_t kre, cudaStream_t s);
 
 // PRUNE for the pair cohort counted by the tensor path (one thread per record).
-cudaError_t launch_settle_pairs(Lattice L, int grid, cudaStream_t s);
+cudaError_t launch_settle_pairs(Lattice L, int grid, uint32_t kre, cudaStream_t s);
 
 // Largest candidate chunk whose bitslice shared-memory footprint fits.
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit);

@@ -118,11 +118,10 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
 
 // PRUNE (Algorithm 4) for the pair cohort after the tensor kernel has added
 // this stop's counts: one thread per record.
-__global__ void __launch_bounds__(256) k_settle_pairs(Lattice L) {
+__global__ void __launch_bounds__(256) k_settle_pairs(Lattice L, uint32_t kre) {
   Ctrl *C = L.ctrl;
-  if (C->stall || C->done) return;
+  if (!L.pair_end || !gram_may_run(L, C, kre)) return;
   const uint32_t g = C->step;
-  if (!L.pair_end || g > L.stop_max) return;
   const uint32_t head = C->head, end = L.pair_end < C->tail ? L.pair_end : C->tail;
   uint32_t pruned = 0, solid = 0;
   // four records per thread, all loads issued before any is used
@@ -148,8 +147,8 @@ __global__ void __launch_bounds__(256) k_settle_pairs(Lattice L) {
   if (solid) atomicAdd(&C->n_solid, solid);
 }
 
-cudaError_t launch_settle_pairs(Lattice L, int grid, cudaStream_t s) {
-  k_settle_pairs<<<grid, 256, 0, s>>>(L);
+cudaError_t launch_settle_pairs(Lattice L, int grid, uint32_t kre, cudaStream_t s) {
+  k_settle_pairs<<<grid, 256, 0, s>>>(L, kre);
   return cudaGetLastError();
 }
 

@@ -8,26 +8,25 @@
 // so pair {a, b} is record pair_off(a) + b - a - 1 and the GEMM's output
 // element (a, b) goes straight to its counter.
 //
-//   k_gram_operand  the stop's block as an e4m3 0/1 matrix X (1.0 = 0x38),
-//                   ranks x rows, in the K-major no-swizzle core-matrix
-//                   layout of tcgen05 (8 rows x 16 bytes per core matrix),
-//                   one contiguous 16 KiB block per (128-rank tile, 128-row
-//                   chunk)
-//   k_gram_pairs    one CTA per (tile pair i <= j, K split): a 4-stage ring
-//                   of bulk copies (cp.async.bulk + mbarrier) feeds
-//                   tcgen05.mma.kind::f8f6f4 (M = N = 128, K = 32 per
-//                   instruction, fp32 accumulation in TMEM); tcgen05.ld
-//                   brings each thread one row of the 128x128 tile; the
-//                   rows are turned through shared memory so that the
-//                   counts of pairs a < b are added to 32 consecutive
-//                   records per warp instruction.
+// k_gram_pairs: one CTA per (128-rank tile pair i <= j, K split). The
+// operands come from the stop's bit columns V (the BITSLICE transposition,
+// 32 rows per word): for every 128-row chunk, sixteen expander warps load
+// each rank's four column words (a few chunks ahead) and write them to
+// shared memory as e4m3 0/1 bytes (1.0 = 0x38) in the K-major no-swizzle
+// core-matrix layout of tcgen05 (8 ranks x 16 rows per 128-byte core
+// matrix), through a 4-stage ring guarded by mbarriers; one thread of a
+// seventeenth warp issues
+// tcgen05.mma.kind::f8f6f4 (M = N = 128, K = 32 per instruction, fp32
+// accumulation in tensor memory). The epilogue brings the 128x128 tile out
+// with tcgen05.ld, turns its rows through shared memory and adds the counts
+// of pairs a < b to 32 consecutive records per warp instruction.
 //
 // Exactness: every product is 0 or 1 and a tile's sum over one split is at
 // most its rows (< 2^24), so fp32 accumulation is exact.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up records
-// DIC_ETIMEOUT in the loop state, lets the copies already issued land, frees
-// the tensor memory and returns.
+// DIC_ETIMEOUT in the loop state, lets the tensor instructions already
+// issued finish, frees the tensor memory and returns.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -40,80 +39,23 @@ constexpr uint32_t GT = 128;             // ranks per tile (M = N)
 constexpr uint32_t GK = 128;             // rows (K) per chunk = bytes per row of a tile
 constexpr uint32_t GSTAGES = 4;
 constexpr uint32_t GTILE_BYTES = GT * GK;  // 16 KiB
-constexpr uint32_t GRAM_THREADS = 128;
+constexpr uint32_t GEXP_WARPS = 16;      // expander / epilogue warps
+constexpr uint32_t GPREFETCH = 4;        // chunks of column words loaded ahead
+constexpr uint32_t GEXP_THREADS = GEXP_WARPS * 32;
+constexpr uint32_t GRAM_THREADS = GEXP_THREADS + 32;  // + the MMA warp
 constexpr long long WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz before giving up
 constexpr uint8_t E4M3_ONE = 0x38;
 
-// ------------------------------------------------------------ operand X
-// Byte offset of element (rank r, row k) inside its 16 KiB tile block:
-// core matrix (r/8, k/16) at (r/8)*1024 + (k/16)*128, element (r%8)*16 + k%16.
+// Byte offset of element (rank r, row k) inside a 16 KiB tile: core matrix
+// (r/8, k/16) at (r/8)*1024 + (k/16)*128, element (r%8)*16 + k%16.
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t k) {
   return (r >> 3) * 1024u + (k >> 4) * 128u + (r & 7u) * 16u + (k & 15u);
 }
 
-// X block for (rank tile ti, chunk kc) starts at ((ti * nkc) + kc) * 16 KiB.
-// The BITSLICE count that follows in the same stop checks (and may stall
-// on) the kernel width and the box-set room before changing anything; the
-// pair-cohort kernels make the same checks and do nothing when that count
-// will stall, so a stop re-run after a stall never counts its pairs twice.
-__device__ __forceinline__ bool gram_may_run(const Lattice &L, const Ctrl *C, uint32_t kre) {
-  if (C->stall || C->done) return false;
-  if (C->max_k > kre) return false;
-  if ((uint64_t)(C->hash_used + C->n_live) * 2 > L.hcap) return false;
-  return C->step <= L.stop_max && C->head == 0;  // the pair cohort is in DASHED
-}
-
-__global__ void __launch_bounds__(256) k_gram_operand(Lattice L, uint8_t *__restrict__ X,
-                                                      uint32_t nkc_max, uint64_t xbytes,
-                                                      uint32_t kre) {
-  Ctrl *C = L.ctrl;
-  if (!gram_may_run(L, C, kre)) return;
-  const uint32_t g = C->step;
-  uint32_t stop;
-  uint64_t first, last;
-  block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
-  const uint32_t nrows = (uint32_t)(last - first);
-  if (blockIdx.x == 0 && threadIdx.x == 0) C->gram_rows += nrows;
-  const uint32_t nkc = (nrows + GK - 1) / GK;
-  const uint32_t ngroups = nkc * (GK / 32);  // 32-row groups, incl. zero padding
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t items = (uint64_t)ngroups * L.wc;
-  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
-       it += nwarps) {
-    const uint32_t grp = (uint32_t)(it / L.wc), j = (uint32_t)(it % L.wc);
-    const uint32_t t = grp * 32 + lane;
-    const uint64_t x = t < nrows ? __ldg(L.rows + (first + t) * L.wc + j) : 0ull;
-    const uint32_t lo = warp_transpose32((uint32_t)x);
-    const uint32_t hi = warp_transpose32((uint32_t)(x >> 32));
-    // lane handles ranks r0 = 64j + lane and r1 = r0 + 32: 32 rows each
-    const uint32_t kc = (grp * 32) / GK, k0 = (grp * 32) % GK;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t r = j * 64 + lane + 32 * h;
-      const uint32_t bits = h ? hi : lo;
-      const uint32_t ti = r / GT, rr = r % GT;
-      const uint64_t base = ((uint64_t)ti * nkc_max + kc) * GTILE_BYTES;
-#pragma unroll
-      for (int part = 0; part < 2; ++part) {  // rows k0+16*part .. +15
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t nib = (bits >> (16 * part + 4 * q)) & 0xFu;
-          w[q] = ((nib & 1u) ? (uint32_t)E4M3_ONE : 0u) |
-                 ((nib & 2u) ? (uint32_t)E4M3_ONE << 8 : 0u) |
-                 ((nib & 4u) ? (uint32_t)E4M3_ONE << 16 : 0u) |
-                 ((nib & 8u) ? (uint32_t)E4M3_ONE << 24 : 0u);
-        }
-        const uint64_t off = base + core_offset(rr, k0 + 16 * part);
-        if (off + 16 > xbytes) {  // internal sizing error: record, skip
-          C->error = DIC_INTERNAL_BOUNDS;
-          continue;
-        }
-        *reinterpret_cast<uint4 *>(X + off) = make_uint4(w[0], w[1], w[2], w[3]);
-      }
-    }
-  }
+// Four 0/1 bits -> four bytes of 0 or e4m3 1.0: the multiply places bit q at
+// bit 8q (its other copies land on bits the mask clears; no carries).
+__device__ __forceinline__ uint32_t expand4(uint32_t nib) {
+  return ((nib * 0x00204081u) & 0x01010101u) * (uint32_t)E4M3_ONE;
 }
 
 // ---------------------------------------------------------- PTX helpers
@@ -123,10 +65,8 @@ __device__ __forceinline__ uint32_t sm_addr(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(bar)), "r"(count));
 }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(bar)),
-               "r"(bytes)
-               : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
@@ -147,12 +87,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(sm_addr(dst)), "l"(src), "r"(bytes), "r"(sm_addr(bar))
-      : "memory");
+// Generic-proxy shared-memory writes -> visible to the tensor core's reads.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 // Shared-memory operand descriptor: K-major, no swizzle; leading byte offset
 // = distance between core matrices along K, stride byte offset = distance
@@ -179,26 +116,37 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
       : "memory");
 }
 
-__device__ __forceinline__ uint64_t gram_pair_index(uint64_t a, uint64_t b, uint64_t l1) {
-  return a * (2 * l1 - a - 1) / 2 + (b - a - 1);
-}
 
 // ------------------------------------------------------------------ GEMM
-__global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
-                                                                const uint8_t *__restrict__ X,
-                                                                uint32_t ntile, uint32_t nkc_max,
+// Expand 32 rows of one rank's column (bit j of w = row 32 q0 + j of the
+// chunk) into the tile at rank row rr (arithmetic only: no shared-memory
+// reads beside the tensor core's).
+__device__ __forceinline__ void expand_rows32(uint8_t *tile, uint32_t rr, uint32_t q0,
+                                              uint32_t w) {
+#pragma unroll
+  for (uint32_t h = 0; h < 2; ++h) {  // 16 rows each
+    const uint32_t x = w >> (16 * h);
+    *reinterpret_cast<uint4 *>(tile + core_offset(rr, 32 * q0 + 16 * h)) =
+        make_uint4(expand4(x & 0xFu), expand4((x >> 4) & 0xFu), expand4((x >> 8) & 0xFu),
+                   expand4((x >> 12) & 0xFu));
+  }
+}
+
+__global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint32_t ntile,
                                                                 uint32_t nsplit, uint32_t kre) {
   extern __shared__ __align__(1024) uint8_t gsm[];
   __shared__ __align__(8) uint64_t full[GSTAGES], empty[GSTAGES], done;
   __shared__ uint32_t tmem_base;
-  __shared__ uint32_t failed;
+  __shared__ volatile uint32_t failed;
   Ctrl *C = L.ctrl;
   if (!gram_may_run(L, C, kre)) return;
   const uint32_t g = C->step;
   uint32_t stop;
   uint64_t first, last;
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
-  const uint32_t nkc = (uint32_t)((last - first + GK - 1) / GK);
+  const uint32_t nrows = (uint32_t)(last - first);
+  if (blockIdx.x == 0 && threadIdx.x == 0) C->gram_rows += nrows;
+  const uint32_t nkc = (nrows + GK - 1) / GK;
   // which tile pair (ti <= tj) and which K split
   const uint32_t pair = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
   uint32_t ti = 0, rem = pair;
@@ -215,12 +163,15 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (uint32_t s = 0; s < GSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (uint32_t s = 0; s < GSTAGES; ++s) {
+      mbar_init(&full[s], GEXP_WARPS);
+      mbar_init(&empty[s], 1);
+    }
     mbar_init(&done, 1);
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {  // tensor memory: 128 columns of 128 lanes (fp32 accumulators)
+  if (warp == GEXP_WARPS) {  // tensor memory: 128 columns of 128 lanes (fp32)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;"
                  ::"r"(sm_addr(&tmem_base)) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -230,27 +181,55 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  const uint8_t *XA = X + ((uint64_t)ti * nkc_max) * GTILE_BYTES;
-  const uint8_t *XB = X + ((uint64_t)tj * nkc_max) * GTILE_BYTES;
-  uint32_t issued = 0;  // stages handed to the copy engine by the producer
-
-  if (threadIdx.x == 0) {
-    // producer: bulk copies of the A and B tiles of each K chunk
-    for (uint32_t i = 0; i < nk; ++i) {
-      const uint32_t s = i % GSTAGES, use = i / GSTAGES;
-      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) { failed = 1; break; }
-      mbar_expect_tx(&full[s], 2 * GTILE_BYTES);
-      bulk_g2s(stage_a + s * GTILE_BYTES, XA + (uint64_t)(kc0 + i) * GTILE_BYTES, GTILE_BYTES,
-               &full[s]);
-      bulk_g2s(stage_b + s * GTILE_BYTES, XB + (uint64_t)(kc0 + i) * GTILE_BYTES, GTILE_BYTES,
-               &full[s]);
-      ++issued;
+  if (warp < GEXP_WARPS) {
+    // expanders: thread (rank rr, quarter q0) writes rows [32 q0, 32 q0 + 32)
+    // of rank rr of both tiles for every chunk; the column words of the next
+    // GPREFETCH chunks are in flight while a chunk is expanded
+    const uint32_t rr = threadIdx.x % GT, q0 = threadIdx.x / GT;
+    const uint64_t ra = (uint64_t)ti * GT + rr, rb = (uint64_t)tj * GT + rr;
+    const bool oka = ra < L.l1, okb = rb < L.l1;
+    const uint32_t tw = L.tw, st = bs_stride((int)tw), l1p = L.l1p;
+    const uint32_t tw_shift = __ffs(tw) - 1;  // tw is 4, 8 or 16
+    const uint32_t *__restrict__ V = L.V;
+    auto load = [&](uint32_t kc, uint64_t r, bool ok) -> uint32_t {
+      const uint32_t w0 = kc * (GK / 32) + q0;  // 32-row word of this quarter
+      const uint64_t t = w0 >> tw_shift, wi = w0 & (tw - 1);
+      return ok ? __ldg(V + (t * l1p + r) * st + wi) : 0u;
+    };
+    uint32_t qa[GPREFETCH], qb[GPREFETCH];
+#pragma unroll
+    for (uint32_t u = 0; u < GPREFETCH; ++u) {
+      qa[u] = u < nk ? load(kc0 + u, ra, oka) : 0u;
+      qb[u] = u < nk ? load(kc0 + u, rb, okb) : 0u;
     }
-  } else if (threadIdx.x == 32) {
+    for (uint32_t i0 = 0; i0 < nk; i0 += GPREFETCH) {
+#pragma unroll
+      for (uint32_t u = 0; u < GPREFETCH; ++u) {
+        const uint32_t i = i0 + u;
+        if (i >= nk || __shfl_sync(0xffffffffu, failed, 0)) break;  // warp-uniform
+        const uint32_t s = i % GSTAGES, use = i / GSTAGES;
+        const uint32_t wa = qa[u], wb = qb[u];
+        if (i + GPREFETCH < nk) {
+          qa[u] = load(kc0 + i + GPREFETCH, ra, oka);
+          qb[u] = load(kc0 + i + GPREFETCH, rb, okb);
+        }
+        // one lane per warp waits for the ring slot and one arrives for the
+        // warp (the barrier counts warps, not threads)
+        bool slot_ok = true;
+        if (use > 0 && lane == 0) slot_ok = mbar_wait(&empty[s], (use - 1) & 1);
+        if (!__shfl_sync(0xffffffffu, slot_ok ? 1u : 0u, 0)) { failed = 1; break; }
+        expand_rows32(stage_a + s * GTILE_BYTES, rr, q0, wa);
+        expand_rows32(stage_b + s * GTILE_BYTES, rr, q0, wb);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[s]);
+      }
+    }
+  } else if (lane == 0) {
     // MMA issuer: 4 instructions (K = 32 bytes each) per 128-row chunk
     for (uint32_t i = 0; i < nk; ++i) {
       const uint32_t s = i % GSTAGES, use = i / GSTAGES;
-      if (!mbar_wait(&full[s], use & 1)) { failed = 1; break; }
+      if (failed || !mbar_wait(&full[s], use & 1)) { failed = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = sm_addr(stage_a + s * GTILE_BYTES);
       const uint32_t b0 = sm_addr(stage_b + s * GTILE_BYTES);
@@ -260,24 +239,29 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
                (i | q) != 0);
       mma_commit(&empty[s]);
     }
-    mma_commit(&done);
+    mma_commit(&done);  // arrives once every MMA issued above has completed
   }
-  // epilogue: every warp reads its 32 TMEM lanes (rows ti*128 + 32w + lane)
-  bool ok = mbar_wait(&done, 0);
+  __syncwarp();
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (ranks of tile ti),
+  // columns 32 (w / 4) .. +31
+  if (lane == 0 && !mbar_wait(&done, 0)) failed = 1;
   __syncthreads();
-  ok = ok && !failed;
+  const bool ok = !failed;  // the same for every thread of the CTA
   if (threadIdx.x == 0 && !ok) C->error = 5;  // DIC_ETIMEOUT
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    // Each warp stages its 32 x 32 sub-tiles through shared memory (the
-    // operand ring is idle once `done` has fired) so that a warp's adds go
-    // to 32 consecutive counters: lane q adds count (a, b0 + q) of row a.
+  if (ok && warp < GEXP_WARPS) {
+    // Each warp stages its 32 x 32 sub-tile through shared memory (the
+    // operand rings, 128 KiB, are idle once `done` has fired) so that a
+    // warp's adds go to 32 consecutive counters: lane q adds count (a, b0 + q)
+    // of row a.
     const uint64_t l1 = L.l1;
     uint32_t *stage = reinterpret_cast<uint32_t *>(stage_a) + warp * (32 * 33);
-    const uint64_t a0 = (uint64_t)ti * GT + warp * 32;
-    for (uint32_t c0 = 0; c0 < GT; c0 += 32) {
+    const uint32_t lq = warp % 4;
+    const uint64_t a0 = (uint64_t)ti * GT + lq * 32;
+    do {
+      const uint32_t c0 = (warp / 4) * 32;
       uint32_t v[32];
-      const uint32_t taddr = tmem + ((warp * 32u) << 16) + c0;
+      const uint32_t taddr = tmem + ((lq * 32u) << 16) + c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
           "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -291,7 +275,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const uint64_t b = (uint64_t)tj * GT + c0 + lane;
-      if (a0 >= l1 || (uint64_t)tj * GT + c0 + 31 <= a0) continue;  // all b <= a (warp-uniform)
+      if (a0 >= l1 || (uint64_t)tj * GT + c0 + 31 <= a0) break;  // all b <= a (warp-uniform)
 #pragma unroll
       for (int q = 0; q < 32; ++q) stage[lane * 33 + q] = (uint32_t)__uint_as_float(v[q]);
       __syncwarp();
@@ -299,52 +283,28 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L,
       for (uint32_t r = 0; r < rmax; ++r) {
         const uint64_t a = a0 + r;
         const uint32_t cnt = stage[r * 33 + lane];
-        if (b > a && b < l1 && cnt) atomicAdd(&L.csupp[gram_pair_index(a, b, l1)], cnt);
+        if (b > a && b < l1 && cnt) atomicAdd(&L.csupp[pair_record(a, b, l1)], cnt);
       }
-      __syncwarp();
-    }
-  } else if (threadIdx.x == 0) {
-    // let the copies already issued land before the shared memory goes away
-    for (uint32_t i = (issued > GSTAGES ? issued - GSTAGES : 0); i < issued; ++i)
-      mbar_wait(&full[i % GSTAGES], (i / GSTAGES) & 1);
+    } while (0);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  if (warp == GEXP_WARPS)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
 
 // -------------------------------------------------------------- launchers
 uint32_t gram_tiles(uint32_t l1) { return (l1 + GT - 1) / GT; }
 uint32_t gram_chunks(uint64_t rows) { return (uint32_t)((rows + GK - 1) / GK); }
-uint64_t gram_operand_bytes(uint32_t l1, uint64_t block_rows) {
-  return (uint64_t)gram_tiles(l1) * gram_chunks(block_rows) * GTILE_BYTES;
-}
 
-cudaError_t launch_gram_operand(Lattice L, uint8_t *X, uint32_t nkc_max, uint64_t xbytes,
-                                uint32_t kre, cudaStream_t s) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t items = (uint64_t)nkc_max * (GK / 32) * L.wc;
-  uint64_t want = (items + 7) / 8;
-  int grid = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
-  if (grid < 1) grid = 1;
-  k_gram_operand<<<grid, 256, 0, s>>>(L, X, nkc_max, xbytes, kre);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gram_pairs(Lattice L, const uint8_t *X, uint32_t nkc_max, uint32_t nsplit,
-                              uint32_t kre, cudaStream_t s) {
+cudaError_t launch_gram_pairs(Lattice L, uint32_t nsplit, uint32_t kre, cudaStream_t s) {
   const uint32_t ntile = gram_tiles(L.l1);
   const uint32_t npair_tiles = ntile * (ntile + 1) / 2;
-  // two rings of tiles + a 16 KiB guard band after them
-  const size_t smem = 2 * GSTAGES * GTILE_BYTES + GTILE_BYTES;
+  const size_t smem = 2 * GSTAGES * GTILE_BYTES;  // the A and B rings
   cudaError_t e =
       cudaFuncSetAttribute(k_gram_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_pairs<<<npair_tiles * nsplit, GRAM_THREADS, smem, s>>>(L, X, ntile, nkc_max, nsplit,
-                                                                 kre);
+  k_gram_pairs<<<npair_tiles * nsplit, GRAM_THREADS, smem, s>>>(L, ntile, nsplit, kre);
   return cudaGetLastError();
 }
 

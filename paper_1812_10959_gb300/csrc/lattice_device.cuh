@@ -112,10 +112,25 @@ __device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_
 // emitted iff every C \ {j} is a box and no j < r has C \ {j} promoted at g
 // (the canonical parent). New records go to base + n_gen; past the capacity
 // the stop stalls (ST_CAND) and nothing is written.
+//
+// First a necessary condition read straight from the pair cohort: C \ {j}
+// for j in A other than a (a = A's first or second rank) contains {a, r},
+// and every subset of a box is a box, so the pair records {a0, r} and
+// {a1, r} must both be boxes. Most ranks r fail it with two loads and no
+// probe of the box set.
 __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_t p, uint32_t r,
                                               uint32_t g, uint32_t base) {
   const uint32_t wc = L.wc;
-  const uint64_t *A = L.cmask + (uint64_t)L.newbox[p] * wc;
+  const uint32_t cA = L.newbox[p];
+  {
+    const uint32_t a0 = L.cranks[(uint64_t)cA * KRMAX], a1 = L.cranks[(uint64_t)cA * KRMAX + 1];
+    if (r == a0 || r == a1) return;  // r in A
+    const uint64_t l1 = L.l1;
+    const uint8_t s0 = L.cshape[r < a0 ? pair_record(r, a0, l1) : pair_record(a0, r, l1)];
+    const uint8_t s1 = L.cshape[r < a1 ? pair_record(r, a1, l1) : pair_record(a1, r, l1)];
+    if (s0 != SH_BOX || s1 != SH_BOX) return;
+  }
+  const uint64_t *A = L.cmask + (uint64_t)cA * wc;
   const uint32_t wr = r >> 6;
   const uint64_t br = 1ull << (r & 63);
   const uint64_t Awr = A[wr];
@@ -159,37 +174,52 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
 // CHECKFULLPASS (cohorts whose full pass is complete leave the window [head,
 // tail)), |DASHED| and the loop test of Algorithm 2.
 __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
-  const uint32_t g = C->step;
+  // one copy of the loop state in registers (independent loads, one round
+  // trip); every field this stop changes is stored once at the end
+  const Ctrl c = *C;
+  const uint32_t g = c.step;
   uint32_t stop;
   uint64_t first, last;
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
-  if (C->n_trace >= L.tcap) {
+  if (c.n_trace >= L.tcap) {
     C->error = 4;  // DIC_ECAPACITY
     C->done = 1;
     return;
   }
-  unsigned long long *row = L.trace + (uint64_t)C->n_trace * TRACE_COLS;
+  unsigned long long *row = L.trace + (uint64_t)c.n_trace * TRACE_COLS;
   row[0] = g; row[1] = stop; row[2] = first; row[3] = last;
-  row[4] = C->n_live; row[5] = C->n_newbox; row[6] = C->n_pruned; row[7] = C->n_gen;
-  row[8] = C->n_solid;
-  C->tests += (unsigned long long)C->n_live * (last - first);
-  if (C->n_gen) {
-    L.cohort_start[C->n_cohorts] = C->tail;
-    L.cohort_birth[C->n_cohorts] = g;
-    C->n_cohorts += 1;
+  row[4] = c.n_live; row[5] = c.n_newbox; row[6] = c.n_pruned; row[7] = c.n_gen;
+  row[8] = c.n_solid;
+  uint32_t n_cohorts = c.n_cohorts;
+  if (c.n_gen) {
+    L.cohort_start[n_cohorts] = c.tail;
+    L.cohort_birth[n_cohorts] = g;
+    n_cohorts += 1;
     C->last_birth = g;
   }
-  C->tail += C->n_gen;
-  C->hash_used += C->n_newbox;
-  C->n_live = C->n_live - C->n_pruned - C->n_solid + C->n_gen;
-  uint32_t ch = C->cohort_head;
-  while (ch < C->n_cohorts && L.cohort_birth[ch] + L.stop_max <= g) ++ch;
+  const uint32_t tail = c.tail + c.n_gen;
+  const uint32_t n_live = c.n_live - c.n_pruned - c.n_solid + c.n_gen;
+  // CHECKFULLPASS: cohorts whose full pass ends with this stop leave the
+  // window (a cohort born now never does: its birth + stop_max > g)
+  // (head = the first remaining cohort's start; the new cohort, if any,
+  // starts at the old tail, and so does an empty window)
+  uint32_t ch = c.cohort_head, head = c.tail;
+  while (ch < c.n_cohorts) {
+    const uint32_t birth = L.cohort_birth[ch], start = L.cohort_start[ch];
+    if (birth + L.stop_max > g) { head = start; break; }
+    ++ch;
+  }
+  C->tests = c.tests + (unsigned long long)c.n_live * (last - first);
+  C->n_cohorts = n_cohorts;
+  C->tail = tail;
+  C->hash_used = c.hash_used + c.n_newbox;
+  C->n_live = n_live;
   C->cohort_head = ch;
-  C->head = ch < C->n_cohorts ? L.cohort_start[ch] : C->tail;
+  C->head = head;
   C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->n_gen = 0;
-  C->n_trace += 1;
+  C->n_trace = c.n_trace + 1;
   C->step = g + 1;
-  if (C->n_live == 0) C->done = 1;
+  if (n_live == 0) C->done = 1;
 }
 
 
