@@ -372,6 +372,7 @@ class Miner {
   bool tc_ok_ = false;
   uint32_t tc_nkc_max_ = 0, tc_nsplit_ = 1;
   cudaStream_t s2_ = nullptr;  // side stream of the pair-cohort kernels
+  bool direct_ = false;        // the counted window was small at the last sync
   cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   uint32_t pred_step_ = 1;     // stop number the next enqueued count runs at
   double gram_ms_ = 0;
@@ -379,7 +380,7 @@ class Miner {
   // CUDA graphs: one captured stop per variant, replayed stop after stop
   struct StopGraph {
     int path = 0, kre = 0;
-    bool gram = false, slice = false;
+    bool gram = false, slice = false, direct = false;
     uint32_t profile = 0;  // DIC_PROFILE_* bits captured as event nodes
     uint32_t nw = 0;
     uint64_t version = 0;
@@ -526,7 +527,7 @@ dic_status Miner::launch_phase(int phase) {
         if (e == cudaSuccess) {
           if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT, s_));
           e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_,
-                                    bs_grid_, s_);
+                                    direct_ ? grid_ : bs_grid_, direct_, s_);
           if (prof(DIC_PROFILE_COUNT)) TRY(iv_close(s_));
         }
         if (gram) CU(cudaStreamWaitEvent(s_, ev_join_, 0));  // join
@@ -808,9 +809,9 @@ dic_status Miner::prepare() {
       tc_ok_ = false;
       if (want && bs_ok_ && blockmax < (1ull << 24) && npairs <= 0xFFFFFFF0ull) {
         tc_nkc_max_ = gram_chunks(blockmax);
-        const uint32_t nt = gram_tiles(l1), ntp = nt * (nt + 1) / 2;
+        const uint32_t ntp = gram_tile_pairs(l1);
         const uint32_t sms = (uint32_t)sm_count();
-        // one CTA per SM (the ring takes 128 KiB): a single wave of splits
+        // one CTA per SM (the rings take 192 KiB): a single wave of splits
         tc_nsplit_ = std::max<uint32_t>(1, std::min<uint32_t>(tc_nkc_max_, sms / ntp));
         if (!s2_) CU(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
         if (!ev_fork_) CU(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
@@ -909,12 +910,14 @@ dic_status Miner::launch_stop() {
   key.gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
   key.slice = fast && !next_v_ready_;
   key.kre = fast ? kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4)) : 0;
+  key.direct = fast && direct_;
   key.nw = cur_path_ == DIC_COUNT_ROWS ? nw_ : 0;
   key.profile = opt_.profile;
   key.version = lat_version_;
   StopGraph *sg = nullptr;
   for (auto &g : graphs_)
     if (g.path == key.path && g.gram == key.gram && g.slice == key.slice && g.kre == key.kre &&
+        g.direct == key.direct &&
         g.nw == key.nw && g.profile == key.profile && g.version == key.version)
       sg = &g;
   const uint32_t pred0 = pred_step_;
@@ -1016,6 +1019,14 @@ dic_status Miner::loop() {
     nw_ = bucket ? (uint32_t)bucket : 0;
     cur_path_ = count_path_for_stop();
     pred_step_ = h_ctrl_->step;
+    {
+      // the window the BITSLICE kernel counts (the pair cohort aside while
+      // the tensor path has it); small ones take the direct form
+      const Ctrl &c = *h_ctrl_;
+      const uint32_t skip = (L_.pair_end && c.step <= L_.stop_max) ? L_.pair_end : 0u;
+      const uint32_t lo = skip > c.head ? std::min(skip, c.tail) : c.head;
+      direct_ = c.tail - lo <= BS_DIRECT_HOST_MAX;
+    }
     for (uint32_t i = 0; i < group; ++i) TRY(launch_stop());
     TRY(sync_ctrl());
     TRY(recover());

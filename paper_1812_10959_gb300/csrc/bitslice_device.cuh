@@ -80,14 +80,18 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
   unsigned long long work = 0;
   for (uint64_t c = lo + (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < hi;
        c += nwarps) {
-    const uint32_t k = L.cshape[c] == SH_NIL ? 0u : (uint32_t)L.ck[c];
+    // the record's state is loaded up front with its ranks (no load of the
+    // count pass waits on PRUNE's operands)
+    const uint8_t sh = L.cshape[c];
+    const uint32_t k = sh == SH_NIL ? 0u : (uint32_t)L.ck[c];
     if (k == 0) continue;  // uniform over the warp
+    const uint32_t supp0 = L.csupp[c], birth = L.cbirth[c];
     const uint16_t *rk = L.cranks + c * KRMAX;
     uint32_t r[KRE];
 #pragma unroll
     for (int q = 0; q < KRE; ++q) r[q] = (uint32_t)q < k ? (uint32_t)rk[q] : 0u;
     uint32_t cnt = 0;
-#pragma unroll 4
+#pragma unroll 8
     for (uint32_t w = lane; w < nw32; w += 32) {
       const uint32_t tb = (w / TW) * l1p;
       const uint32_t wi = w % TW;
@@ -99,9 +103,9 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
     if (lane == 0) {
-      const uint32_t s = L.csupp[c] + cnt;
+      const uint32_t s = supp0 + cnt;
       L.csupp[c] = s;
-      settle_record(L, C, (uint32_t)c, s, g, true, pruned, solid);
+      settle_loaded(L, C, (uint32_t)c, sh, birth, s, g, true, pruned, solid);
       work += (unsigned long long)(k + 1) * nw32;
     }
   }

@@ -168,8 +168,13 @@ cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, ui
 size_t bitslice_tile_words(int tw, uint32_t l1p);
 // Columns of the block of stop g (g = Ctrl.step when g == 0).
 cudaError_t launch_slice_block(Lattice L, cudaStream_t s);
+// `direct`: the shared-memory-free form for windows expected to be small
+// (grid = CTAs of 256 threads); otherwise grid CTAs of 1024 threads.
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
-                                  uint32_t chunk, uint64_t vwords, int grid, cudaStream_t s);
+                                  uint32_t chunk, uint64_t vwords, int grid, bool direct,
+                                  cudaStream_t s);
+// Windows of at most this many counted records get the direct form.
+constexpr uint32_t BS_DIRECT_HOST_MAX = 8192;
 // Batched rounds (kernels_batch.cu): one launch per phase for all queries.
 cudaError_t launch_batch_plan(const Lattice *Ls, uint32_t Q, bool finish, uint32_t grid,
                               uint32_t chunk_cap, uint32_t *item_prefix, uint32_t *chunk,
@@ -184,7 +189,7 @@ cudaError_t launch_batch_gen(const Lattice *Ls, uint32_t Q, uint32_t slice_offse
                              cudaStream_t s);
 
 // TENSOR path for the pair cohort (kernels_count_tensor.cu).
-uint32_t gram_tiles(uint32_t l1);
+uint32_t gram_tile_pairs(uint32_t l1);  // CTAs per K split
 uint32_t gram_chunks(uint64_t rows);
 // Reads the stop's bit columns L.V (so it needs L.tw in {4, 8, 16}); does
 // nothing when the BITSLICE count of the same stop (kre ranks) will stall,

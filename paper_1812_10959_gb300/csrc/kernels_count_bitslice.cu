@@ -116,6 +116,27 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   (void)V; (void)l1p; (void)vwords;
 }
 
+// The same count for a window the host expects to be small: direct mode
+// only (it is exact at any window size), no shared memory, so its CTAs can
+// share SMs with the pair-cohort GEMM of the same stop.
+template <int TW, int KRE>
+__global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
+  Ctrl *C = L.ctrl;
+  if (C->stall || C->done) return;
+  if (!bs_checks<KRE>(L, C, blockIdx.x == 0)) return;
+  const uint32_t g = C->step;
+  uint32_t nw32, ntiles;
+  if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
+  const uint32_t head = C->head, tail = C->tail;
+  const uint32_t skip = (L.pair_end && g <= L.stop_max) ? L.pair_end : 0u;
+  const uint32_t lo = skip > head ? (skip < tail ? skip : tail) : head;
+  if (lo >= tail) return;
+  uint32_t pruned = 0, solid = 0;
+  bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid);
+  if (pruned) atomicAdd(&C->n_pruned, pruned);
+  if (solid) atomicAdd(&C->n_solid, solid);
+}
+
 // PRUNE (Algorithm 4) for the pair cohort after the tensor kernel has added
 // this stop's counts: one thread per record.
 __global__ void __launch_bounds__(256) k_settle_pairs(Lattice L, uint32_t kre) {
@@ -154,7 +175,11 @@ cudaError_t launch_settle_pairs(Lattice L, int grid, uint32_t kre, cudaStream_t 
 
 template <int TW, int KRE>
 static cudaError_t go(Lattice L, const uint32_t *V, uint32_t l1p, uint32_t chunk, uint64_t vw,
-                      int grid, cudaStream_t s) {
+                      int grid, bool direct, cudaStream_t s) {
+  if (direct) {
+    k_count_direct<TW, KRE><<<grid, 256, 0, s>>>(L);
+    return cudaGetLastError();
+  }
   const size_t smem = bitslice_smem(TW, KRE, l1p, chunk);
   cudaError_t e = cudaFuncSetAttribute(k_count_bitslice<TW, KRE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -165,23 +190,24 @@ static cudaError_t go(Lattice L, const uint32_t *V, uint32_t l1p, uint32_t chunk
 
 template <int TW>
 static cudaError_t go_k(Lattice L, const uint32_t *V, int kre, uint32_t l1p, uint32_t chunk,
-                        uint64_t vw, int grid, cudaStream_t s) {
+                        uint64_t vw, int grid, bool direct, cudaStream_t s) {
   switch (kre) {
-    case 2: return go<TW, 2>(L, V, l1p, chunk, vw, grid, s);
-    case 4: return go<TW, 4>(L, V, l1p, chunk, vw, grid, s);
-    case 8: return go<TW, 8>(L, V, l1p, chunk, vw, grid, s);
-    default: return go<TW, 16>(L, V, l1p, chunk, vw, grid, s);
+    case 2: return go<TW, 2>(L, V, l1p, chunk, vw, grid, direct, s);
+    case 4: return go<TW, 4>(L, V, l1p, chunk, vw, grid, direct, s);
+    case 8: return go<TW, 8>(L, V, l1p, chunk, vw, grid, direct, s);
+    default: return go<TW, 16>(L, V, l1p, chunk, vw, grid, direct, s);
   }
 }
 
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
-                                  uint32_t chunk, uint64_t vwords, int grid, cudaStream_t s) {
+                                  uint32_t chunk, uint64_t vwords, int grid, bool direct,
+                                  cudaStream_t s) {
   if (tw != 16 && tw != 8 && tw != 4) return cudaErrorInvalidValue;
   if (bitslice_tile_words(tw, l1p) % 4) return cudaErrorInvalidValue;
   switch (tw) {
-    case 16: return go_k<16>(L, V, kre, l1p, chunk, vwords, grid, s);
-    case 8: return go_k<8>(L, V, kre, l1p, chunk, vwords, grid, s);
-    default: return go_k<4>(L, V, kre, l1p, chunk, vwords, grid, s);
+    case 16: return go_k<16>(L, V, kre, l1p, chunk, vwords, grid, direct, s);
+    case 8: return go_k<8>(L, V, kre, l1p, chunk, vwords, grid, direct, s);
+    default: return go_k<4>(L, V, kre, l1p, chunk, vwords, grid, direct, s);
   }
 }
 

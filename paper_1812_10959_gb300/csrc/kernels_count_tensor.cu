@@ -8,18 +8,18 @@
 // so pair {a, b} is record pair_off(a) + b - a - 1 and the GEMM's output
 // element (a, b) goes straight to its counter.
 //
-// k_gram_pairs: one CTA per (128-rank tile pair i <= j, K split). The
-// operands come from the stop's bit columns V (the BITSLICE transposition,
-// 32 rows per word): for every 128-row chunk, sixteen expander warps load
-// each rank's four column words (a few chunks ahead) and write them to
-// shared memory as e4m3 0/1 bytes (1.0 = 0x38) in the K-major no-swizzle
-// core-matrix layout of tcgen05 (8 ranks x 16 rows per 128-byte core
-// matrix), through a 4-stage ring guarded by mbarriers; one thread of a
-// seventeenth warp issues
-// tcgen05.mma.kind::f8f6f4 (M = N = 128, K = 32 per instruction, fp32
-// accumulation in tensor memory). The epilogue brings the 128x128 tile out
-// with tcgen05.ld, turns its rows through shared memory and adds the counts
-// of pairs a < b to 32 consecutive records per warp instruction.
+// k_gram_pairs: one CTA per (128-rank A tile i, 256-rank B tile j >= i/2,
+// K split). The operands come from the stop's bit columns V (the BITSLICE
+// transposition, 32 rows per word): for every 128-row chunk, twelve
+// expander warps (a thread per rank row) load each rank's four column words
+// (a few chunks ahead, one 16-byte load) and write them to shared memory as
+// e4m3 0/1 bytes (1.0 = 0x38) in the K-major no-swizzle core-matrix layout
+// of tcgen05 (8 ranks x 16 rows per 128-byte core matrix), through a
+// 4-stage ring guarded by mbarriers; one thread of a seventeenth warp issues
+// tcgen05.mma.kind::f8f6f4 (M = 128, N = 256, K = 32 per instruction, fp32
+// accumulation in tensor memory). Sixteen warps then bring the 128x256 tile
+// out with tcgen05.ld, turn its rows through shared memory and add the
+// counts of pairs a < b to 32 consecutive records per warp instruction.
 //
 // Exactness: every product is 0 or 1 and a tile's sum over one split is at
 // most its rows (< 2^24), so fp32 accumulation is exact.
@@ -35,19 +35,24 @@
 
 namespace dic {
 
-constexpr uint32_t GT = 128;             // ranks per tile (M = N)
-constexpr uint32_t GK = 128;             // rows (K) per chunk = bytes per row of a tile
+constexpr uint32_t GM = 128;             // A-tile ranks (MMA M, TMEM lanes)
+constexpr uint32_t GN = 256;             // B-tile ranks (MMA N, TMEM columns)
+constexpr uint32_t GK = 128;             // rows (K) per chunk = bytes per rank row of a tile
 constexpr uint32_t GSTAGES = 4;
-constexpr uint32_t GTILE_BYTES = GT * GK;  // 16 KiB
-constexpr uint32_t GEXP_WARPS = 16;      // expander / epilogue warps
+constexpr uint32_t GTILE_A = GM * GK;    // 16 KiB
+constexpr uint32_t GTILE_B = GN * GK;    // 32 KiB
+constexpr uint32_t GEXP_WARPS = 16;      // epilogue warps (4 TMEM lane quarters x 4)
+constexpr uint32_t GLOAD_WARPS = (GM + GN) / 32;  // expander warps: one thread per rank row
 constexpr uint32_t GPREFETCH = 4;        // chunks of column words loaded ahead
 constexpr uint32_t GEXP_THREADS = GEXP_WARPS * 32;
 constexpr uint32_t GRAM_THREADS = GEXP_THREADS + 32;  // + the MMA warp
+static_assert((GM + GN) % 32 == 0 && GLOAD_WARPS <= GEXP_WARPS, "expander warps");
 constexpr long long WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz before giving up
 constexpr uint8_t E4M3_ONE = 0x38;
 
-// Byte offset of element (rank r, row k) inside a 16 KiB tile: core matrix
-// (r/8, k/16) at (r/8)*1024 + (k/16)*128, element (r%8)*16 + k%16.
+// Byte offset of element (rank r, row k) inside a tile of 128-row chunks:
+// core matrix (r/8, k/16) at (r/8)*1024 + (k/16)*128, element (r%8)*16 +
+// k%16.
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t k) {
   return (r >> 3) * 1024u + (k >> 4) * 128u + (r & 7u) * 16u + (k & 15u);
 }
@@ -100,7 +105,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 // Instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B e4m3
 // (0), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t GRAM_IDESC = (1u << 4) | ((GT >> 3) << 17) | ((GT >> 4) << 24);
+constexpr uint32_t GRAM_IDESC = (1u << 4) | ((GN >> 3) << 17) | ((GM >> 4) << 24);
 
 __device__ __forceinline__ void mma_f8(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
@@ -118,22 +123,16 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 
 
 // ------------------------------------------------------------------ GEMM
-// Expand 32 rows of one rank's column (bit j of w = row 32 q0 + j of the
-// chunk) into the tile at rank row rr (arithmetic only: no shared-memory
-// reads beside the tensor core's).
-__device__ __forceinline__ void expand_rows32(uint8_t *tile, uint32_t rr, uint32_t q0,
-                                              uint32_t w) {
-#pragma unroll
-  for (uint32_t h = 0; h < 2; ++h) {  // 16 rows each
-    const uint32_t x = w >> (16 * h);
-    *reinterpret_cast<uint4 *>(tile + core_offset(rr, 32 * q0 + 16 * h)) =
-        make_uint4(expand4(x & 0xFu), expand4((x >> 4) & 0xFu), expand4((x >> 8) & 0xFu),
-                   expand4((x >> 12) & 0xFu));
-  }
+// Tile pairs: A tile i (ranks 128 i ..) with every B tile J (ranks 256 J ..)
+// that holds a rank above one of A's, i.e. J >= i / 2.
+__host__ __device__ __forceinline__ uint32_t gram_pairs_of(uint32_t na, uint32_t nb) {
+  uint32_t p = 0;
+  for (uint32_t i = 0; i < na; ++i) p += nb > i / 2 ? nb - i / 2 : 0u;
+  return p;
 }
 
-__global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint32_t ntile,
-                                                                uint32_t nsplit, uint32_t kre) {
+__global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint32_t nsplit,
+                                                                uint32_t kre) {
   extern __shared__ __align__(1024) uint8_t gsm[];
   __shared__ __align__(8) uint64_t full[GSTAGES], empty[GSTAGES], done;
   __shared__ uint32_t tmem_base;
@@ -147,32 +146,33 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
   const uint32_t nrows = (uint32_t)(last - first);
   if (blockIdx.x == 0 && threadIdx.x == 0) C->gram_rows += nrows;
   const uint32_t nkc = (nrows + GK - 1) / GK;
-  // which tile pair (ti <= tj) and which K split
+  // which tile pair (A tile ti, B tile tj >= ti / 2) and which K split
+  const uint32_t na = (L.l1 + GM - 1) / GM, nb = (L.l1 + GN - 1) / GN;
   const uint32_t pair = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
   uint32_t ti = 0, rem = pair;
-  while (ti < ntile && rem >= ntile - ti) { rem -= ntile - ti; ++ti; }
-  if (ti >= ntile) return;
-  const uint32_t tj = ti + rem;
+  while (ti < na && rem >= nb - ti / 2) { rem -= nb - ti / 2; ++ti; }
+  if (ti >= na) return;
+  const uint32_t tj = ti / 2 + rem;
   const uint32_t per = (nkc + nsplit - 1) / nsplit;
   const uint32_t kc0 = split * per;
   const uint32_t kc1 = kc0 + per < nkc ? kc0 + per : nkc;
   if (kc0 >= kc1) return;  // nothing to count for this split (uniform per CTA)
   const uint32_t nk = kc1 - kc0;
-  uint8_t *stage_a = gsm;                          // GSTAGES x 16 KiB
-  uint8_t *stage_b = gsm + GSTAGES * GTILE_BYTES;  // GSTAGES x 16 KiB
+  uint8_t *stage_a = gsm;                      // GSTAGES x 16 KiB
+  uint8_t *stage_b = gsm + GSTAGES * GTILE_A;  // GSTAGES x 32 KiB
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < GSTAGES; ++s) {
-      mbar_init(&full[s], GEXP_WARPS);
+      mbar_init(&full[s], GLOAD_WARPS);
       mbar_init(&empty[s], 1);
     }
     mbar_init(&done, 1);
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == GEXP_WARPS) {  // tensor memory: 128 columns of 128 lanes (fp32)
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;"
+  if (warp == GEXP_WARPS) {  // tensor memory: 256 columns of 128 lanes (fp32)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
                  ::"r"(sm_addr(&tmem_base)) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -181,85 +181,90 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  if (warp < GEXP_WARPS) {
-    // expanders: thread (rank rr, quarter q0) writes rows [32 q0, 32 q0 + 32)
-    // of rank rr of both tiles for every chunk; the column words of the next
-    // GPREFETCH chunks are in flight while a chunk is expanded
-    const uint32_t rr = threadIdx.x % GT, q0 = threadIdx.x / GT;
-    const uint64_t ra = (uint64_t)ti * GT + rr, rb = (uint64_t)tj * GT + rr;
-    const bool oka = ra < L.l1, okb = rb < L.l1;
-    const uint32_t tw = L.tw, st = bs_stride((int)tw), l1p = L.l1p;
-    const uint32_t tw_shift = __ffs(tw) - 1;  // tw is 4, 8 or 16
-    const uint32_t *__restrict__ V = L.V;
-    auto load = [&](uint32_t kc, uint64_t r, bool ok) -> uint32_t {
-      const uint32_t w0 = kc * (GK / 32) + q0;  // 32-row word of this quarter
-      const uint64_t t = w0 >> tw_shift, wi = w0 & (tw - 1);
-      return ok ? __ldg(V + (t * l1p + r) * st + wi) : 0u;
+  if (warp < GLOAD_WARPS) {
+    // expanders: thread rr owns rank row rr (the A tile's 128, then the B
+    // tile's 256) and writes its 128 rows of every chunk; the rank's four
+    // column words of a chunk are one 16-byte load, issued GPREFETCH chunks
+    // ahead
+    const uint32_t rr = threadIdx.x;
+    const bool is_a = rr < GM;
+    const uint64_t rank = is_a ? (uint64_t)ti * GM + rr : (uint64_t)tj * GN + (rr - GM);
+    const bool ok = rank < L.l1;
+    const uint32_t tw = L.tw, st = bs_stride((int)tw);
+    const uint32_t tw_shift = __ffs(tw) - 1;  // tw is 4, 8 or 16: a chunk's 4 words share a tile
+    const uint64_t tile_words = (uint64_t)L.l1p * st;
+    const uint32_t *col = L.V + (ok ? rank : 0) * st;
+    uint8_t *row0 = gsm + (is_a ? 0u : GSTAGES * GTILE_A) + core_offset(is_a ? rr : rr - GM, 0);
+    const uint32_t stage_bytes = is_a ? GTILE_A : GTILE_B;
+    auto load = [&](uint32_t kc) -> uint4 {
+      const uint32_t w0 = kc * (GK / 32);
+      return ok ? __ldg(reinterpret_cast<const uint4 *>(col + (w0 >> tw_shift) * tile_words +
+                                                        (w0 & (tw - 1))))
+                : make_uint4(0u, 0u, 0u, 0u);
     };
-    uint32_t qa[GPREFETCH], qb[GPREFETCH];
+    uint4 q[GPREFETCH];
 #pragma unroll
-    for (uint32_t u = 0; u < GPREFETCH; ++u) {
-      qa[u] = u < nk ? load(kc0 + u, ra, oka) : 0u;
-      qb[u] = u < nk ? load(kc0 + u, rb, okb) : 0u;
-    }
+    for (uint32_t d = 0; d < GPREFETCH; ++d) q[d] = d < nk ? load(kc0 + d) : make_uint4(0, 0, 0, 0);
     for (uint32_t i0 = 0; i0 < nk; i0 += GPREFETCH) {
 #pragma unroll
-      for (uint32_t u = 0; u < GPREFETCH; ++u) {
-        const uint32_t i = i0 + u;
+      for (uint32_t d = 0; d < GPREFETCH; ++d) {
+        const uint32_t i = i0 + d;
         if (i >= nk || __shfl_sync(0xffffffffu, failed, 0)) break;  // warp-uniform
         const uint32_t s = i % GSTAGES, use = i / GSTAGES;
-        const uint32_t wa = qa[u], wb = qb[u];
-        if (i + GPREFETCH < nk) {
-          qa[u] = load(kc0 + i + GPREFETCH, ra, oka);
-          qb[u] = load(kc0 + i + GPREFETCH, rb, okb);
-        }
+        const uint4 w = q[d];
+        if (i + GPREFETCH < nk) q[d] = load(kc0 + i + GPREFETCH);
         // one lane per warp waits for the ring slot and one arrives for the
         // warp (the barrier counts warps, not threads)
         bool slot_ok = true;
         if (use > 0 && lane == 0) slot_ok = mbar_wait(&empty[s], (use - 1) & 1);
         if (!__shfl_sync(0xffffffffu, slot_ok ? 1u : 0u, 0)) { failed = 1; break; }
-        expand_rows32(stage_a + s * GTILE_BYTES, rr, q0, wa);
-        expand_rows32(stage_b + s * GTILE_BYTES, rr, q0, wb);
+        uint8_t *dst = row0 + s * stage_bytes;
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (uint32_t h = 0; h < 8; ++h) {  // 16 rows each: core matrix column h
+          const uint32_t x = ws[h >> 1] >> (16 * (h & 1));
+          *reinterpret_cast<uint4 *>(dst + h * 128u) =
+              make_uint4(expand4(x & 0xFu), expand4((x >> 4) & 0xFu),
+                         expand4((x >> 8) & 0xFu), expand4((x >> 12) & 0xFu));
+        }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[s]);
       }
     }
-  } else if (lane == 0) {
+  } else if (warp == GEXP_WARPS && lane == 0) {
     // MMA issuer: 4 instructions (K = 32 bytes each) per 128-row chunk
     for (uint32_t i = 0; i < nk; ++i) {
       const uint32_t s = i % GSTAGES, use = i / GSTAGES;
       if (failed || !mbar_wait(&full[s], use & 1)) { failed = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = sm_addr(stage_a + s * GTILE_BYTES);
-      const uint32_t b0 = sm_addr(stage_b + s * GTILE_BYTES);
+      const uint32_t a0 = sm_addr(stage_a + s * GTILE_A);
+      const uint32_t b0 = sm_addr(stage_b + s * GTILE_B);
 #pragma unroll
-      for (uint32_t q = 0; q < GK / 32; ++q)
-        mma_f8(tmem, smem_desc(a0 + q * 256, 128, 1024), smem_desc(b0 + q * 256, 128, 1024),
-               (i | q) != 0);
+      for (uint32_t k = 0; k < GK / 32; ++k)
+        mma_f8(tmem, smem_desc(a0 + k * 256, 128, 1024), smem_desc(b0 + k * 256, 128, 1024),
+               (i | k) != 0);
       mma_commit(&empty[s]);
     }
     mma_commit(&done);  // arrives once every MMA issued above has completed
   }
   __syncwarp();
-  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (ranks of tile ti),
-  // columns 32 (w / 4) .. +31
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (ranks of A tile
+  // ti), columns 64 (w / 4) .. +63 (ranks of B tile tj)
   if (lane == 0 && !mbar_wait(&done, 0)) failed = 1;
   __syncthreads();
   const bool ok = !failed;  // the same for every thread of the CTA
   if (threadIdx.x == 0 && !ok) C->error = 5;  // DIC_ETIMEOUT
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok && warp < GEXP_WARPS) {
-    // Each warp stages its 32 x 32 sub-tile through shared memory (the
-    // operand rings, 128 KiB, are idle once `done` has fired) so that a
-    // warp's adds go to 32 consecutive counters: lane q adds count (a, b0 + q)
-    // of row a.
+    // Each warp stages 32 x 32 sub-tiles through shared memory (the operand
+    // rings are idle once `done` has fired) so that a warp's adds go to 32
+    // consecutive counters: lane q adds count (a, b0 + q) of row a.
     const uint64_t l1 = L.l1;
-    uint32_t *stage = reinterpret_cast<uint32_t *>(stage_a) + warp * (32 * 33);
+    uint32_t *stage = reinterpret_cast<uint32_t *>(gsm) + warp * (32 * 33);
     const uint32_t lq = warp % 4;
-    const uint64_t a0 = (uint64_t)ti * GT + lq * 32;
-    do {
-      const uint32_t c0 = (warp / 4) * 32;
+    const uint64_t a0 = (uint64_t)ti * GM + lq * 32;
+    for (uint32_t c0 = (warp / 4) * 64; c0 < (warp / 4) * 64 + 64; c0 += 32) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((lq * 32u) << 16) + c0;
       asm volatile(
@@ -274,10 +279,10 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const uint64_t b = (uint64_t)tj * GT + c0 + lane;
-      if (a0 >= l1 || (uint64_t)tj * GT + c0 + 31 <= a0) break;  // all b <= a (warp-uniform)
+      const uint64_t b = (uint64_t)tj * GN + c0 + lane;
+      if (a0 >= l1 || (uint64_t)tj * GN + c0 + 31 <= a0) continue;  // all b <= a (warp-uniform)
 #pragma unroll
-      for (int q = 0; q < 32; ++q) stage[lane * 33 + q] = (uint32_t)__uint_as_float(v[q]);
+      for (int k = 0; k < 32; ++k) stage[lane * 33 + k] = (uint32_t)__uint_as_float(v[k]);
       __syncwarp();
       const uint32_t rmax = l1 - a0 < 32 ? (uint32_t)(l1 - a0) : 32u;
       for (uint32_t r = 0; r < rmax; ++r) {
@@ -285,26 +290,28 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
         const uint32_t cnt = stage[r * 33 + lane];
         if (b > a && b < l1 && cnt) atomicAdd(&L.csupp[pair_record(a, b, l1)], cnt);
       }
-    } while (0);
+      __syncwarp();
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == GEXP_WARPS)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
 // -------------------------------------------------------------- launchers
-uint32_t gram_tiles(uint32_t l1) { return (l1 + GT - 1) / GT; }
+uint32_t gram_tile_pairs(uint32_t l1) {
+  return gram_pairs_of((l1 + GM - 1) / GM, (l1 + GN - 1) / GN);
+}
 uint32_t gram_chunks(uint64_t rows) { return (uint32_t)((rows + GK - 1) / GK); }
 
 cudaError_t launch_gram_pairs(Lattice L, uint32_t nsplit, uint32_t kre, cudaStream_t s) {
-  const uint32_t ntile = gram_tiles(L.l1);
-  const uint32_t npair_tiles = ntile * (ntile + 1) / 2;
-  const size_t smem = 2 * GSTAGES * GTILE_BYTES;  // the A and B rings
+  const uint32_t npairs = gram_tile_pairs(L.l1);
+  const size_t smem = GSTAGES * (GTILE_A + GTILE_B);  // the A and B rings
   cudaError_t e =
       cudaFuncSetAttribute(k_gram_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_pairs<<<npair_tiles * nsplit, GRAM_THREADS, smem, s>>>(L, ntile, nsplit, kre);
+  k_gram_pairs<<<npairs * nsplit, GRAM_THREADS, smem, s>>>(L, nsplit, kre);
   return cudaGetLastError();
 }
 
