@@ -63,7 +63,8 @@ constexpr uint32_t BS_DIRECT_MAX = 24576;
 
 // Count records [lo, hi) with one warp per record: lane w reads word w of
 // each of the record's rank columns from L.V (tile t = w / TW), ANDs them and
-// popcounts; the warp sum is the record's count. Then PRUNE. The ranks are
+// popcounts; the warp sum is the record's count. Then PRUNE (tallies and
+// algorithmic work are added to the caller's counters). The ranks are
 // held in registers and the rank loop is unrolled (predicated on q < k) so
 // that a lane's column loads, and those of its next words, are all in
 // flight together. Whole warps must call this
@@ -71,13 +72,13 @@ constexpr uint32_t BS_DIRECT_MAX = 24576;
 template <int TW, int KRE>
 __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint32_t g,
                                                 uint32_t lo, uint32_t hi, uint32_t nw32,
-                                                uint32_t &pruned, uint32_t &solid) {
+                                                uint32_t &pruned, uint32_t &solid,
+                                                unsigned long long &work) {
   constexpr uint32_t ST = bs_stride(TW);
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint32_t *__restrict__ V = L.V;
   const uint32_t l1p = L.l1p;
-  unsigned long long work = 0;
   for (uint64_t c = lo + (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < hi;
        c += nwarps) {
     // the record's state is loaded up front with its ranks (no load of the
@@ -109,7 +110,6 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
       work += (unsigned long long)(k + 1) * nw32;
     }
   }
-  warp_add_u64(&C->work, work);
 }
 
 // Count records [c0, c0+cn) of the window over the block of stop g and apply
@@ -120,7 +120,8 @@ template <int TW, int KRE, int NT>
 __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32_t g, uint32_t c0,
                                                uint32_t cn, uint32_t nw32, uint32_t ntiles,
                                                uint32_t *sm, uint32_t chunk_cap,
-                                               uint32_t &pruned, uint32_t &solid) {
+                                               uint32_t &pruned, uint32_t &solid,
+                                               unsigned long long &work) {
   constexpr uint32_t ST = bs_stride(TW);
   constexpr int NV = TW / 4;  // 128-bit loads per rank and tile
   const uint32_t tile_words = L.l1p * ST;
@@ -186,7 +187,6 @@ __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32
     }
     __syncthreads();  // the buffer of tile t may be overwritten next
   }
-  unsigned long long work = 0;
   for (uint32_t i = tid; i < cn; i += NT) {
     if (!kk[i]) continue;
     const uint32_t c = c0 + i;
@@ -200,7 +200,6 @@ __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32
     // algorithmic work: k-1 AND + POPC + ADD per 32-row word
     work += (unsigned long long)(kk[i] + 1) * nw32;
   }
-  warp_add_u64(&C->work, work);
 }
 
 }  // namespace dic

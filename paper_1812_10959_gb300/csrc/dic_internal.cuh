@@ -55,6 +55,34 @@ struct Ctrl {
   unsigned long long gram_rows;  // block rows whose pair cohort the GEMM counted
 };
 
+// Add per-thread PRUNE tallies and count work of one CTA to the loop state
+// with at most one atomic per field (every thread of the CTA must call; the
+// same address taken by every warp of a launch serialises at L2).
+__device__ __forceinline__ void block_add_tallies(Ctrl *C, uint32_t pruned, uint32_t solid,
+                                                  unsigned long long work) {
+  __shared__ uint32_t s_pr[32], s_so[32];
+  __shared__ unsigned long long s_wk[32];
+  const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pruned = __reduce_add_sync(0xffffffffu, pruned);
+  solid = __reduce_add_sync(0xffffffffu, solid);
+  for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(0xffffffffu, work, o);
+  __syncthreads();  // the arrays may hold a previous call's sums
+  if (lane == 0) { s_pr[w] = pruned; s_so[w] = solid; s_wk[w] = work; }
+  __syncthreads();
+  if (w == 0) {
+    const bool in = lane < (blockDim.x >> 5);
+    pruned = __reduce_add_sync(0xffffffffu, in ? s_pr[lane] : 0u);
+    solid = __reduce_add_sync(0xffffffffu, in ? s_so[lane] : 0u);
+    work = in ? s_wk[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(0xffffffffu, work, o);
+    if (lane == 0) {
+      if (pruned) atomicAdd(&C->n_pruned, pruned);
+      if (solid) atomicAdd(&C->n_solid, solid);
+      if (work) atomicAdd(&C->work, work);
+    }
+  }
+}
+
 // Add a per-thread amount to a 64-bit counter with one atomic per warp.
 __device__ __forceinline__ void warp_add_u64(unsigned long long *dst, unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

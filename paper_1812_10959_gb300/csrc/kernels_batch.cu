@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(BATCH_COUNT_THREADS) k_batch_count(
       continue;
     }
     uint32_t pruned = 0, solid = 0;
+    unsigned long long work = 0;
     bs_count_chunk<TW, KRE, BATCH_COUNT_THREADS>(L, C, g, c0, cn, nw32, ntiles, sm, cap, pruned,
-                                                 solid);
-    if (pruned) atomicAdd(&C->n_pruned, pruned);
-    if (solid) atomicAdd(&C->n_solid, solid);
+                                                 solid, work);
+    block_add_tallies(C, pruned, solid, work);  // (the item is the CTA's alone)
   }
 }
 

@@ -67,6 +67,10 @@ size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk) {
 }
 
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit) {
+  // the count kernels' static shared memory (block tallies) comes out of the
+  // same per-block limit
+  constexpr size_t kStaticReserve = 1024;
+  smem_limit = smem_limit > kStaticReserve ? smem_limit - kStaticReserve : 0;
   const size_t tile = bitslice_tile_words(tw, l1p) * 4;
   if (2 * tile + 16 >= smem_limit) return 0;
   size_t c = (smem_limit - 2 * tile - 16) / (2 * kre + 4 + 1);
@@ -93,11 +97,12 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   const uint32_t lo = skip > head ? (skip < tail ? skip : tail) : head;
   const uint32_t ncand = tail - lo;
   uint32_t pruned = 0, solid = 0;
+  unsigned long long work = 0;
   if (ncand == 0) return;
   if (ncand <= BS_DIRECT_MAX) {
     // few candidates: no shared tiles; a warp per candidate ANDs its columns
     // straight from the (L2-resident) column buffer
-    bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid);
+    bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid, work);
   } else {
     uint32_t chunk = (ncand + gridDim.x - 1) / gridDim.x;
     chunk = (chunk + 3) & ~3u;
@@ -108,11 +113,10 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
       const uint32_t c0 = lo + ch * chunk;
       const uint32_t cn = (tail - c0) < chunk ? (tail - c0) : chunk;
       bs_count_chunk<TW, KRE, BS_THREADS>(L, C, g, c0, cn, nw32, ntiles, sm, chunk_cap, pruned,
-                                          solid);
+                                          solid, work);
     }
   }
-  if (pruned) atomicAdd(&C->n_pruned, pruned);
-  if (solid) atomicAdd(&C->n_solid, solid);
+  block_add_tallies(C, pruned, solid, work);
   (void)V; (void)l1p; (void)vwords;
 }
 
@@ -132,9 +136,9 @@ __global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
   const uint32_t lo = skip > head ? (skip < tail ? skip : tail) : head;
   if (lo >= tail) return;
   uint32_t pruned = 0, solid = 0;
-  bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid);
-  if (pruned) atomicAdd(&C->n_pruned, pruned);
-  if (solid) atomicAdd(&C->n_solid, solid);
+  unsigned long long work = 0;
+  bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid, work);
+  block_add_tallies(C, pruned, solid, work);
 }
 
 // PRUNE (Algorithm 4) for the pair cohort after the tensor kernel has added
@@ -164,8 +168,7 @@ __global__ void __launch_bounds__(256) k_settle_pairs(Lattice L, uint32_t kre) {
       settle_loaded(L, C, (uint32_t)(c + u * stride), sh[u], bi[u], sp[u], g, true, pruned,
                     solid);
   }
-  if (pruned) atomicAdd(&C->n_pruned, pruned);
-  if (solid) atomicAdd(&C->n_solid, solid);
+  block_add_tallies(C, pruned, solid, 0ull);
 }
 
 cudaError_t launch_settle_pairs(Lattice L, int grid, uint32_t kre, cudaStream_t s) {

@@ -223,8 +223,7 @@ __global__ void __launch_bounds__(256) k_promote(Lattice L) {
   for (uint32_t c = head + blockIdx.x * blockDim.x + threadIdx.x; c < tail;
        c += gridDim.x * blockDim.x)
     settle_record(L, C, c, L.csupp[c], g, false, pruned, solid);
-  if (pruned) atomicAdd(&C->n_pruned, pruned);
-  if (solid) atomicAdd(&C->n_solid, solid);
+  block_add_tallies(C, pruned, solid, 0ull);
 }
 
 cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s) {
