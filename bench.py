@@ -183,6 +183,21 @@ def cpu_sample_desc(db):
             f"block (M={CPU_SAMPLE_M} instead of {db.M} to bound the sample)")
 
 
+def aggregate_replicas(seconds: float, tests: float, device: str):
+    """Whole-job figures over the replicas (one process per GPU, each mining
+    its own copy): the slowest rank's time and the sum of the ranks' tests.
+    Without an initialised process group of more than one rank, the inputs."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, float(tests)
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    n = torch.tensor([float(tests)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(n[0])
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -203,8 +218,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": {"workload": db.name, "n": db.n, "m": db.m,
-                                        "minsup": db.minsup, "M": CPU_SAMPLE_M,
-                                        "sample": "first pass + first stop"},
+                                        "minsup": db.minsup, "M": db.M,
+                                        "sample": cpu_sample_desc(db)},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": cpu_sample_desc(db)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -422,13 +437,7 @@ def main():
     total_s = sum(ms) / 1000.0
     tests_step = stats[0]["tests"]
     tests_all = tests_step * args.steps
-    t_max = total_s
-    if world > 1:
-        tt = torch.tensor([total_s, float(tests_all)], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_max, tests_all = float(mx[0]), float(tt[1])
+    t_max, tests_all = aggregate_replicas(total_s, tests_all, "cuda")
     value = tests_all / t_max
 
     # ---- end to end through the C ABI from host buffers: the rows as CSR
@@ -448,11 +457,8 @@ def main():
         e2e_s += time.perf_counter() - t0
         d2h = r2.masks.nbytes + r2.k.nbytes + r2.support.nbytes + r2.trace.nbytes
     h2d = rp_h.numel() * 8 + it_h.numel() * 4
-    e2e_v = tests_step * args.steps / e2e_s
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_v = tests_step * args.steps * world / float(tt[0])
+    e2e_max, e2e_tests = aggregate_replicas(e2e_s, tests_step * args.steps, "cuda")
+    e2e_v = e2e_tests / e2e_max
 
     # ---- roofline of the dominant kernel kind, timed live with CUDA events
     # on the mining stream around each of its launches in the timed steps
