@@ -43,10 +43,13 @@ CPU_SAMPLE_M = 1_000
 # LOP3 per touched 32-bit half + compare + add per test; BITSLICE: k-1 AND +
 # POPC + ADD per 32-row word) in stats["count_ops"].
 ALU_PEAK_TOPS = 152 * 64 * 2.070e9 / 1e12
-COUNT_KERNELS = {1: "k_count_rows", 2: "k_count_bitslice", 3: "k_count_bitslice"}
+COUNT_KERNELS = {1: "k_count_rows", 2: "k_count_direct", 3: "k_count_direct"}  # (k_count_bitslice for large windows)
 # fp8 (kind::f8f6f4) dense tensor peak = the measured bf16 peak x 2, the
 # nominal fp8:bf16 ratio (4.5 / 2.25 PFLOP/s)
 FP8_PER_BF16 = 2.0
+# the timed steps bracket the dominant kernel kind with CUDA events on one
+# stop in this many
+PROFILE_EVERY = 8
 # timed kinds of the stop loop: stats key prefix -> profile name, kernels
 KINDS = {"count": "count", "gram": "gram", "settle": "settle", "gen": "gen"}
 KIND_KERNELS = {"gram": "k_gram_pairs", "settle": "k_settle_pairs",
@@ -63,6 +66,27 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
+    None when there is none or a source file it was built from has changed
+    since (the file records their SHA-256)."""
+    import hashlib
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        entry = json.load(f).get(kernel)
+    if not entry:
+        return None
+    h = hashlib.sha256()
+    for rel in entry["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
+
+
 def roofline_of(kind, stats, shares_ms, step_ms, db):
     """Roofline object of the kernel kind `kind` from the profiled timed steps."""
     pk = peaks()
@@ -72,23 +96,24 @@ def roofline_of(kind, stats, shares_ms, step_ms, db):
     nl = sum(s[nkey[kind]] if kind in nkey else s["path_launches"][3] for s in stats)
     avg_ms = tot_ms / max(nl, 1)
     st = stats[0]
-    common = {"avg_launch_ms": avg_ms, "launches_timed": nl, "share_of_step": tot_ms / step_ms,
-              "kind_ms_per_step": {k: v for k, v in shares_ms.items()}}
+    common = {"avg_launch_ms": avg_ms, "launches_timed": nl,
+              "timed_stops": f"one stop in {PROFILE_EVERY} of the timed steps",
+              "kind_ms_per_step_warmup": {k: v for k, v in shares_ms.items()}}
     if kind == "gram":
         flops = sum(s["gram_flops"] for s in stats) / max(nl, 1)
         ach = flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
         peak = pk["bf16"] * FP8_PER_BF16
         return dict(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                    traffic=None, kernel=KIND_KERNELS[kind],
+                    traffic=ncu_traffic(KIND_KERNELS[kind]), kernel=KIND_KERNELS[kind],
                     peak_source=f"{pk['source']} bf16 burst x {FP8_PER_BF16} (fp8 e4m3)",
                     flops_per_launch=flops, **common)
     if kind == "count":
         ops = sum(s["count_ops"] for s in stats) / max(nl, 1)
         ach = ops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
         pl = st["path_launches"]
+        kern = COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])]
         return dict(bound="alu", achieved=ach, peak=ALU_PEAK_TOPS, unit="Top/s",
-                    frac=ach / ALU_PEAK_TOPS, traffic=None,
-                    kernel=COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])],
+                    frac=ach / ALU_PEAK_TOPS, traffic=ncu_traffic(kern), kernel=kern,
                     peak_source="derived: 152 SM x 64 INT32 lanes x 2070 MHz",
                     ops_per_launch=ops, **common)
     # gen / settle: memory-side kernels; algorithmic bytes per launch
@@ -101,7 +126,8 @@ def roofline_of(kind, stats, shares_ms, step_ms, db):
         byts = l1 * (l1 - 1) / 2 * 9
     ach = byts / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
     return dict(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
-                frac=ach / pk["hbm_gbs"], traffic=None, kernel=KIND_KERNELS[kind],
+                frac=ach / pk["hbm_gbs"], traffic=ncu_traffic(KIND_KERNELS[kind]),
+                kernel=KIND_KERNELS[kind],
                 peak_source=f"{pk['source']} copy bandwidth", bytes_per_launch=byts, **common)
 
 
@@ -424,8 +450,11 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            # the dominant kernel kind is bracketed by events inside the step
-            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream, profile=kind)
+            # the dominant kernel kind is bracketed by events inside the step,
+            # on one stop in PROFILE_EVERY (each timed stop adds two event
+            # records to its graph)
+            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream, profile=kind,
+                           profile_every=PROFILE_EVERY)
             b.record(stream)
             evs.append((a, b))
             stats.append(res.stats)

@@ -87,7 +87,10 @@ typedef struct {
   uint32_t profile;         /* bitmask of DIC_PROFILE_*: kernels to time
                                with CUDA events on the mining stream       */
   uint32_t max_candidates;  /* 0 = no limit; else DIC_ECAPACITY beyond it  */
-  uint32_t reserved[10];
+  uint32_t profile_every;   /* with profile: time one stop in this many
+                               (stops whose number is a multiple of it);
+                               0 or 1 = every stop                         */
+  uint32_t reserved[9];
 } dic_options;
 
 /* Per-run statistics (dic_result_stats). */

@@ -350,7 +350,9 @@ class Miner {
   int iv_kind_ = 0;
   dic_status iv_open(int kind, cudaStream_t st);
   dic_status iv_close(cudaStream_t st);
-  bool prof(uint32_t bit) const { return (opt_.profile & bit) != 0; }
+  // profiling bits in force for the stop being enqueued (profile_every)
+  uint32_t prof_now_ = 0;
+  bool prof(uint32_t bit) const { return (prof_now_ & bit) != 0; }
   double settle_ms_ = 0, gen_ms_ = 0;
   uint64_t gen_timed_ = 0;
   double count_ms_ = 0;
@@ -903,6 +905,8 @@ dic_status Miner::recover() {
 }
 
 dic_status Miner::launch_stop() {
+  prof_now_ = (opt_.profile_every <= 1 || pred_step_ % opt_.profile_every == 0) ? opt_.profile
+                                                                               : 0u;
   if (!opt_.use_graph) return launch_stop_from(PH_COUNT);
   const bool fast = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
   StopGraph key;
@@ -912,7 +916,7 @@ dic_status Miner::launch_stop() {
   key.kre = fast ? kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4)) : 0;
   key.direct = fast && direct_;
   key.nw = cur_path_ == DIC_COUNT_ROWS ? nw_ : 0;
-  key.profile = opt_.profile;
+  key.profile = prof_now_;
   key.version = lat_version_;
   StopGraph *sg = nullptr;
   for (auto &g : graphs_)

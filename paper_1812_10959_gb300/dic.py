@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("count_path", ctypes.c_uint32),
                 ("steps_per_sync", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
                 ("profile", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 10)]
+                ("profile_every", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 9)]
 
 
 class Stats(ctypes.Structure):
@@ -249,22 +249,23 @@ def profile_mask(profile) -> int:
 
 
 def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
-            profile=False, max_candidates: int = 0) -> Options:
+            profile=False, max_candidates: int = 0, profile_every: int = 0) -> Options:
     o = Options()
     _lib.dic_options_init(ctypes.byref(o))
     o.count_path = PATHS[path]
     o.steps_per_sync = steps_per_sync
     o.use_graph = 1 if use_graph else 0
     o.profile = profile_mask(profile)
+    o.profile_every = profile_every
     o.max_candidates = max_candidates
     return o
 
 
 def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
          profile=False, steps_per_sync: int = 0, use_graph: bool = True,
-         max_candidates: int = 0) -> Result:
+         max_candidates: int = 0, profile_every: int = 0) -> Result:
     """All itemsets with support >= minsup (integer count), blocks of M rows."""
-    o = options(path, steps_per_sync, use_graph, profile, max_candidates)
+    o = options(path, steps_per_sync, use_graph, profile, max_candidates, profile_every)
     h = ctypes.c_void_p()
     _check(_lib.dic_mine_ex(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
                             ctypes.byref(h)))
