@@ -87,7 +87,7 @@ def ncu_traffic(kernel: str):
     return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
 
 
-def roofline_of(kind, stats, shares_ms, step_ms, db):
+def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto"):
     """Roofline object of the kernel kind `kind` from the profiled timed steps."""
     pk = peaks()
     tot_ms = sum(s[kind + "_ms"] for s in stats)
@@ -112,6 +112,8 @@ def roofline_of(kind, stats, shares_ms, step_ms, db):
         ach = ops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
         pl = st["path_launches"]
         kern = COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])]
+        if kern != "k_count_rows" and count_form == "tiled":
+            kern = "k_count_bitslice"
         return dict(bound="alu", achieved=ach, peak=ALU_PEAK_TOPS, unit="Top/s",
                     frac=ach / ALU_PEAK_TOPS, traffic=ncu_traffic(kern), kernel=kern,
                     peak_source="derived: 152 SM x 64 INT32 lanes x 2070 MHz",
@@ -393,6 +395,8 @@ def main():
     ap.add_argument("--workload", default="paper-scale")
     ap.add_argument("--path", default="auto", choices=["auto", "rows", "bitslice", "tensor"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="with --path auto: use the library's rule instead of the autotuner")
     ap.add_argument("--batch-dbs", type=int, default=512, help="databases for --workload batched")
     ap.add_argument("--served-queries", type=int, default=10_000)
     ap.add_argument("--plain-sample", type=int, default=300,
@@ -430,10 +434,20 @@ def main():
         if world > 1:
             dist.barrier()
 
+    # count configuration: the autotuner's choice for this query (timed on the
+    # query itself, all candidates checked to give the same result), or the
+    # path given on the command line
+    tuned = None
+    if args.path == "auto" and not args.no_tune:
+        from paper_1812_10959_gb300 import autotune
+        tuned = autotune.Tuner(repeats=2).tune(handle, db.minsup, db.M)
+        kw = tuned.kwargs()
+    else:
+        kw = dict(path=args.path)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
             # the last warm-up step times every kernel kind of the stop loop
-            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream,
+            res = dic.mine(handle, db.minsup, db.M, **kw, stream=stream,
                            profile=(i == args.warmup - 1))
     ref_count = len(res.k)
     shares_ms = {k: res.stats[k + "_ms"] for k in KINDS}
@@ -453,7 +467,7 @@ def main():
             # the dominant kernel kind is bracketed by events inside the step,
             # on one stop in PROFILE_EVERY (each timed stop adds two event
             # records to its graph)
-            res = dic.mine(handle, db.minsup, db.M, path=args.path, stream=stream, profile=kind,
+            res = dic.mine(handle, db.minsup, db.M, **kw, stream=stream, profile=kind,
                            profile_every=PROFILE_EVERY)
             b.record(stream)
             evs.append((a, b))
@@ -481,7 +495,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = dic.load_db_csr(rp_h, it_h, db.n, db.m)
-        r2 = dic.mine(h2, db.minsup, db.M, path=args.path)
+        r2 = dic.mine(h2, db.minsup, db.M, **kw)
         h2.free()
         e2e_s += time.perf_counter() - t0
         d2h = r2.masks.nbytes + r2.k.nbytes + r2.support.nbytes + r2.trace.nbytes
@@ -491,7 +505,7 @@ def main():
 
     # ---- roofline of the dominant kernel kind, timed live with CUDA events
     # on the mining stream around each of its launches in the timed steps
-    roofline = roofline_of(kind, stats, shares_ms, sum(ms), db)
+    roofline = roofline_of(kind, stats, shares_ms, sum(ms), db, kw.get("count_form", "auto"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -507,13 +521,18 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": db.name, "n": db.n, "m": db.m, "minsup": db.minsup,
-                       "M": db.M, "count_path": args.path, "tests_per_step": tests_step,
+                       "M": db.M,
+                       "count_path": (f"autotuned: {tuned.path}, tile_words {tuned.tile_words}, "
+                                      f"count form {tuned.count_form}") if tuned else args.path,
+                       "tests_per_step": tests_step,
                        "frequent_itemsets": ref_count, "l2": "flushed (512 MiB write) per step",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "roofline": roofline,
+            "autotune": ({"choice": tuned.kwargs(), "candidates_s": tuned.timings}
+                         if tuned else None),
             "cpu_baseline": cpu,
             "clocks": clk,
             "stats": stats[0],

@@ -90,7 +90,15 @@ typedef struct {
   uint32_t profile_every;   /* with profile: time one stop in this many
                                (stops whose number is a multiple of it);
                                0 or 1 = every stop                         */
-  uint32_t reserved[9];
+  uint32_t tile_words;      /* BITSLICE tile width in 32-row words: 0 = the
+                               widest that fits shared memory, or 4, 8, 16
+                               (a width that does not fit leaves the query
+                               on ROWS); other values: DIC_EINVAL          */
+  uint32_t count_form;      /* BITSLICE count kernel: 0 = by window size at
+                               each host check, 1 = always the tiled
+                               shared-memory kernel, 2 = always the direct
+                               kernel; other values: DIC_EINVAL            */
+  uint32_t reserved[7];
 } dic_options;
 
 /* Per-run statistics (dic_result_stats). */

@@ -252,7 +252,7 @@ struct DevBuf {
 class Miner {
  public:
   Miner(const dic_db *db, uint32_t minsup, uint64_t M, const dic_options &opt, cudaStream_t s)
-      : db_(db), minsup_(minsup), M_(M), opt_(opt), s_(s) {}
+      : db_(db), minsup_(minsup), M_(M), opt_(opt), s_(s), forced_tw_((int)opt.tile_words) {}
   ~Miner() { release(); }
 
   dic_status run(dic_result **out);
@@ -1029,7 +1029,8 @@ dic_status Miner::loop() {
       const Ctrl &c = *h_ctrl_;
       const uint32_t skip = (L_.pair_end && c.step <= L_.stop_max) ? L_.pair_end : 0u;
       const uint32_t lo = skip > c.head ? std::min(skip, c.tail) : c.head;
-      direct_ = c.tail - lo <= BS_DIRECT_HOST_MAX;
+      direct_ = opt_.count_form == 2 ||
+                (opt_.count_form == 0 && c.tail - lo <= BS_DIRECT_HOST_MAX);
     }
     for (uint32_t i = 0; i < group; ++i) TRY(launch_stop());
     TRY(sync_ctrl());
@@ -1145,6 +1146,16 @@ dic_status Miner::run(dic_result **out) {
 
 }  // namespace
 
+// Checks of the option fields with a closed set of values.
+static dic_status check_options(const dic_options &o) {
+  if (o.tile_words != 0 && o.tile_words != 4 && o.tile_words != 8 && o.tile_words != 16)
+    return fail(DIC_EINVAL, "tile_words must be 0, 4, 8 or 16 (got %u)", o.tile_words);
+  if (o.count_form > 2) return fail(DIC_EINVAL, "count_form must be 0, 1 or 2 (got %u)", o.count_form);
+  if (o.count_path > DIC_COUNT_TENSOR)
+    return fail(DIC_EINVAL, "unknown count_path %u", o.count_path);
+  return DIC_OK;
+}
+
 extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint64_t M,
                                   const dic_options *opt, void *stream, dic_result **out) {
   if (!out) return fail(DIC_EINVAL, "out is NULL");
@@ -1155,6 +1166,7 @@ extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint6
   dic_options o;
   dic_options_init(&o);
   if (opt) std::memcpy(&o, opt, std::min<size_t>(sizeof o, opt->struct_size ? opt->struct_size : sizeof o));
+  TRY(check_options(o));
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != db->device) cudaSetDevice(db->device);
@@ -1378,6 +1390,7 @@ extern "C" dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *m
   dic_options o;
   dic_options_init(&o);
   if (opt) std::memcpy(&o, opt, std::min<size_t>(sizeof o, opt->struct_size ? opt->struct_size : sizeof o));
+  TRY(check_options(o));
   if (o.count_path == DIC_COUNT_ROWS) {  // plain per-query GPU DIC, one after another
     for (uint32_t i = 0; i < count; ++i) {
       dic_status st = dic_mine_ex(dbs[i], minsup[i], M[i], &o, nullptr, &out[i]);
@@ -1654,6 +1667,7 @@ extern "C" dic_status dic_server_create(uint64_t hbm_budget_bytes, uint32_t max_
   sv->max_slots = max_slots;
   dic_options_init(&sv->opt);
   if (opt) std::memcpy(&sv->opt, opt, std::min<size_t>(sizeof sv->opt, opt->struct_size ? opt->struct_size : sizeof sv->opt));
+  TRY(check_options(sv->opt));
   cudaGetDevice(&sv->device);
   init_pool(sv->device);
   CU(cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking));

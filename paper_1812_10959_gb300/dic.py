@@ -29,7 +29,8 @@ class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("count_path", ctypes.c_uint32),
                 ("steps_per_sync", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
                 ("profile", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
-                ("profile_every", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 9)]
+                ("profile_every", ctypes.c_uint32), ("tile_words", ctypes.c_uint32),
+                ("count_form", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
 
 
 class Stats(ctypes.Structure):
@@ -248,8 +249,12 @@ def profile_mask(profile) -> int:
     return sum(PROFILE_BITS[k] for k in set(profile))
 
 
+COUNT_FORMS = {"auto": 0, "tiled": 1, "direct": 2}
+
+
 def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
-            profile=False, max_candidates: int = 0, profile_every: int = 0) -> Options:
+            profile=False, max_candidates: int = 0, profile_every: int = 0,
+            tile_words: int = 0, count_form: str = "auto") -> Options:
     o = Options()
     _lib.dic_options_init(ctypes.byref(o))
     o.count_path = PATHS[path]
@@ -257,29 +262,33 @@ def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
     o.use_graph = 1 if use_graph else 0
     o.profile = profile_mask(profile)
     o.profile_every = profile_every
+    o.tile_words = tile_words
+    o.count_form = COUNT_FORMS[count_form]
     o.max_candidates = max_candidates
     return o
 
 
 def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
          profile=False, steps_per_sync: int = 0, use_graph: bool = True,
-         max_candidates: int = 0, profile_every: int = 0) -> Result:
+         max_candidates: int = 0, profile_every: int = 0, tile_words: int = 0,
+         count_form: str = "auto") -> Result:
     """All itemsets with support >= minsup (integer count), blocks of M rows."""
-    o = options(path, steps_per_sync, use_graph, profile, max_candidates, profile_every)
+    o = options(path, steps_per_sync, use_graph, profile, max_candidates, profile_every,
+                tile_words, count_form)
     h = ctypes.c_void_p()
     _check(_lib.dic_mine_ex(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
                             ctypes.byref(h)))
     return _result(h)
 
 
-def mine_batch(dbs, minsups, Ms, path: str = "auto", profile=False):
+def mine_batch(dbs, minsups, Ms, path: str = "auto", profile=False, tile_words: int = 0):
     """Mine several (db, minsup, M) queries together; returns a list of Result."""
     cnt = len(dbs)
     handles = (ctypes.c_void_p * max(cnt, 1))(*[d.handle.value for d in dbs])
     ms = np.ascontiguousarray(minsups, dtype=np.uint32)
     Ms_ = np.ascontiguousarray(Ms, dtype=np.uint64)
     outs = (ctypes.c_void_p * max(cnt, 1))()
-    o = options(path, profile=profile)
+    o = options(path, profile=profile, tile_words=tile_words)
     _check(_lib.dic_mine_batch(ctypes.cast(handles, ctypes.c_void_p), ms.ctypes.data,
                                Ms_.ctypes.data, cnt, ctypes.byref(o),
                                ctypes.cast(outs, ctypes.c_void_p)))
