@@ -321,6 +321,8 @@ class Miner {
     if (ev_fork_) { cudaEventDestroy(ev_fork_); ev_fork_ = nullptr; }
     if (ev_join_) { cudaEventDestroy(ev_join_); ev_join_ = nullptr; }
     if (s2_) { cudaStreamDestroy(s2_); s2_ = nullptr; }
+    if (ev_slice_) { cudaEventDestroy(ev_slice_); ev_slice_ = nullptr; }
+    if (s3_) { cudaStreamDestroy(s3_); s3_ = nullptr; }
   }
 
   dic_status grow_candidates(uint32_t need);
@@ -374,6 +376,9 @@ class Miner {
   bool tc_ok_ = false;
   uint32_t tc_nkc_max_ = 0, tc_nsplit_ = 1;
   cudaStream_t s2_ = nullptr;  // side stream of the pair-cohort kernels
+  cudaStream_t s3_ = nullptr;  // side stream of the next block's transposition
+  cudaEvent_t ev_slice_ = nullptr;
+  bool vdouble_ = false;       // double-buffered columns (single-query loop)
   bool direct_ = false;        // the counted window was small at the last sync
   cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   uint32_t pred_step_ = 1;     // stop number the next enqueued count runs at
@@ -503,16 +508,26 @@ dic_status Miner::launch_phase(int phase) {
         const uint32_t chunk = std::min<uint32_t>(
             bitslice_max_chunk(bs_tw_, kre, bs_l1p_, smem_optin_), 1u << 20);
         if (!next_v_ready_) {
-          e = launch_slice_block(L_, s_);
+          e = launch_slice_block(L_, 0, s_);
           ++launches_;
         }
         next_v_ready_ = false;
         const bool gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
+        if (e == cudaSuccess && (gram || L_.vdouble)) CU(cudaEventRecord(ev_fork_, s_));
+        if (e == cudaSuccess && L_.vdouble) {
+          // fork: the next stop's block is transposed into the other column
+          // buffer on its own stream while this one is counted (the stop
+          // number it reads changes only at the end of generation, which
+          // waits for it)
+          CU(cudaStreamWaitEvent(s3_, ev_fork_, 0));
+          e = launch_slice_block(L_, 1, s3_);
+          CU(cudaEventRecord(ev_slice_, s3_));
+          ++launches_;
+        }
         if (e == cudaSuccess && gram) {
           // fork: the pair cohort (in DASHED up to stop_max) is counted on the
           // tensor cores and pruned on the side stream while the rest of the
           // window is counted here; generation waits for both
-          CU(cudaEventRecord(ev_fork_, s_));
           CU(cudaStreamWaitEvent(s2_, ev_fork_, 0));
           if (prof(DIC_PROFILE_GRAM)) TRY(iv_open(IV_GRAM, s2_));
           e = launch_gram_pairs(L_, tc_nsplit_, (uint32_t)kre, s2_);
@@ -533,6 +548,7 @@ dic_status Miner::launch_phase(int phase) {
           if (prof(DIC_PROFILE_COUNT)) TRY(iv_close(s_));
         }
         if (gram) CU(cudaStreamWaitEvent(s_, ev_join_, 0));  // join
+        if (L_.vdouble) CU(cudaStreamWaitEvent(s_, ev_slice_, 0));
         path_launches_[DIC_COUNT_BITSLICE]++;
       } else {
         if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT, s_));
@@ -545,11 +561,12 @@ dic_status Miner::launch_phase(int phase) {
     case PH_PROMOTE: e = launch_promote(L_, grid_, s_); break;
     case PH_HASH: e = launch_hash_insert(L_, grid_, s_); break;
     case PH_GEN: {
-      const bool slice = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
+      const bool fast = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
       if (prof(DIC_PROFILE_GEN)) TRY(iv_open(IV_GEN, s_));
-      e = launch_generate_finish(L_, grid_, slice, s_);
+      // (with double-buffered columns the next block is already transposed)
+      e = launch_generate_finish(L_, grid_, fast && !L_.vdouble, s_);
       if (prof(DIC_PROFILE_GEN)) TRY(iv_close(s_));
-      next_v_ready_ = slice;
+      next_v_ready_ = fast;
       ++pred_step_;
       break;
     }
@@ -793,9 +810,15 @@ dic_status Miner::prepare() {
         const uint64_t blockmax = std::min<uint64_t>(M_, n);
         const uint64_t ntiles = ((blockmax + 31) / 32 + bs_tw_ - 1) / bs_tw_;
         bs_V_words_ = (uint64_t)ntiles * bitslice_tile_words(bs_tw_, bs_l1p_);
-        TRY(alloc(&bs_V_, bs_V_words_));
+        TRY(alloc(&bs_V_, bs_V_words_ * (vdouble_ ? 2 : 1)));
         L_.V = bs_V_;
         L_.vwords = bs_V_words_;
+        L_.vdouble = vdouble_ ? 1u : 0u;
+        if (vdouble_) {
+          if (!s3_) CU(cudaStreamCreateWithFlags(&s3_, cudaStreamNonBlocking));
+          if (!ev_slice_) CU(cudaEventCreateWithFlags(&ev_slice_, cudaEventDisableTiming));
+          if (!ev_fork_) CU(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+        }
         L_.tw = (uint32_t)bs_tw_;
         L_.l1p = bs_l1p_;
         bs_grid_ = sm_count();
@@ -856,7 +879,7 @@ dic_status Miner::set_tile_width(int tw, bool *ok) {
   drop(bs_V_);
   bs_tw_ = tw;
   bs_V_words_ = (uint64_t)ntiles * bitslice_tile_words(bs_tw_, bs_l1p_);
-  TRY(alloc(&bs_V_, bs_V_words_));
+  TRY(alloc(&bs_V_, bs_V_words_ * (L_.vdouble ? 2 : 1)));
   L_.V = bs_V_;
   L_.vwords = bs_V_words_;
   L_.tw = (uint32_t)bs_tw_;
@@ -1137,6 +1160,7 @@ dic_status Miner::collect(dic_result **out) {
 
 
 dic_status Miner::run(dic_result **out) {
+  vdouble_ = true;  // this query's own stop loop: transpose the next block beside the count
   TRY(begin());
   CU(cudaStreamSynchronize(s_));
   TRY(prepare());

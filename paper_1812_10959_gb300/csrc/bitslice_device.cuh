@@ -62,7 +62,8 @@ __device__ __forceinline__ bool bs_block_tiles(const Lattice &L, Ctrl *C, uint32
 constexpr uint32_t BS_DIRECT_MAX = 24576;
 
 // Count records [lo, hi) with one warp per record: lane w reads word w of
-// each of the record's rank columns from L.V (tile t = w / TW), ANDs them and
+// each of the record's rank columns from the block's column buffer (tile
+// t = w / TW), ANDs them and
 // popcounts; the warp sum is the record's count. Then PRUNE (tallies and
 // algorithmic work are added to the caller's counters). The ranks are
 // held in registers and the rank loop is unrolled (predicated on q < k) so
@@ -77,7 +78,7 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
   constexpr uint32_t ST = bs_stride(TW);
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  const uint32_t *__restrict__ V = L.V;
+  const uint32_t *__restrict__ V = vcols(L, g);
   const uint32_t l1p = L.l1p;
   for (uint64_t c = lo + (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < hi;
        c += nwarps) {
@@ -113,7 +114,7 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
 }
 
 // Count records [c0, c0+cn) of the window over the block of stop g and apply
-// PRUNE (Algorithm 4) to each. Tiles of L.V stream through a cp.async double
+// PRUNE (Algorithm 4) to each. Tiles of the columns stream through a cp.async double
 // buffer; every thread ANDs its candidates' rank columns with 128-bit shared
 // loads and popcounts. The whole CTA must call this (it synchronises).
 template <int TW, int KRE, int NT>
@@ -125,7 +126,7 @@ __device__ __forceinline__ void bs_count_chunk(const Lattice &L, Ctrl *C, uint32
   constexpr uint32_t ST = bs_stride(TW);
   constexpr int NV = TW / 4;  // 128-bit loads per rank and tile
   const uint32_t tile_words = L.l1p * ST;
-  const uint32_t *V = L.V;
+  const uint32_t *V = vcols(L, g);
   uint32_t *S0 = sm;
   uint32_t *S1 = sm + tile_words;
   uint16_t *rk = reinterpret_cast<uint16_t *>(sm + 2 * tile_words);

@@ -128,8 +128,15 @@ struct Lattice {
   // records [0, pair_end) (the pair cohort) are counted by the tensor path
   // while it is live; 0 when that path is off
   uint32_t pair_end;
-  uint32_t pad2;
+  // 1: V holds two column buffers of vwords words each, stop g's block in
+  // buffer g % 2 (the next block is transposed while this one is counted)
+  uint32_t vdouble;
 };
+
+// The column buffer of stop g's block.
+__device__ __forceinline__ uint32_t *vcols(const Lattice &L, uint32_t g) {
+  return L.V + ((L.vdouble && (g & 1u)) ? L.vwords : 0ull);
+}
 
 // The pair-cohort kernels of the TENSOR path (GEMM and its PRUNE, which run
 // beside the BITSLICE count of the same stop) make the same checks as that
@@ -195,7 +202,8 @@ cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, ui
 // being padding. l1p = l1 rounded up to a multiple of 4.
 size_t bitslice_tile_words(int tw, uint32_t l1p);
 // Columns of the block of stop g (g = Ctrl.step when g == 0).
-cudaError_t launch_slice_block(Lattice L, cudaStream_t s);
+// ahead = 1: the block of the next stop (double-buffered columns only).
+cudaError_t launch_slice_block(Lattice L, uint32_t ahead, cudaStream_t s);
 // `direct`: the shared-memory-free form for windows expected to be small
 // (grid = CTAs of 256 threads); otherwise grid CTAs of 1024 threads.
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,

@@ -36,16 +36,18 @@ namespace dic {
 constexpr int BS_THREADS = 1024;
 
 // ------------------------------------------------------------ transpose
-// Standalone form (first stop of a run, or a resumed stop); later stops get
-// their columns from the previous stop's generate kernel.
-__global__ void __launch_bounds__(256) k_slice_block(Lattice L) {
+// Standalone form: the first stop of a run or a resumed stop, and, with
+// double-buffered columns, the next stop's block while this one is counted
+// (otherwise the previous stop's generate kernel transposes it).
+__global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t ahead) {
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
-  slice_block_warps(L, C->step, (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+  slice_block_warps(L, C->step + ahead,
+                    (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
                     (uint64_t)gridDim.x * (blockDim.x >> 5));
 }
 
-cudaError_t launch_slice_block(Lattice L, cudaStream_t s) {
+cudaError_t launch_slice_block(Lattice L, uint32_t ahead, cudaStream_t s) {
   const uint64_t blockmax = L.M < L.n ? L.M : L.n;
   const uint64_t nw32 = (blockmax + 31) / 32;
   const uint64_t items = ((nw32 + L.tw - 1) / L.tw) * L.tw * L.wc;
@@ -55,7 +57,7 @@ cudaError_t launch_slice_block(Lattice L, cudaStream_t s) {
   uint64_t want = (items + 7) / 8;
   int grid = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
   if (grid < 1) grid = 1;
-  k_slice_block<<<grid, 256, 0, s>>>(L);
+  k_slice_block<<<grid, 256, 0, s>>>(L, ahead);
   return cudaGetLastError();
 }
 

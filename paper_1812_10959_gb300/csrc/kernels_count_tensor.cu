@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
     const uint32_t tw = L.tw, st = bs_stride((int)tw);
     const uint32_t tw_shift = __ffs(tw) - 1;  // tw is 4, 8 or 16: a chunk's 4 words share a tile
     const uint64_t tile_words = (uint64_t)L.l1p * st;
-    const uint32_t *col = L.V + (ok ? rank : 0) * st;
+    const uint32_t *col = vcols(L, g) + (ok ? rank : 0) * st;
     uint8_t *row0 = gsm + (is_a ? 0u : GSTAGES * GTILE_A) + core_offset(is_a ? rr : rr - GM, 0);
     const uint32_t stage_bytes = is_a ? GTILE_A : GTILE_B;
     auto load = [&](uint32_t kc) -> uint4 {

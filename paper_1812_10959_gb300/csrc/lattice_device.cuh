@@ -273,7 +273,7 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
 // consecutive ranks with 128-bit loads hit distinct banks.
 __host__ __device__ constexpr uint32_t bs_stride(int tw) { return tw == 4 ? 4u : (uint32_t)tw + 4u; }
 
-// Transpose the block of stop g into L.V (see dic_internal.cuh): warp `wid`
+// Transpose the block of stop g into its column buffer: warp `wid`
 // of `nwarps` handles (32-row word w, mask word j) items; bit j' of the
 // result is row first+32w+j'. Out-of-range rows read as 0. An index outside
 // V (an internal sizing error) is recorded in Ctrl.error and skipped.
@@ -287,6 +287,7 @@ __device__ __forceinline__ void slice_block_warps(const Lattice &L, uint32_t g, 
   const uint32_t ntiles = (nw32 + tw - 1) / tw;
   const uint32_t wc = L.wc;
   const uint32_t lane = threadIdx.x & 31;
+  uint32_t *V = vcols(L, g);
   const uint64_t items = (uint64_t)ntiles * tw * wc;
   for (uint64_t it = wid; it < items; it += nwarps) {
     const uint32_t w = (uint32_t)(it / wc), j = (uint32_t)(it % wc);
@@ -302,8 +303,8 @@ __device__ __forceinline__ void slice_block_warps(const Lattice &L, uint32_t g, 
       L.ctrl->error = DIC_INTERNAL_BOUNDS;
       continue;
     }
-    if (r0 < l1p) L.V[i0] = lo;
-    if (r1 < l1p) L.V[i1] = hi;
+    if (r0 < l1p) V[i0] = lo;
+    if (r1 < l1p) V[i1] = hi;
   }
 }
 
