@@ -87,7 +87,7 @@ def ncu_traffic(kernel: str):
     return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
 
 
-def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto"):
+def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=None):
     """Roofline object of the kernel kind `kind` from the profiled timed steps."""
     pk = peaks()
     tot_ms = sum(s[kind + "_ms"] for s in stats)
@@ -118,11 +118,18 @@ def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto"):
                     frac=ach / ALU_PEAK_TOPS, traffic=ncu_traffic(kern), kernel=kern,
                     peak_source="derived: 152 SM x 64 INT32 lanes x 2070 MHz",
                     ops_per_launch=ops, **common)
-    # gen / settle: memory-side kernels; algorithmic bytes per launch
+    # gen / settle: latency-bound memory-side kernels; algorithmic bytes per launch
     wc, l1 = st["words_compact"], st["l1"]
     if kind == "gen":
-        # the next block's compacted rows read and its bit columns written
-        byts = db.M * wc * 8 + db.M * l1 / 8
+        # MAKECANDIDATES + CHECKFULLPASS (the next block's transposition runs
+        # beside the count): per (promoted record, rank) two pair-record
+        # shape bytes read, per emitted candidate its record written (mask
+        # W'*8 + ranks 32 + count, birth, shape, size 10 bytes), from the trace
+        if trace is not None and len(trace):
+            promoted, generated = float(trace[:, 5].sum()), float(trace[:, 7].sum())
+            byts = (promoted * l1 * 2 + generated * (wc * 8 + 32 + 10)) / len(trace)
+        else:
+            byts = 0.0
     else:
         # every pair record's counter, shape and birth read once
         byts = l1 * (l1 - 1) / 2 * 9
@@ -505,7 +512,8 @@ def main():
 
     # ---- roofline of the dominant kernel kind, timed live with CUDA events
     # on the mining stream around each of its launches in the timed steps
-    roofline = roofline_of(kind, stats, shares_ms, sum(ms), db, kw.get("count_form", "auto"))
+    roofline = roofline_of(kind, stats, shares_ms, sum(ms), db, kw.get("count_form", "auto"),
+                           res.trace)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
