@@ -19,7 +19,12 @@
 //                    stay in shared memory until the chunk is done; then each
 //                    record's support is written once and PRUNE (Algorithm
 //                    4) is applied to it in the same pass, inserting new
-//                    boxes into the box set.
+//                    boxes into the box set. Windows of at most
+//                    BS_DIRECT_MAX records are counted a warp per record
+//                    straight from the (L2-resident) columns instead.
+//   k_count_direct   that direct form alone, without shared memory, for
+//                    windows the host expects to be small.
+//   k_settle_pairs   PRUNE of the pair cohort the tensor path counted.
 //
 // Tile rows are padded to 16-byte multiples (TW+4 words for TW = 8, 16; TW
 // for TW = 4) so that eight threads reading consecutive ranks with 128-bit
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
   const uint32_t head = C->head, tail = C->tail;
   // records below `skip` (the pair cohort while the tensor path counts it)
-  // are settled by k_settle_range; this kernel counts [lo, tail)
+  // are counted and pruned by the tensor path; this kernel counts [lo, tail)
   const uint32_t skip = (L.pair_end && g <= L.stop_max) ? L.pair_end : 0u;
   const uint32_t lo = skip > head ? (skip < tail ? skip : tail) : head;
   const uint32_t ncand = tail - lo;
@@ -144,7 +149,8 @@ __global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
 }
 
 // PRUNE (Algorithm 4) for the pair cohort after the tensor kernel has added
-// this stop's counts: one thread per record.
+// this stop's counts: four records per thread, every load issued before any
+// record is examined.
 __global__ void __launch_bounds__(256) k_settle_pairs(Lattice L, uint32_t kre) {
   Ctrl *C = L.ctrl;
   if (!L.pair_end || !gram_may_run(L, C, kre)) return;
