@@ -98,7 +98,13 @@ typedef struct {
                                each host check, 1 = always the tiled
                                shared-memory kernel, 2 = always the direct
                                kernel; other values: DIC_EINVAL            */
-  uint32_t reserved[7];
+  uint32_t algorithm;       /* 0 = ParallelDIC (Algorithm 2: first pass,
+                               then the pairs of frequent items); 1 =
+                               classic DIC (Algorithm 1: every 1-itemset
+                               starts in Dashed Circle, no first pass;
+                               single queries only, DIC_EINVAL in batches
+                               and the server). Same result either way.   */
+  uint32_t reserved[6];
 } dic_options;
 
 /* Per-run statistics (dic_result_stats). */

@@ -687,6 +687,7 @@ dic_status Miner::begin() {
     CU(cudaMallocHost((void **)&h_ctrl_, sizeof(Ctrl)));
     own_h_ctrl_ = true;
   }
+  if (opt_.algorithm == 1) return DIC_OK;  // classic DIC: no first pass
   CU(cudaMallocHost((void **)&h_cnt1_, (size_t)db_->m * 4));
   uint32_t *d_cnt1 = nullptr;
   TRY(alloc(&d_cnt1, db_->m));
@@ -710,22 +711,30 @@ dic_status Miner::prepare() {
   const uint64_t n = n_;
   const uint32_t m = db_->m, W = db_->W;
   const uint64_t stop_max64 = stop_max64_;
-  if (opt_.profile) {
+  const bool classic = opt_.algorithm == 1;
+  if (opt_.profile && !classic) {
     float ms = 0;
     cudaEventElapsedTime(&ms, fa_, fb_);
     res_->stats.firstpass_ms = ms;
   }
-  const uint32_t *cnt1 = h_cnt1_;
-  for (uint32_t i = 0; i < m; ++i)
-    if (cnt1[i] >= minsup_) l1items_.push_back(i);
+  if (classic) {
+    // Algorithm 1: no first pass; every item is a rank and a 1-itemset circle
+    for (uint32_t i = 0; i < m; ++i) l1items_.push_back(i);
+  } else {
+    const uint32_t *cnt1 = h_cnt1_;
+    for (uint32_t i = 0; i < m; ++i)
+      if (cnt1[i] >= minsup_) l1items_.push_back(i);
+  }
   const std::vector<uint32_t> &l1items = l1items_;
   const uint32_t l1 = (uint32_t)l1items.size();
   res_->stats.l1 = l1;
   const uint32_t wc = std::max<uint32_t>(1, (l1 + 63) / 64);
   res_->stats.words_compact = wc;
-  tests_ = (uint64_t)m * n;
-  for (uint32_t i : l1items) { sets_.push_back({i}); supps_.push_back(cnt1[i]); }
-  const uint64_t npairs = (uint64_t)l1 * (l1 - (l1 ? 1 : 0)) / 2;
+  tests_ = classic ? 0 : (uint64_t)m * n;
+  if (!classic)
+    for (uint32_t i : l1items) { sets_.push_back({i}); supps_.push_back(h_cnt1_[i]); }
+  // the first cohort: all pairs of frequent ranks, or (classic) all 1-itemsets
+  const uint64_t npairs = classic ? (uint64_t)l1 : (uint64_t)l1 * (l1 - (l1 ? 1 : 0)) / 2;
   if (npairs > 0) {
     if (npairs > candidates_cap_limit_ ||
         (opt_.max_candidates && npairs > opt_.max_candidates))
@@ -752,6 +761,7 @@ dic_status Miner::prepare() {
     L_.wc = wc;
     L_.l1 = l1;
     uint64_t cap = npairs + npairs / 8 + 4096;
+    L_.pairs_lex = classic ? 0u : 1u;
     if (opt_.max_candidates && cap > opt_.max_candidates) cap = opt_.max_candidates;
     if (cap > candidates_cap_limit_) cap = candidates_cap_limit_;
     L_.cap = (uint32_t)cap;
@@ -779,13 +789,16 @@ dic_status Miner::prepare() {
     c.tail = (uint32_t)npairs;
     c.n_live = (uint32_t)npairs;
     c.n_cohorts = 1;
-    c.max_k = 2;
+    c.max_k = classic ? 1 : 2;
     c.tests = tests_;
     *h_ctrl_ = c;
     CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
-    CU(launch_pair_join(L_, npairs, s_));
+    if (classic)
+      CU(launch_singleton_join(L_, s_));
+    else
+      CU(launch_pair_join(L_, npairs, s_));
     ++launches_;
-    nw_ = (uint32_t)rows_width_bucket(2, wc);
+    nw_ = (uint32_t)rows_width_bucket(c.max_k, wc);
 
     // ---- BITSLICE tiles: widest tile whose double buffer leaves room for
     // a useful candidate chunk in shared memory
@@ -829,8 +842,9 @@ dic_status Miner::prepare() {
     // fill a tile (AUTO) or an explicit request
     {
       const uint64_t blockmax = std::min<uint64_t>(M_, n);
-      const bool want = opt_.count_path == DIC_COUNT_TENSOR ||
-                        (opt_.count_path == DIC_COUNT_AUTO && l1 >= 256 && blockmax >= 2048);
+      const bool want = !classic && (opt_.count_path == DIC_COUNT_TENSOR ||
+                                     (opt_.count_path == DIC_COUNT_AUTO && l1 >= 256 &&
+                                      blockmax >= 2048));
       tc_ok_ = false;
       if (want && bs_ok_ && blockmax < (1ull << 24) && npairs <= 0xFFFFFFF0ull) {
         tc_nkc_max_ = gram_chunks(blockmax);
@@ -1177,6 +1191,7 @@ static dic_status check_options(const dic_options &o) {
   if (o.count_form > 2) return fail(DIC_EINVAL, "count_form must be 0, 1 or 2 (got %u)", o.count_form);
   if (o.count_path > DIC_COUNT_TENSOR)
     return fail(DIC_EINVAL, "unknown count_path %u", o.count_path);
+  if (o.algorithm > 1) return fail(DIC_EINVAL, "algorithm must be 0 or 1 (got %u)", o.algorithm);
   return DIC_OK;
 }
 
@@ -1415,6 +1430,7 @@ extern "C" dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *m
   dic_options_init(&o);
   if (opt) std::memcpy(&o, opt, std::min<size_t>(sizeof o, opt->struct_size ? opt->struct_size : sizeof o));
   TRY(check_options(o));
+  if (o.algorithm != 0) return fail(DIC_EINVAL, "classic DIC runs single queries only");
   if (o.count_path == DIC_COUNT_ROWS) {  // plain per-query GPU DIC, one after another
     for (uint32_t i = 0; i < count; ++i) {
       dic_status st = dic_mine_ex(dbs[i], minsup[i], M[i], &o, nullptr, &out[i]);
@@ -1692,6 +1708,7 @@ extern "C" dic_status dic_server_create(uint64_t hbm_budget_bytes, uint32_t max_
   dic_options_init(&sv->opt);
   if (opt) std::memcpy(&sv->opt, opt, std::min<size_t>(sizeof sv->opt, opt->struct_size ? opt->struct_size : sizeof sv->opt));
   TRY(check_options(sv->opt));
+  if (sv->opt.algorithm != 0) return fail(DIC_EINVAL, "classic DIC runs single queries only");
   cudaGetDevice(&sv->device);
   init_pool(sv->device);
   CU(cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking));

@@ -131,6 +131,11 @@ struct Lattice {
   // 1: V holds two column buffers of vwords words each, stop g's block in
   // buffer g % 2 (the next block is transposed while this one is counted)
   uint32_t vdouble;
+  // 1: records [0, l1(l1-1)/2) are all pairs of ranks in lexicographic order
+  // (the first pass's pair join); 0 for classic DIC, whose pairs are
+  // generated one by one
+  uint32_t pairs_lex;
+  uint32_t pad3;
 };
 
 // The column buffer of stop g's block.
@@ -181,6 +186,8 @@ cudaError_t launch_pack_csr(const uint64_t *row_ptr, const uint32_t *items, uint
 cudaError_t launch_check_padding(const uint64_t *words, uint64_t n, uint32_t m, uint32_t W,
                                  uint32_t *bad, cudaStream_t s);
 cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s);
+// Classic DIC (Algorithm 1): every rank as a 1-itemset circle, records 0..l1-1.
+cudaError_t launch_singleton_join(Lattice L, cudaStream_t s);
 cudaError_t launch_count_rows(Lattice L, int nw, int grid, cudaStream_t s);
 cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s);
 cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s);

@@ -200,6 +200,32 @@ __global__ void k_pair_join(Lattice L, uint64_t npairs) {
   }
 }
 
+// Algorithm 1's start: Dashed Circle holds every 1-itemset (rank r is record
+// r); with no first pass the ranks are all m items.
+__global__ void k_singleton_join(Lattice L) {
+  const uint64_t total = (uint64_t)L.l1 * L.wc;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)(i / L.wc), w = (uint32_t)(i % L.wc);
+    L.cmask[i] = (r >> 6) == w ? 1ull << (r & 63) : 0ull;
+    if (w == 0) {
+      L.csupp[r] = 0;
+      L.cbirth[r] = 0;
+      L.cshape[r] = SH_CIRCLE;
+      L.ck[r] = 1;
+      L.cranks[(uint64_t)r * KRMAX] = (uint16_t)r;
+    }
+  }
+}
+
+cudaError_t launch_singleton_join(Lattice L, cudaStream_t s) {
+  const uint64_t total = (uint64_t)L.l1 * L.wc;
+  const uint64_t want = (total + 255) / 256;
+  const int grid = (int)(want < 65535ull * 4 ? (want ? want : 1) : 65535ull * 4);
+  k_singleton_join<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s) {
   if (npairs == 0) return cudaSuccess;
   uint64_t want = (npairs * L.wc + 255) / 256;

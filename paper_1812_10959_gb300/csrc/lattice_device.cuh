@@ -118,47 +118,50 @@ __device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_
 // and every subset of a box is a box, so the pair records {a0, r} and
 // {a1, r} must both be boxes. Most ranks r fail it with two loads and no
 // probe of the box set; for a pair A those two records are all of C's
-// other subsets, and the box set is not probed at all.
+// other subsets, and the box set is not probed at all. (Only where the pair
+// records are the first pass's complete lexicographic join.)
 __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_t p, uint32_t r,
                                               uint32_t g, uint32_t base) {
   const uint32_t wc = L.wc;
   const uint32_t cA = L.newbox[p];
   const uint32_t kA = L.ck[cA];
-  const uint32_t a0 = L.cranks[(uint64_t)cA * KRMAX], a1 = L.cranks[(uint64_t)cA * KRMAX + 1];
-  if (r == a0 || r == a1) return;  // r in A
-  const uint64_t l1 = L.l1;
-  const uint64_t i0 = r < a0 ? pair_record(r, a0, l1) : pair_record(a0, r, l1);
-  const uint64_t i1 = r < a1 ? pair_record(r, a1, l1) : pair_record(a1, r, l1);
-  if (L.cshape[i0] != SH_BOX || L.cshape[i1] != SH_BOX) return;
-  if (kA == 2) {
-    // A = {a0, a1}: the 2-subsets of C other than A are the pair records
-    // {a1, r} = C \ {a0} and {a0, r} = C \ {a1}, both boxes by the check
-    // above, so only the canonical-parent rule remains (no box-set probe)
-    if (a0 < r && L.cpromo[i1] == g) return;
-    if (a1 < r && L.cpromo[i0] == g) return;
-    const uint32_t pos = base + atomicAdd(&C->n_gen, 1u);
-    if (pos >= L.cap) {
-      C->stall = ST_CAND;
+  if (L.pairs_lex && kA >= 2) {
+    const uint32_t a0 = L.cranks[(uint64_t)cA * KRMAX], a1 = L.cranks[(uint64_t)cA * KRMAX + 1];
+    if (r == a0 || r == a1) return;  // r in A
+    const uint64_t l1 = L.l1;
+    const uint64_t i0 = r < a0 ? pair_record(r, a0, l1) : pair_record(a0, r, l1);
+    const uint64_t i1 = r < a1 ? pair_record(r, a1, l1) : pair_record(a1, r, l1);
+    if (L.cshape[i0] != SH_BOX || L.cshape[i1] != SH_BOX) return;
+    if (kA == 2) {
+      // A = {a0, a1}: the 2-subsets of C other than A are the pair records
+      // {a1, r} = C \ {a0} and {a0, r} = C \ {a1}, both boxes by the check
+      // above, so only the canonical-parent rule remains (no box-set probe)
+      if (a0 < r && L.cpromo[i1] == g) return;
+      if (a1 < r && L.cpromo[i0] == g) return;
+      const uint32_t pos = base + atomicAdd(&C->n_gen, 1u);
+      if (pos >= L.cap) {
+        C->stall = ST_CAND;
+        return;
+      }
+      const uint32_t lo = r < a0 ? r : a0, hi = r > a1 ? r : a1;
+      const uint32_t mid = r < a0 ? a0 : (r > a1 ? a1 : r);
+      for (uint32_t i = 0; i < wc; ++i) {
+        uint64_t x = 0;
+        if ((lo >> 6) == i) x |= 1ull << (lo & 63);
+        if ((mid >> 6) == i) x |= 1ull << (mid & 63);
+        if ((hi >> 6) == i) x |= 1ull << (hi & 63);
+        L.cmask[(uint64_t)pos * wc + i] = x;
+      }
+      uint16_t *rk = L.cranks + (uint64_t)pos * KRMAX;
+      rk[0] = (uint16_t)lo; rk[1] = (uint16_t)mid; rk[2] = (uint16_t)hi;
+      L.csupp[pos] = 0;
+      L.cbirth[pos] = g;
+      L.cshape[pos] = SH_CIRCLE;
+      L.ck[pos] = 3;
+      atomicMax(&C->max_k, 3u);
       return;
     }
-    const uint32_t lo = r < a0 ? r : a0, hi = r > a1 ? r : a1;
-    const uint32_t mid = r < a0 ? a0 : (r > a1 ? a1 : r);
-    for (uint32_t i = 0; i < wc; ++i) {
-      uint64_t x = 0;
-      if ((lo >> 6) == i) x |= 1ull << (lo & 63);
-      if ((mid >> 6) == i) x |= 1ull << (mid & 63);
-      if ((hi >> 6) == i) x |= 1ull << (hi & 63);
-      L.cmask[(uint64_t)pos * wc + i] = x;
-    }
-    uint16_t *rk = L.cranks + (uint64_t)pos * KRMAX;
-    rk[0] = (uint16_t)lo; rk[1] = (uint16_t)mid; rk[2] = (uint16_t)hi;
-    L.csupp[pos] = 0;
-    L.cbirth[pos] = g;
-    L.cshape[pos] = SH_CIRCLE;
-    L.ck[pos] = 3;
-    atomicMax(&C->max_k, 3u);
-    return;
-  }
+  }  // (classic DIC, or a 1-itemset parent: the box-set probes below decide)
   const uint64_t *A = L.cmask + (uint64_t)cA * wc;
   const uint32_t wr = r >> 6;
   const uint64_t br = 1ull << (r & 63);

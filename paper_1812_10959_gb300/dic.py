@@ -30,7 +30,8 @@ class Options(ctypes.Structure):
                 ("steps_per_sync", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
                 ("profile", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
                 ("profile_every", ctypes.c_uint32), ("tile_words", ctypes.c_uint32),
-                ("count_form", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+                ("count_form", ctypes.c_uint32), ("algorithm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -250,11 +251,13 @@ def profile_mask(profile) -> int:
 
 
 COUNT_FORMS = {"auto": 0, "tiled": 1, "direct": 2}
+ALGORITHMS = {"paralleldic": 0, "classic": 1}
 
 
 def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
             profile=False, max_candidates: int = 0, profile_every: int = 0,
-            tile_words: int = 0, count_form: str = "auto") -> Options:
+            tile_words: int = 0, count_form: str = "auto",
+            algorithm: str = "paralleldic") -> Options:
     o = Options()
     _lib.dic_options_init(ctypes.byref(o))
     o.count_path = PATHS[path]
@@ -264,6 +267,7 @@ def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
     o.profile_every = profile_every
     o.tile_words = tile_words
     o.count_form = COUNT_FORMS[count_form]
+    o.algorithm = ALGORITHMS[algorithm]
     o.max_candidates = max_candidates
     return o
 
@@ -271,24 +275,28 @@ def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
 def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
          profile=False, steps_per_sync: int = 0, use_graph: bool = True,
          max_candidates: int = 0, profile_every: int = 0, tile_words: int = 0,
-         count_form: str = "auto") -> Result:
-    """All itemsets with support >= minsup (integer count), blocks of M rows."""
+         count_form: str = "auto", algorithm: str = "paralleldic") -> Result:
+    """All itemsets with support >= minsup (integer count), blocks of M rows.
+    algorithm: "paralleldic" (Algorithm 2, first pass then pairs) or
+    "classic" (Algorithm 1, every 1-itemset a dashed circle)."""
     o = options(path, steps_per_sync, use_graph, profile, max_candidates, profile_every,
-                tile_words, count_form)
+                tile_words, count_form, algorithm)
     h = ctypes.c_void_p()
     _check(_lib.dic_mine_ex(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
                             ctypes.byref(h)))
     return _result(h)
 
 
-def mine_batch(dbs, minsups, Ms, path: str = "auto", profile=False, tile_words: int = 0):
-    """Mine several (db, minsup, M) queries together; returns a list of Result."""
+def mine_batch(dbs, minsups, Ms, path: str = "auto", profile=False, tile_words: int = 0,
+               algorithm: str = "paralleldic"):
+    """Mine several (db, minsup, M) queries together; returns a list of Result
+    (ParallelDIC only: the library rejects algorithm="classic" here)."""
     cnt = len(dbs)
     handles = (ctypes.c_void_p * max(cnt, 1))(*[d.handle.value for d in dbs])
     ms = np.ascontiguousarray(minsups, dtype=np.uint32)
     Ms_ = np.ascontiguousarray(Ms, dtype=np.uint64)
     outs = (ctypes.c_void_p * max(cnt, 1))()
-    o = options(path, profile=profile, tile_words=tile_words)
+    o = options(path, profile=profile, tile_words=tile_words, algorithm=algorithm)
     _check(_lib.dic_mine_batch(ctypes.cast(handles, ctypes.c_void_p), ms.ctypes.data,
                                Ms_.ctypes.data, cnt, ctypes.byref(o),
                                ctypes.cast(outs, ctypes.c_void_p)))
