@@ -263,6 +263,39 @@ def run_reference(args):
     return 0
 
 
+def run_sweep(args, dic, torch):
+    """Mine time of both algorithms over block sizes M and support thresholds
+    on one database (the analogue of the paper's study of M): every point
+    is checked to give the same itemsets under both algorithms."""
+    db = workload(args.workload)
+    h = dic.load_db_csr(db.row_ptr, db.items, db.n, db.m)
+    points = []
+    for frac in (0.0025, 0.005, 0.01):
+        minsup = synth.minsup_count(db.n, frac)
+        for M in sorted({db.n // 400, db.n // 100, db.n // 20, db.n // 2}):
+            row = {"minsup": minsup, "M": M}
+            ref = None
+            for alg in ("paralleldic", "classic"):
+                for _ in range(args.warmup):
+                    r = dic.mine(h, minsup, M, algorithm=alg)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    r = dic.mine(h, minsup, M, algorithm=alg)
+                dt = (time.perf_counter() - t0) / args.steps
+                sig = r.itemsets()
+                assert ref is None or sig == ref, "algorithms disagree"
+                ref = sig
+                row[alg] = {"ms": 1000 * dt, "tests": int(r.stats["tests"]),
+                            "stops": int(r.stats["stops"]), "tests_per_s": r.stats["tests"] / dt}
+            row["frequent_itemsets"] = len(ref)
+            points.append(row)
+    print(json.dumps({"sweep": "mine time over M and minsup (wall clock, result on the host)",
+                      "workload": db.name, "steps": args.steps, "warmup": args.warmup,
+                      "points": points}), flush=True)
+    return 0
+
+
 def run_batched(args, dic, torch):
     """512 databases of the batched recipe mined together (one dic_mine_batch
     per step), against plain per-query GPU DIC (ROWS path, one query at a
@@ -404,6 +437,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
     ap.add_argument("--no-tune", action="store_true",
                     help="with --path auto: use the library's rule instead of the autotuner")
+    ap.add_argument("--algorithm", default="paralleldic", choices=["paralleldic", "classic"],
+                    help="classic: Algorithm 1 (no first pass; every item a dashed circle)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="mine time over M and minsup for both algorithms (one JSON line)")
     ap.add_argument("--batch-dbs", type=int, default=512, help="databases for --workload batched")
     ap.add_argument("--served-queries", type=int, default=10_000)
     ap.add_argument("--plain-sample", type=int, default=300,
@@ -428,6 +465,8 @@ def main():
     pb.build()
     import paper_1812_10959_gb300 as dic
 
+    if args.sweep:
+        return run_sweep(args, dic, torch)
     if args.workload == "batched":
         return run_batched(args, dic, torch)
     if args.workload == "served":
@@ -445,7 +484,9 @@ def main():
     # query itself, all candidates checked to give the same result), or the
     # path given on the command line
     tuned = None
-    if args.path == "auto" and not args.no_tune:
+    if args.algorithm != "paralleldic":
+        kw = dict(path=args.path, algorithm=args.algorithm)
+    elif args.path == "auto" and not args.no_tune:
         from paper_1812_10959_gb300 import autotune
         tuned = autotune.Tuner(repeats=2).tune(handle, db.minsup, db.M)
         kw = tuned.kwargs()
@@ -529,7 +570,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": db.name, "n": db.n, "m": db.m, "minsup": db.minsup,
-                       "M": db.M,
+                       "M": db.M, "algorithm": args.algorithm,
                        "count_path": (f"autotuned: {tuned.path}, tile_words {tuned.tile_words}, "
                                       f"count form {tuned.count_form}") if tuned else args.path,
                        "tests_per_step": tests_step,
