@@ -53,15 +53,20 @@ typedef struct dic_db dic_db;
 typedef struct dic_result dic_result;
 
 /* Support-counting kernel used for Algorithm 3 (COUNTSUPPORT). All paths
- * give identical supports; they differ only in speed.
+ * give identical supports and traces; they differ only in speed.
  *   ROWS      the paper's test (T AND C) == C on row-major bitmaps, one
  *             candidate per thread, rows staged through shared memory.
  *   BITSLICE  the block is transposed into per-item bit columns; a
  *             candidate's count over 32 rows is popc of the AND of its
  *             items' column words.
- *   TENSOR    matched-item counts as a 0/1 GEMM (rows x items times items x
- *             candidates) on tcgen05 with an exact compare-to-|C| epilogue.
- *   AUTO      chosen per stop by the built-in tuner. */
+ *   TENSOR    BITSLICE, except that the first pass's pair cohort is counted
+ *             as the Gram matrix of the block's 0/1 item columns on the
+ *             tcgen05 tensor cores (e4m3 operands, fp32 accumulation, exact
+ *             below 2^24 rows per block).
+ *   AUTO      a rule: TENSOR when there are >= 256 frequent items and
+ *             blocks of >= 2,048 rows, else BITSLICE when a block's columns
+ *             fit shared memory and every itemset has <= 16 items, else
+ *             ROWS. (The Python autotuner times the paths per query.) */
 typedef enum {
   DIC_COUNT_AUTO = 0,
   DIC_COUNT_ROWS = 1,
@@ -72,9 +77,9 @@ typedef enum {
 /* dic_options.profile bits: which kernels of the stop loop are bracketed by
  * CUDA events (each timed kind adds two event records per stop). */
 #define DIC_PROFILE_COUNT  1u  /* COUNTSUPPORT: ROWS or BITSLICE count kernel  */
-#define DIC_PROFILE_GRAM   2u  /* TENSOR pair-cohort operand + GEMM            */
+#define DIC_PROFILE_GRAM   2u  /* TENSOR pair-cohort GEMM                      */
 #define DIC_PROFILE_SETTLE 4u  /* PRUNE of the tensor-counted pairs            */
-#define DIC_PROFILE_GEN    8u  /* MAKECANDIDATES + CHECKFULLPASS (+ slicing)   */
+#define DIC_PROFILE_GEN    8u  /* MAKECANDIDATES + CHECKFULLPASS               */
 #define DIC_PROFILE_ALL   15u
 
 /* Mining options. Initialise with dic_options_init(); unknown trailing
@@ -110,12 +115,13 @@ typedef struct {
 /* Per-run statistics (dic_result_stats). */
 typedef struct {
   uint64_t tests;           /* candidate-transaction tests: m*n for the
-                               first pass plus sum over stops of
-                               |DASHED| * |block|                          */
+                               first pass (none in classic DIC) plus sum
+                               over stops of |DASHED| * |block|            */
   uint64_t stops;           /* iterations of Algorithm 2's loop            */
   uint64_t candidates;      /* candidates ever created (incl. pairs)       */
   uint64_t frequent;        /* itemsets in the result                      */
-  uint32_t l1;              /* frequent items                              */
+  uint32_t l1;              /* frequent items (classic DIC: all m items,
+                               the ranks it counts)                        */
   uint32_t words;           /* W = ceil(m/64)                              */
   uint32_t words_compact;   /* W' = ceil(l1/64)                            */
   uint32_t kernel_launches; /* kernels launched by this run                */
@@ -127,7 +133,7 @@ typedef struct {
   uint64_t count_ops;       /* algorithmic integer ops of the count kernels:
                                ROWS h+2 per test (h = touched 32-bit
                                halves), BITSLICE k+1 per 32-row word      */
-  double gram_ms;           /* TENSOR pair-cohort operand + GEMM
+  double gram_ms;           /* TENSOR pair-cohort GEMM
                                (DIC_PROFILE_GRAM)                          */
   uint64_t gram_launches;   /* pair-cohort GEMMs timed                     */
   double settle_ms;         /* PRUNE of the tensor-counted pairs
