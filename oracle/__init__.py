@@ -12,6 +12,8 @@ Every function wraps a plain serial routine of ``dic_oracle.cpp``:
   * :func:`support`      support of given itemsets by tid-list intersection
   * :func:`pair_supports` co-occurrence counts of every item pair
   * :func:`pack`         BitMask of Section 4.1
+  * :func:`rules`        association rules from frequent itemsets (Section 1's
+                         second subtask), plain Python loops
 Results are lists of ``(items_tuple, support)`` in canonical order (size, then
 lexicographic), plus a per-stop trace for the DIC forms.
 
@@ -186,3 +188,31 @@ def pack(row_ptr, items, n: int, m: int) -> np.ndarray:
     out = np.zeros((max(n, 1), W), dtype=np.uint64)
     lib.oracle_pack(rp.ctypes.data, it.ctypes.data, n, m, out.ctypes.data)
     return out[:n]
+
+
+def rules(itemsets, conf_num: int, conf_den: int) -> list:
+    """Association rules from frequent itemsets, the second subtask of
+    Section 1 (the paper leaves its definition to its reference [1]; the
+    textbook one is taken): for every frequent Z with |Z| >= 2 and every
+    non-empty proper subset X of Z, the rule X -> Z \\ X holds when its
+    confidence supp(Z) / supp(X) is at least conf_num / conf_den, compared
+    exactly as supp(Z) * conf_den >= conf_num * supp(X).
+
+    `itemsets` is a list of (items_tuple, support), downward closed (every
+    subset of a member is a member). Returns [(X, Z \\ X, supp(Z), supp(X))]
+    sorted by X (size, then items) and then by Z \\ X (size, then items).
+    Plain loops: small inputs only."""
+    sup = {tuple(s): int(v) for s, v in itemsets}
+    out = []
+    for z, sz in sup.items():
+        k = len(z)
+        if k < 2:
+            continue
+        for code in range(1, (1 << k) - 1):
+            x = tuple(z[b] for b in range(k) if code >> b & 1)
+            y = tuple(z[b] for b in range(k) if not code >> b & 1)
+            sx = sup[x]  # KeyError: not downward closed
+            if sz * conf_den >= conf_num * sx:
+                out.append((x, y, sz, sx))
+    out.sort(key=lambda r: (len(r[0]), r[0], len(r[1]), r[1]))
+    return out

@@ -198,3 +198,59 @@ def test_hand_worked_examples(ex):
     assert r.trace.tolist() == ex["trace"]
     assert r.tests == ex["tests"]
     assert oracle.bruteforce(rp, it, ex["n"], ex["m"], ex["minsup"]).itemsets == ex["L"]
+
+
+# ---------------------------------------------------------------- rules
+def _rules_direct(rows, m, minsup, num, den):
+    """Every split X -> Y (disjoint, non-empty) of a frequent X | Y, with
+    supports counted by scanning the rows and confidence compared as
+    fractions: an enumeration independent of the oracle's."""
+    from fractions import Fraction
+    sets = [frozenset(r) for r in rows]
+
+    def supp(s):
+        return sum(1 for t in sets if s <= t)
+
+    out = []
+    for zmask in range(1, 1 << m):
+        z = [i for i in range(m) if zmask >> i & 1]
+        if len(z) < 2:
+            continue
+        sz = supp(frozenset(z))
+        if sz < minsup:
+            continue
+        for xmask in range(1, 1 << m):
+            if xmask & ~zmask or xmask == zmask:
+                continue
+            x = tuple(i for i in range(m) if xmask >> i & 1)
+            y = tuple(i for i in z if not xmask >> i & 1)
+            sx = supp(frozenset(x))
+            if Fraction(sz, sx) >= Fraction(num, den):
+                out.append((x, y, sz, sx))
+    out.sort(key=lambda r: (len(r[0]), r[0], len(r[1]), r[1]))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_rules_match_direct_enumeration(seed):
+    rng = np.random.default_rng(4000 + seed)
+    m = int(rng.integers(2, 9))
+    n = int(rng.integers(1, 50))
+    rows = [np.flatnonzero(rng.random(m) < 0.5).tolist() for _ in range(n)]
+    rp, it = to_csr(rows)
+    minsup = max(1, n // 6)
+    L = oracle.bruteforce(rp, it, n, m, minsup).itemsets
+    for num, den in ((0, 1), (1, 2), (2, 3), (1, 1)):
+        assert oracle.rules(L, num, den) == _rules_direct(rows, m, minsup, num, den)
+
+
+def test_rules_closed_form_identical_rows():
+    # r copies of one row T, minsup 1: every split of every subset holds at
+    # confidence 1; there are 3^k - 2^(k+1) + 1 of them
+    k, r = 6, 4
+    rows = [list(range(k))] * r
+    rp, it = to_csr(rows)
+    L = oracle.bruteforce(rp, it, r, k, 1).itemsets
+    got = oracle.rules(L, 1, 1)
+    assert len(got) == 3 ** k - 2 ** (k + 1) + 1
+    assert all(sz == r and sx == r for _, _, sz, sx in got)
