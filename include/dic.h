@@ -262,6 +262,37 @@ dic_status dic_result_trace(const dic_result *r, uint64_t *rows);
 dic_status dic_result_stats(const dic_result *r, dic_stats *out);
 void dic_result_free(dic_result *r);
 
+/* ------------------------------------------------------ association rules */
+
+/* Association rules from frequent itemsets: the second subtask of the
+ * problem statement (Section 1; the paper leaves the definition to its
+ * reference [1], the textbook one is used). For every itemset Z with >= 2
+ * items and every non-empty proper subset X of Z, the rule X -> Z \ X is
+ * output when supp(Z) * conf_den >= conf_num * supp(X) (confidence at least
+ * conf_num / conf_den, compared exactly). Evaluated on the current device.
+ *
+ * masks[count * W] (W = ceil(m/64), item p = bit p%64 of word p/64), k[count]
+ * (popcounts of the masks, <= 31) and support[count] are host arrays, e.g. the
+ * output of dic_result_copy; they must be downward closed (every non-empty
+ * subset of an itemset is one of them). The call copies them; the caller
+ * keeps ownership. On DIC_OK *out owns the rules (dic_rules_free).
+ * Errors: DIC_EINVAL for NULL pointers, m = 0, conf_den = 0, a size that is
+ * not the mask's popcount, an item >= m, or input that is not downward
+ * closed; DIC_ECAPACITY for an itemset of more than 31 items or more than
+ * 2^32 splits in total; DIC_ENOMEM / DIC_ECUDA. */
+typedef struct dic_rules dic_rules;
+dic_status dic_rules_from_itemsets(const uint64_t *masks, const uint32_t *k,
+                                   const uint32_t *support, uint64_t count, uint32_t m,
+                                   uint32_t conf_num, uint32_t conf_den, dic_rules **out);
+uint64_t dic_rules_count(const dic_rules *r);
+/* Copy the rules in canonical order (antecedent by size then items, then
+ * consequent by size then items): antecedent[count*W], consequent[count*W],
+ * support[count] (= supp(Z)), antecedent_support[count] (= supp(X)). Any
+ * pointer may be NULL to skip it. */
+dic_status dic_rules_copy(const dic_rules *r, uint64_t *antecedent, uint64_t *consequent,
+                          uint32_t *support, uint32_t *antecedent_support);
+void dic_rules_free(dic_rules *r);
+
 /* ------------------------------------------------ allocation-free count */
 
 /* Size of the scratch array of dic_count_support_noalloc, in 32-bit words

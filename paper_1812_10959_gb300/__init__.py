@@ -8,7 +8,7 @@ exists; using the binding without the library raises ImportError."""
 import importlib
 
 _EXPORTS = ("Database", "DicError", "Result", "Server", "load_db", "load_db_csr",
-            "load_db_device", "mine", "mine_batch", "minsup_count")
+            "load_db_device", "mine", "mine_batch", "minsup_count", "rules")
 __all__ = list(_EXPORTS) + ["dic"]
 
 

@@ -1852,6 +1852,171 @@ extern "C" dic_status dic_result_stats(const dic_result *r, dic_stats *out) {
 }
 extern "C" void dic_result_free(dic_result *r) { delete r; }
 
+// ------------------------------------------------------ association rules
+namespace {
+// A device buffer of the rules call, allocated and freed on its stream.
+struct RuleBuf {
+  void *p = nullptr;
+  cudaStream_t s;
+  explicit RuleBuf(cudaStream_t st) : s(st) {}
+  dic_status alloc(size_t bytes) {
+    cudaError_t e = cudaMallocAsync(&p, bytes < 16 ? 16 : bytes, s);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(DIC_ENOMEM, "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    return DIC_OK;
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  ~RuleBuf() { release(); }
+};
+}  // namespace
+
+struct dic_rules {
+  uint32_t W = 1;
+  std::vector<uint64_t> ante, cons;  // [count][W]
+  std::vector<uint32_t> supp, supp_ante;
+};
+
+extern "C" dic_status dic_rules_from_itemsets(const uint64_t *masks, const uint32_t *k,
+                                              const uint32_t *support, uint64_t count,
+                                              uint32_t m, uint32_t conf_num, uint32_t conf_den,
+                                              dic_rules **out) {
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (m == 0) return fail(DIC_EINVAL, "m must be >= 1");
+  if (conf_den == 0) return fail(DIC_EINVAL, "conf_den must be >= 1");
+  if (count && (!masks || !k || !support)) return fail(DIC_EINVAL, "NULL argument");
+  if (count >= 0xFFFFFFFFull) return fail(DIC_ECAPACITY, "too many itemsets");
+  const uint32_t W = (m + 63) / 64;
+  // host checks: sizes are the popcounts, no item >= m, the work fits
+  std::vector<uint64_t> prefix((size_t)count + 1, 0);
+  for (uint64_t i = 0; i < count; ++i) {
+    uint32_t pc = 0;
+    for (uint32_t w = 0; w < W; ++w) pc += (uint32_t)__builtin_popcountll(masks[i * W + w]);
+    if (pc != k[i]) return fail(DIC_EINVAL, "k[%llu] is not the popcount of its mask",
+                                (unsigned long long)i);
+    if (m % 64 && (masks[i * W + W - 1] >> (m % 64)))
+      return fail(DIC_EINVAL, "itemset %llu holds an item >= m", (unsigned long long)i);
+    if (pc > 31) return fail(DIC_ECAPACITY, "itemset %llu has more than 31 items",
+                             (unsigned long long)i);
+    prefix[i + 1] = prefix[i] + (pc >= 2 ? (1ull << pc) - 2 : 0);
+  }
+  const uint64_t total = prefix[count];
+  if (total > 0xFFFFFFFFull) return fail(DIC_ECAPACITY, "more than 2^32 splits");
+  std::unique_ptr<dic_rules> r(new (std::nothrow) dic_rules());
+  if (!r) return fail(DIC_ENOMEM, "host allocation");
+  r->W = W;
+  if (total == 0) { *out = r.release(); return DIC_OK; }
+  uint32_t hcap = 1024;
+  while ((uint64_t)hcap < 2 * count) hcap <<= 1;
+  cudaStream_t s;
+  CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  RuleBuf d_masks(s), d_k(s), d_supp(s), d_prefix(s), d_hslot(s), d_cursor(s), d_z(s),
+      d_code(s), d_sx(s), d_err(s);
+  dic_status st = DIC_OK;
+  uint32_t herr = 0;
+  unsigned long long nrules = 0;
+  do {
+    if ((st = d_masks.alloc(count * W * 8)) != DIC_OK) break;
+    if ((st = d_k.alloc(count * 4)) != DIC_OK) break;
+    if ((st = d_supp.alloc(count * 4)) != DIC_OK) break;
+    if ((st = d_prefix.alloc((count + 1) * 8)) != DIC_OK) break;
+    if ((st = d_hslot.alloc((uint64_t)hcap * 4)) != DIC_OK) break;
+    if ((st = d_cursor.alloc(8)) != DIC_OK) break;
+    if ((st = d_z.alloc(total * 4)) != DIC_OK) break;
+    if ((st = d_code.alloc(total * 4)) != DIC_OK) break;
+    if ((st = d_sx.alloc(total * 4)) != DIC_OK) break;
+    if ((st = d_err.alloc(4)) != DIC_OK) break;
+    cudaError_t e = cudaMemcpyAsync(d_masks.p, masks, count * W * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_k.p, k, count * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_supp.p, support, count * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_prefix.p, prefix.data(), (count + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_hslot.p, 0, (size_t)hcap * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cursor.p, 0, 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err.p, 0, 4, s);
+    if (e == cudaSuccess)
+      e = launch_rules((const uint64_t *)d_masks.p, (const uint32_t *)d_k.p,
+                       (const uint32_t *)d_supp.p, (const uint64_t *)d_prefix.p,
+                       (uint32_t *)d_hslot.p, count, W, hcap, conf_num, conf_den, total,
+                       (unsigned long long *)d_cursor.p, (uint32_t *)d_z.p,
+                       (uint32_t *)d_code.p, (uint32_t *)d_sx.p, (uint32_t *)d_err.p, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nrules, d_cursor.p, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err.p, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = fail(DIC_ECUDA, "rules: %s", cudaGetErrorString(e)); break; }
+    if (herr & 1u) { st = fail(DIC_EINVAL, "the itemsets are not downward closed"); break; }
+    if (herr & 2u) { st = fail(DIC_ECUDA, "rules: internal table sizing error"); break; }
+    if (nrules > total) nrules = total;
+    std::vector<uint32_t> hz(nrules), hc(nrules), hs(nrules);
+    if (nrules) {
+      e = cudaMemcpyAsync(hz.data(), d_z.p, nrules * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), d_code.p, nrules * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), d_sx.p, nrules * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { st = fail(DIC_ECUDA, "rules: %s", cudaGetErrorString(e)); break; }
+    }
+    // expand (itemset, split code) into item lists and sort canonically
+    struct Rule { std::vector<uint32_t> x, y; uint32_t sz, sx; };
+    std::vector<Rule> rules(nrules);
+    for (uint64_t q = 0; q < nrules; ++q) {
+      const uint64_t *Z = masks + (uint64_t)hz[q] * W;
+      uint32_t t = 0;
+      for (uint32_t w = 0; w < W; ++w)
+        for (uint64_t y = Z[w]; y; y &= y - 1, ++t) {
+          const uint32_t item = w * 64 + (uint32_t)__builtin_ctzll(y);
+          ((hc[q] >> t) & 1u ? rules[q].x : rules[q].y).push_back(item);
+        }
+      rules[q].sz = support[hz[q]];
+      rules[q].sx = hs[q];
+    }
+    std::sort(rules.begin(), rules.end(), [](const Rule &a, const Rule &b) {
+      if (a.x.size() != b.x.size()) return a.x.size() < b.x.size();
+      if (a.x != b.x) return a.x < b.x;
+      if (a.y.size() != b.y.size()) return a.y.size() < b.y.size();
+      return a.y < b.y;
+    });
+    r->ante.assign(nrules * W, 0);
+    r->cons.assign(nrules * W, 0);
+    r->supp.resize(nrules);
+    r->supp_ante.resize(nrules);
+    for (uint64_t q = 0; q < nrules; ++q) {
+      for (uint32_t it : rules[q].x) r->ante[q * W + it / 64] |= 1ull << (it % 64);
+      for (uint32_t it : rules[q].y) r->cons[q * W + it / 64] |= 1ull << (it % 64);
+      r->supp[q] = rules[q].sz;
+      r->supp_ante[q] = rules[q].sx;
+    }
+  } while (false);
+  d_masks.release(); d_k.release(); d_supp.release(); d_prefix.release(); d_hslot.release();
+  d_cursor.release(); d_z.release(); d_code.release(); d_sx.release(); d_err.release();
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (st != DIC_OK) return st;
+  *out = r.release();
+  return DIC_OK;
+}
+
+extern "C" uint64_t dic_rules_count(const dic_rules *r) { return r ? r->supp.size() : 0; }
+
+extern "C" dic_status dic_rules_copy(const dic_rules *r, uint64_t *antecedent,
+                                     uint64_t *consequent, uint32_t *support,
+                                     uint32_t *antecedent_support) {
+  if (!r) return fail(DIC_EINVAL, "rules is NULL");
+  if (antecedent) std::memcpy(antecedent, r->ante.data(), r->ante.size() * 8);
+  if (consequent) std::memcpy(consequent, r->cons.data(), r->cons.size() * 8);
+  if (support) std::memcpy(support, r->supp.data(), r->supp.size() * 4);
+  if (antecedent_support)
+    std::memcpy(antecedent_support, r->supp_ante.data(), r->supp_ante.size() * 4);
+  return DIC_OK;
+}
+
+extern "C" void dic_rules_free(dic_rules *r) { delete r; }
+
 // -------------------------------------------------------------------- misc
 extern "C" uint32_t dic_minsup_count(uint64_t n, double frac) {
   if (!(frac > 0)) return 1;

@@ -242,6 +242,16 @@ cudaError_t launch_gram_pairs(Lattice L, uint32_t nsplit, uint32_t kre, cudaStre
 // PRUNE for the pair cohort counted by the tensor path (one thread per record).
 cudaError_t launch_settle_pairs(Lattice L, int grid, uint32_t kre, cudaStream_t s);
 
+// Association rules (kernels_rules.cu): insert the itemsets into a table,
+// then evaluate every split of every itemset of >= 2 items; rules go to
+// out_* at an atomic cursor; err bit 0 = an itemset's subset is missing,
+// bit 1 = table full.
+cudaError_t launch_rules(const uint64_t *masks, const uint32_t *k, const uint32_t *supp,
+                         const uint64_t *work_prefix, uint32_t *hslot, uint64_t count,
+                         uint32_t W, uint32_t hcap, uint32_t num, uint32_t den, uint64_t total,
+                         unsigned long long *cursor, uint32_t *out_z, uint32_t *out_code,
+                         uint32_t *out_sx, uint32_t *err, cudaStream_t s);
+
 // Largest candidate chunk whose bitslice shared-memory footprint fits.
 uint32_t bitslice_max_chunk(int tw, int kre, uint32_t l1p, size_t smem_limit);
 size_t bitslice_smem(int tw, int kre, uint32_t l1p, uint32_t chunk);

@@ -99,6 +99,10 @@ def _load():
         "dic_server_wait": ([vp, u64, ctypes.c_int64, pvp], i32),
         "dic_server_stats": ([vp, ctypes.POINTER(ServerMetrics)], i32),
         "dic_server_destroy": ([vp], i32),
+        "dic_rules_from_itemsets": ([vp, vp, vp, u64, u32, u32, u32, pvp], i32),
+        "dic_rules_count": ([vp], u64),
+        "dic_rules_copy": ([vp, vp, vp, vp, vp], i32),
+        "dic_rules_free": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -301,6 +305,39 @@ def mine_batch(dbs, minsups, Ms, path: str = "auto", profile=False, tile_words: 
                                Ms_.ctypes.data, cnt, ctypes.byref(o),
                                ctypes.cast(outs, ctypes.c_void_p)))
     return [_result(ctypes.c_void_p(outs[i])) for i in range(cnt)]
+
+
+def _items_of(mask_row) -> tuple:
+    return tuple(int(w * 64 + b) for w, x in enumerate(mask_row) for b in range(64)
+                 if (int(x) >> b) & 1)
+
+
+def rules(res: Result, conf_num: int, conf_den: int, m: int | None = None) -> list:
+    """Association rules X -> Z \\ X of the mined itemsets with confidence
+    supp(Z) / supp(X) >= conf_num / conf_den (exact), evaluated on the GPU.
+    Returns [(X, Z \\ X, supp(Z), supp(X))] in canonical order."""
+    W = res.W
+    masks = np.ascontiguousarray(res.masks, dtype=np.uint64).reshape(-1)
+    k = np.ascontiguousarray(res.k, dtype=np.uint32)
+    sp = np.ascontiguousarray(res.support, dtype=np.uint32)
+    cnt = len(k)
+    h = ctypes.c_void_p()
+    _check(_lib.dic_rules_from_itemsets(masks.ctypes.data if cnt else None,
+                                        k.ctypes.data if cnt else None,
+                                        sp.ctypes.data if cnt else None, cnt,
+                                        m if m is not None else W * 64, conf_num, conf_den,
+                                        ctypes.byref(h)))
+    try:
+        nr = _lib.dic_rules_count(h)
+        ante = np.zeros((max(nr, 1), W), dtype=np.uint64)
+        cons = np.zeros((max(nr, 1), W), dtype=np.uint64)
+        sz = np.zeros(max(nr, 1), dtype=np.uint32)
+        sx = np.zeros(max(nr, 1), dtype=np.uint32)
+        _check(_lib.dic_rules_copy(h, ante.ctypes.data, cons.ctypes.data, sz.ctypes.data,
+                                   sx.ctypes.data))
+    finally:
+        _lib.dic_rules_free(h)
+    return [(_items_of(ante[i]), _items_of(cons[i]), int(sz[i]), int(sx[i])) for i in range(nr)]
 
 
 def minsup_count(n: int, frac: float) -> int:
