@@ -87,7 +87,8 @@ def ncu_traffic(kernel: str):
     return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
 
 
-def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=None):
+def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=None,
+                alu_peak=None):
     """Roofline object of the kernel kind `kind` from the profiled timed steps."""
     pk = peaks()
     tot_ms = sum(s[kind + "_ms"] for s in stats)
@@ -114,10 +115,12 @@ def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=No
         kern = COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])]
         if kern != "k_count_rows" and count_form == "tiled":
             kern = "k_count_bitslice"
-        return dict(bound="alu", achieved=ach, peak=ALU_PEAK_TOPS, unit="Top/s",
-                    frac=ach / ALU_PEAK_TOPS, traffic=ncu_traffic(kern), kernel=kern,
-                    peak_source="derived: 152 SM x 64 INT32 lanes x 2070 MHz",
-                    ops_per_launch=ops, **common)
+        peak = alu_peak if alu_peak else ALU_PEAK_TOPS
+        src = ("measured in this run: lop3.b32 issue rate (dic_measure_alu_peak)" if alu_peak
+               else "derived: 152 SM x 64 INT32 lanes x 2070 MHz")
+        return dict(bound="alu", achieved=ach, peak=peak, unit="Top/s", frac=ach / peak,
+                    traffic=ncu_traffic(kern), kernel=kern, peak_source=src,
+                    derived_peak=ALU_PEAK_TOPS, ops_per_launch=ops, **common)
     # gen / settle: latency-bound memory-side kernels; algorithmic bytes per launch
     wc, l1 = st["words_compact"], st["l1"]
     if kind == "gen":
@@ -553,8 +556,12 @@ def main():
 
     # ---- roofline of the dominant kernel kind, timed live with CUDA events
     # on the mining stream around each of its launches in the timed steps
+    try:
+        alu_peak = dic.dic.measure_alu_peak()
+    except Exception:  # noqa: BLE001 (the derived peak is used instead)
+        alu_peak = None
     roofline = roofline_of(kind, stats, shares_ms, sum(ms), db, kw.get("count_form", "auto"),
-                           res.trace)
+                           res.trace, alu_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

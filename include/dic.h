@@ -293,6 +293,14 @@ dic_status dic_rules_copy(const dic_rules *r, uint64_t *antecedent, uint64_t *co
                           uint32_t *support, uint32_t *antecedent_support);
 void dic_rules_free(dic_rules *r);
 
+/* ------------------------------------------------------ measurement aid */
+
+/* Integer-ALU issue rate of the current device, in tera ops per second:
+ * eight independent chains of lop3.b32 per thread on every SM for a few ms,
+ * timed with CUDA events (the denominator of the BITSLICE count's roofline).
+ * No counterpart in the paper. DIC_EINVAL for NULL; DIC_ECUDA on failure. */
+dic_status dic_measure_alu_peak(double *tera_ops_per_s);
+
 /* ------------------------------------------------ allocation-free count */
 
 /* Size of the scratch array of dic_count_support_noalloc, in 32-bit words

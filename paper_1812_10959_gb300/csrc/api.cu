@@ -2018,6 +2018,18 @@ extern "C" dic_status dic_rules_copy(const dic_rules *r, uint64_t *antecedent,
 extern "C" void dic_rules_free(dic_rules *r) { delete r; }
 
 // -------------------------------------------------------------------- misc
+namespace dic {
+cudaError_t measure_alu_peak(double *tops);
+}
+
+extern "C" dic_status dic_measure_alu_peak(double *tera_ops_per_s) {
+  if (!tera_ops_per_s) return fail(DIC_EINVAL, "out is NULL");
+  *tera_ops_per_s = 0;
+  cudaError_t e = dic::measure_alu_peak(tera_ops_per_s);
+  if (e != cudaSuccess) return fail(DIC_ECUDA, "ALU peak: %s", cudaGetErrorString(e));
+  return DIC_OK;
+}
+
 extern "C" uint32_t dic_minsup_count(uint64_t n, double frac) {
   if (!(frac > 0)) return 1;
   double v = std::ceil(frac * (double)n - 1e-9);

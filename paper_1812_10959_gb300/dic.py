@@ -103,6 +103,7 @@ def _load():
         "dic_rules_count": ([vp], u64),
         "dic_rules_copy": ([vp, vp, vp, vp, vp], i32),
         "dic_rules_free": ([vp], None),
+        "dic_measure_alu_peak": ([ctypes.POINTER(ctypes.c_double)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -338,6 +339,13 @@ def rules(res: Result, conf_num: int, conf_den: int, m: int | None = None) -> li
     finally:
         _lib.dic_rules_free(h)
     return [(_items_of(ante[i]), _items_of(cons[i]), int(sz[i]), int(sx[i])) for i in range(nr)]
+
+
+def measure_alu_peak() -> float:
+    """Measured integer-ALU (lop3) issue rate of the current device, Top/s."""
+    v = ctypes.c_double(0.0)
+    _check(_lib.dic_measure_alu_peak(ctypes.byref(v)))
+    return v.value
 
 
 def minsup_count(n: int, frac: float) -> int:
