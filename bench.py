@@ -9,6 +9,12 @@ The L2 cache is flushed (a 512 MiB write) before every timed step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The count configuration is the autotuner's choice for the query (timed on it,
+every candidate checked to give the same result); `--path` forces one,
+`--no-tune` keeps the library's rule, `--algorithm classic` runs Algorithm 1.
+Other workloads: `--workload dense|batched|served|planted-small`; `--sweep`
+times both algorithms over block sizes and thresholds (one JSON line).
+
 `--impl reference` times the CPU oracle (the plain serial restatement of the
 paper's algorithm) on the host cores instead, on a bounded sample of the same
 workload. With N > 1 (torchrun) every rank mines its own replica; the value is
