@@ -72,3 +72,39 @@ def test_host_side_validation_without_gpu(libpath):
     assert lib.dic_load_db(None, 1 << 31, 4, ctypes.byref(h)) == dic.dic.DIC_EINVAL
     # mining arguments
     assert lib.dic_mine(None, 1, 1, ctypes.byref(h)) == dic.dic.DIC_EINVAL
+
+
+def test_options_defaults_and_rules_validation_without_gpu(libpath):
+    import paper_1812_10959_gb300 as dic
+    d = dic.dic
+    o = d.Options()
+    d.lib().dic_options_init(ctypes.byref(o))
+    assert o.struct_size == ctypes.sizeof(d.Options)
+    assert (o.count_path, o.use_graph, o.profile, o.tile_words, o.count_form, o.algorithm) == \
+        (0, 1, 0, 0, 0, 0)
+    # the rules entry point checks its arguments on the host, before any CUDA call
+    W = 1
+    masks = np.array([[0b11]], dtype=np.uint64)
+    res = d.Result(W, masks, np.array([3], dtype=np.uint32), np.array([5], dtype=np.uint32),
+                   np.zeros((0, 9), dtype=np.uint64), {})
+    with pytest.raises(d.DicError) as e:
+        d.rules(res, 1, 2, m=2)            # size 3 is not the popcount 2
+    assert e.value.status == d.DIC_EINVAL
+    with pytest.raises(d.DicError) as e:
+        d.rules(res, 1, 0, m=2)            # zero denominator
+    assert e.value.status == d.DIC_EINVAL
+    wide = d.Result(W, np.array([[1 << 40]], dtype=np.uint64), np.array([1], dtype=np.uint32),
+                    np.array([5], dtype=np.uint32), np.zeros((0, 9), dtype=np.uint64), {})
+    with pytest.raises(d.DicError) as e:
+        d.rules(wide, 1, 2, m=10)          # item 40 >= m
+    assert e.value.status == d.DIC_EINVAL
+    big = d.Result(W, np.array([[(1 << 32) - 1]], dtype=np.uint64),
+                   np.array([32], dtype=np.uint32), np.array([5], dtype=np.uint32),
+                   np.zeros((0, 9), dtype=np.uint64), {})
+    with pytest.raises(d.DicError) as e:
+        d.rules(big, 1, 2, m=64)           # more than 31 items in one itemset
+    assert e.value.status == d.DIC_ECAPACITY
+    # no itemset of two or more items: no rules and no device work
+    single = d.Result(W, np.array([[1], [2]], dtype=np.uint64), np.array([1, 1], dtype=np.uint32),
+                      np.array([5, 4], dtype=np.uint32), np.zeros((0, 9), dtype=np.uint64), {})
+    assert d.rules(single, 1, 2, m=2) == []
