@@ -158,15 +158,25 @@ extern "C" dic_status dic_count_support_noalloc(const uint64_t *dev_words, uint6
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms <= 0) sms = 1;
+  // each launch's own status (cudaLaunchKernelEx), so an error left over
+  // from unrelated earlier work is neither reported here nor cleared
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
   for (uint64_t r0 = 0; r0 < n; r0 += slab) {
     const uint32_t nrows = (uint32_t)(n - r0 < slab ? n - r0 : slab);
     const uint64_t sitems = (uint64_t)((nrows + 31) / 32) * W;
     int g1 = (int)((sitems + 7) / 8 < (uint64_t)sms * 8 ? (sitems + 7) / 8 : (uint64_t)sms * 8);
-    k_noalloc_slice<<<g1 > 0 ? g1 : 1, 256, 0, s>>>(dev_words, W, m, r0, nrows, cols, vw);
+    cfg.gridDim = dim3(g1 > 0 ? g1 : 1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_noalloc_slice, dev_words, W, m, r0, nrows, cols, vw);
+    if (e != cudaSuccess)
+      return noalloc_fail(DIC_ECUDA, "dic_count_support_noalloc: slice launch failed");
     int g2 = (int)((ncand + 255) / 256 < (uint32_t)sms * 8 ? (ncand + 255) / 256 : sms * 8);
-    k_noalloc_count<<<g2, 256, 0, s>>>(dev_masks, ncand, W, m, cols, vw, nrows, dev_supp);
+    cfg.gridDim = dim3(g2);
+    e = cudaLaunchKernelEx(&cfg, k_noalloc_count, dev_masks, ncand, W, m,
+                           (const uint32_t *)cols, vw, nrows, dev_supp);
+    if (e != cudaSuccess)
+      return noalloc_fail(DIC_ECUDA, "dic_count_support_noalloc: count launch failed");
   }
-  if (cudaGetLastError() != cudaSuccess)
-    return noalloc_fail(DIC_ECUDA, "dic_count_support_noalloc: kernel launch failed");
   return DIC_OK;
 }

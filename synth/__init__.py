@@ -174,13 +174,9 @@ def dense_zipf(seed: int = 2, n: int = 200_000) -> Database:
 BATCH_M_CHOICES = (64, 128, 256, 512, 1024)
 
 
-def batched_db(index: int, base_seed: int = 1000, n_lo: int = 1_000, n_hi: int = 200_000) -> Database:
-    """The index-th database of the batched recipe: n log-uniform in
-    [n_lo, n_hi], m uniform from {64,...,1024}, mean row length U(5,40)
-    capped at m/16 (rows at most 6.25% dense, so that two independent items
-    are not frequent together even at 0.5% support; uncapped, a 64-item
-    database with 40-item rows has ~10^11 frequent itemsets), mean pattern
-    length U(2,8), pool of 2m patterns, minsup U(0.5%,5%) of n, M = n/10."""
+def batched_params(index: int, base_seed: int = 1000, n_lo: int = 1_000, n_hi: int = 200_000):
+    """(seed, n, m, mean row length, mean pattern length, minsup fraction) of
+    the index-th database of the batched recipe, without drawing its rows."""
     s = base_seed + index
     u = [uniform(s, 0, k) for k in range(5)]
     n = int(round(math.exp(math.log(n_lo) + u[0] * (math.log(n_hi) - math.log(n_lo)))))
@@ -188,6 +184,17 @@ def batched_db(index: int, base_seed: int = 1000, n_lo: int = 1_000, n_hi: int =
     tx_len = min(5.0 + 35.0 * u[2], m / 16.0)
     pat_len = 2.0 + 6.0 * u[3]
     frac = 0.005 + 0.045 * u[4]
+    return s, n, m, tx_len, pat_len, frac
+
+
+def batched_db(index: int, base_seed: int = 1000, n_lo: int = 1_000, n_hi: int = 200_000) -> Database:
+    """The index-th database of the batched recipe: n log-uniform in
+    [n_lo, n_hi], m uniform from {64,...,1024}, mean row length U(5,40)
+    capped at m/16 (rows at most 6.25% dense, so that two independent items
+    are not frequent together even at 0.5% support; uncapped, a 64-item
+    database with 40-item rows has ~10^11 frequent itemsets), mean pattern
+    length U(2,8), pool of 2m patterns, minsup U(0.5%,5%) of n, M = n/10."""
+    s, n, m, tx_len, pat_len, frac = batched_params(index, base_seed, n_lo, n_hi)
     rp, it = planted(s, n, m, 2 * m, pat_len, tx_len)
     return Database(f"batched#{index} n={n} m={m}", n, m, rp, it, minsup_count(n, frac),
                     max(1, n // 10), dict(seed=s, tx_len=tx_len, pat_len=pat_len, frac=frac))
