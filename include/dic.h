@@ -109,7 +109,16 @@ typedef struct {
                                starts in Dashed Circle, no first pass;
                                single queries only, DIC_EINVAL in batches
                                and the server). Same result either way.   */
-  uint32_t reserved[6];
+  uint32_t prestage;        /* 0 = before the stop loop, transpose every
+                               block's bit columns and (TENSOR) count the
+                               pair cohort over every block in one GEMM,
+                               precomputing its promotions and prunes per
+                               stop, when they fit a quarter of the free
+                               device memory (at most 16 GiB); 1 = transpose
+                               each stop's block and count the pairs per
+                               stop. Single queries only; same result.
+                               Other values: DIC_EINVAL                    */
+  uint32_t reserved[5];
 } dic_options;
 
 /* Per-run statistics (dic_result_stats). */

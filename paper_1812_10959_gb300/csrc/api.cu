@@ -45,6 +45,11 @@ static dic_status fail(dic_status s, const char *fmt, ...) {
 
 void dic::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
+bool &dic::pdl_enabled() {
+  static thread_local bool on = false;
+  return on;
+}
+
 #define CU(call)                                                                        \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \
@@ -322,6 +327,8 @@ class Miner {
     if (ev_join_) { cudaEventDestroy(ev_join_); ev_join_ = nullptr; }
     if (s2_) { cudaStreamDestroy(s2_); s2_ = nullptr; }
     if (ev_slice_) { cudaEventDestroy(ev_slice_); ev_slice_ = nullptr; }
+    if (eg0_) { cudaEventDestroy(eg0_); eg0_ = nullptr; }
+    if (eg1_) { cudaEventDestroy(eg1_); eg1_ = nullptr; }
     if (s3_) { cudaStreamDestroy(s3_); s3_ = nullptr; }
   }
 
@@ -418,7 +425,30 @@ class Miner {
   Ctrl *ext_ctrl_ = nullptr;
   bool own_h_ctrl_ = false;
   int forced_tw_ = 0;
+  // every block's columns staged before the loop (L_.vall), the pair cohort
+  // counted over the whole pass with precomputed events (L_.pair_events),
+  // and the stop kernels chained by programmatic dependent launch
+  bool vall_ = false, events_ = false, pc_wide_ = false, pdl_ = false;
+  int32_t *d_rank_ = nullptr;  // rank of each item (-1: not frequent)
+  bool rows_ready_ = false;    // L_.rows (compacted rows) built
+  cudaEvent_t eg0_ = nullptr, eg1_ = nullptr;  // the all-blocks GEMM, profiled
+  dic_status ensure_rows();
 };
+
+// Compacted rows (only the frequent items, by rank) for the kernels that
+// read rows: the ROWS count and the per-stop transposition.
+dic_status Miner::ensure_rows() {
+  if (rows_ready_) return DIC_OK;
+  const uint32_t wc = std::max<uint32_t>(1, ((uint32_t)l1items_.size() + 63) / 64);
+  uint64_t *d_rows = nullptr;
+  TRY(alloc(&d_rows, (size_t)n_ * wc));
+  CU(launch_compact_rows(db_->words, n_, db_->W, d_rank_, d_rows, wc, s_));
+  ++launches_;
+  L_.rows = d_rows;
+  rows_ready_ = true;
+  ++lat_version_;
+  return DIC_OK;
+}
 
 // Count path for the next stops: BITSLICE whenever the block's columns fit in
 // shared memory and every dashed itemset has at most KRMAX items, else ROWS.
@@ -507,12 +537,13 @@ dic_status Miner::launch_phase(int phase) {
         const int kre = kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4));
         const uint32_t chunk = std::min<uint32_t>(
             bitslice_max_chunk(bs_tw_, kre, bs_l1p_, smem_optin_), 1u << 20);
-        if (!next_v_ready_) {
+        if (!next_v_ready_ && !L_.vall) {
           e = launch_slice_block(L_, 0, s_);
           ++launches_;
         }
         next_v_ready_ = false;
-        const bool gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
+        const bool gram =
+            cur_path_ == DIC_COUNT_TENSOR && !L_.pair_events && pred_step_ <= L_.stop_max;
         if (e == cudaSuccess && (gram || L_.vdouble)) CU(cudaEventRecord(ev_fork_, s_));
         if (e == cudaSuccess && L_.vdouble) {
           // fork: the next stop's block is transposed into the other column
@@ -563,8 +594,8 @@ dic_status Miner::launch_phase(int phase) {
     case PH_GEN: {
       const bool fast = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
       if (prof(DIC_PROFILE_GEN)) TRY(iv_open(IV_GEN, s_));
-      // (with double-buffered columns the next block is already transposed)
-      e = launch_generate_finish(L_, grid_, fast && !L_.vdouble, s_);
+      // (with double-buffered or staged columns the next block is ready)
+      e = launch_generate_finish(L_, grid_, fast && !L_.vdouble && !L_.vall, s_);
       if (prof(DIC_PROFILE_GEN)) TRY(iv_close(s_));
       next_v_ready_ = fast;
       ++pred_step_;
@@ -581,6 +612,11 @@ dic_status Miner::launch_phase(int phase) {
 // box-set insert as kernels of their own; the BITSLICE count kernel applies
 // both in its epilogue.
 dic_status Miner::launch_stop_from(int phase) {
+  struct PdlScope {  // the stop's kernels chained by programmatic launch
+    bool prev;
+    explicit PdlScope(bool on) : prev(pdl_enabled()) { pdl_enabled() = on; }
+    ~PdlScope() { pdl_enabled() = prev; }
+  } scope(pdl_);
   for (int p = phase; p <= PH_GEN; ++p) {
     if (cur_path_ != DIC_COUNT_ROWS && (p == PH_PROMOTE || p == PH_HASH)) continue;
     TRY(launch_phase(p));
@@ -741,19 +777,56 @@ dic_status Miner::prepare() {
       return fail(DIC_ECAPACITY, "%llu candidate pairs exceed the candidate limit",
                   (unsigned long long)npairs);
     if (stop_max64 > 0x7FFFFFFFull) return fail(DIC_EINVAL, "too many blocks");
-    // ---- column compaction to the l1 frequent items (ranks)
+    // ---- ranks of the frequent items
     std::vector<int32_t> rank_of((size_t)W * 64, -1);
     for (uint32_t r = 0; r < l1; ++r) rank_of[l1items[r]] = (int32_t)r;
-    int32_t *d_rank = nullptr;
-    TRY(alloc(&d_rank, rank_of.size()));
-    CU(cudaMemcpyAsync(d_rank, rank_of.data(), rank_of.size() * 4, cudaMemcpyHostToDevice, s_));
-    uint64_t *d_rows = nullptr;
-    TRY(alloc(&d_rows, (size_t)n * wc));
-    CU(launch_compact_rows(db_->words, n, W, d_rank, d_rows, wc, s_));
-    ++launches_;
+    TRY(alloc(&d_rank_, rank_of.size()));
+    CU(cudaMemcpyAsync(d_rank_, rank_of.data(), rank_of.size() * 4, cudaMemcpyHostToDevice, s_));
+
+    // ---- BITSLICE tiles: widest tile whose double buffer leaves room for
+    // a useful candidate chunk in shared memory
+    {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      smem_optin_ = (size_t)optin;
+      bs_l1p_ = (l1 + 3) & ~3u;
+      bs_ok_ = false;
+      if (l1 <= 65535 && opt_.count_path != DIC_COUNT_ROWS) {
+        for (int tw : {16, 8, 4}) {
+          if (forced_tw_ && tw != forced_tw_) continue;
+          if (bitslice_max_chunk(tw, 16, bs_l1p_, smem_optin_) >= 1024) {
+            bs_tw_ = tw;
+            bs_ok_ = true;
+            break;
+          }
+        }
+      }
+    }
+    const uint64_t blockmax = std::min<uint64_t>(M_, n);
+    if (bs_ok_) {
+      const uint64_t ntiles = ((blockmax + 31) / 32 + bs_tw_ - 1) / bs_tw_;
+      bs_V_words_ = (uint64_t)ntiles * bitslice_tile_words(bs_tw_, bs_l1p_);
+    }
+    // Every block's columns are transposed once, before the loop, when this
+    // query runs its own loop and they fit the memory rule (a quarter of the
+    // free device memory, at most 16 GiB); otherwise the loop transposes
+    // each stop's block (double-buffered, one stop ahead).
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const uint64_t stage_cap = std::min<uint64_t>(free_b / 4, 16ull << 30);
+    vall_ = false;
+    if (bs_ok_ && vdouble_ && opt_.prestage == 0 &&
+        stop_max64 * bs_V_words_ * 4 <= stage_cap)
+      vall_ = true;
+
+    // ---- compacted rows: the ROWS path and the per-stop transposition
+    // read them; with every block staged they are built only if the loop
+    // falls back to ROWS (itemsets beyond KRMAX items)
+    rows_ready_ = false;
+    if (!vall_) TRY(ensure_rows());
 
     // ---- lattice buffers
-    L_.rows = d_rows;
     L_.n = n;
     L_.M = M_;
     L_.stop_max = (uint32_t)stop_max64;
@@ -791,6 +864,37 @@ dic_status Miner::prepare() {
     c.n_cohorts = 1;
     c.max_k = classic ? 1 : 2;
     c.tests = tests_;
+    // ---- TENSOR path for the pair cohort: needs the BITSLICE path for the
+    // rest, a block below 2^24 rows (exact fp32 sums), and enough pairs to
+    // fill a tile (AUTO) or an explicit request. With every block staged and
+    // room for the per-block counts, the pairs are counted over the whole
+    // pass by one GEMM before the loop and their promotions and prunes are
+    // precomputed per stop (pair events); otherwise a GEMM per stop runs
+    // beside the BITSLICE count.
+    const bool want_tc = !classic && (opt_.count_path == DIC_COUNT_TENSOR ||
+                                      (opt_.count_path == DIC_COUNT_AUTO && l1 >= 256 &&
+                                       blockmax >= 2048));
+    tc_ok_ = false;
+    events_ = false;
+    if (want_tc && bs_ok_ && blockmax < (1ull << 24) && npairs <= 0xFFFFFFF0ull) {
+      tc_ok_ = true;
+      L_.pair_end = (uint32_t)npairs;
+      pc_wide_ = blockmax > 65535;
+      const uint64_t pc_bytes = stop_max64 * npairs * (pc_wide_ ? 4 : 2);
+      if (vall_ && pc_bytes <= stage_cap && stop_max64 * gram_tile_pairs(l1) <= 0x7FFFFFFFull) {
+        events_ = true;
+        c.gram_rows = n;  // every row of the pass, counted once for the pairs
+      } else {
+        tc_nkc_max_ = gram_chunks(blockmax);
+        const uint32_t ntp = gram_tile_pairs(l1);
+        const uint32_t sms = (uint32_t)sm_count();
+        // one CTA per SM (the rings take 192 KiB): a single wave of splits
+        tc_nsplit_ = std::max<uint32_t>(1, std::min<uint32_t>(tc_nkc_max_, sms / ntp));
+        if (!s2_) CU(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
+        if (!ev_fork_) CU(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+        if (!ev_join_) CU(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
+      }
+    }
     *h_ctrl_ = c;
     CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
     if (classic)
@@ -800,65 +904,58 @@ dic_status Miner::prepare() {
     ++launches_;
     nw_ = (uint32_t)rows_width_bucket(c.max_k, wc);
 
-    // ---- BITSLICE tiles: widest tile whose double buffer leaves room for
-    // a useful candidate chunk in shared memory
-    {
-      int dev = 0, optin = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      smem_optin_ = (size_t)optin;
-      bs_l1p_ = (l1 + 3) & ~3u;
-      bs_ok_ = false;
-      if (l1 <= 65535 && opt_.count_path != DIC_COUNT_ROWS) {
-        for (int tw : {16, 8, 4}) {
-          if (forced_tw_ && tw != forced_tw_) continue;
-          if (bitslice_max_chunk(tw, 16, bs_l1p_, smem_optin_) >= 1024) {
-            bs_tw_ = tw;
-            bs_ok_ = true;
-            break;
-          }
-        }
-      }
-      if (bs_ok_) {
-        const uint64_t blockmax = std::min<uint64_t>(M_, n);
-        const uint64_t ntiles = ((blockmax + 31) / 32 + bs_tw_ - 1) / bs_tw_;
-        bs_V_words_ = (uint64_t)ntiles * bitslice_tile_words(bs_tw_, bs_l1p_);
-        TRY(alloc(&bs_V_, bs_V_words_ * (vdouble_ ? 2 : 1)));
-        L_.V = bs_V_;
-        L_.vwords = bs_V_words_;
-        L_.vdouble = vdouble_ ? 1u : 0u;
-        if (vdouble_) {
-          if (!s3_) CU(cudaStreamCreateWithFlags(&s3_, cudaStreamNonBlocking));
-          if (!ev_slice_) CU(cudaEventCreateWithFlags(&ev_slice_, cudaEventDisableTiming));
-          if (!ev_fork_) CU(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
-        }
-        L_.tw = (uint32_t)bs_tw_;
-        L_.l1p = bs_l1p_;
-        bs_grid_ = sm_count();
-      }
-    }
-    // ---- TENSOR path for the pair cohort: needs the BITSLICE path for the
-    // rest, a block below 2^24 rows (exact fp32 sums), and enough pairs to
-    // fill a tile (AUTO) or an explicit request
-    {
-      const uint64_t blockmax = std::min<uint64_t>(M_, n);
-      const bool want = !classic && (opt_.count_path == DIC_COUNT_TENSOR ||
-                                     (opt_.count_path == DIC_COUNT_AUTO && l1 >= 256 &&
-                                      blockmax >= 2048));
-      tc_ok_ = false;
-      if (want && bs_ok_ && blockmax < (1ull << 24) && npairs <= 0xFFFFFFF0ull) {
-        tc_nkc_max_ = gram_chunks(blockmax);
-        const uint32_t ntp = gram_tile_pairs(l1);
-        const uint32_t sms = (uint32_t)sm_count();
-        // one CTA per SM (the rings take 192 KiB): a single wave of splits
-        tc_nsplit_ = std::max<uint32_t>(1, std::min<uint32_t>(tc_nkc_max_, sms / ntp));
-        if (!s2_) CU(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
+    // ---- BITSLICE column buffers: every block of the pass (staged), or two
+    // blocks (this stop's and the next) / one block (batched forms)
+    if (bs_ok_) {
+      const uint64_t nbuf = vall_ ? stop_max64 : (vdouble_ ? 2 : 1);
+      TRY(alloc(&bs_V_, bs_V_words_ * nbuf));
+      L_.V = bs_V_;
+      L_.vwords = bs_V_words_;
+      L_.vall = vall_ ? 1u : 0u;
+      L_.vdouble = (vdouble_ && !vall_) ? 1u : 0u;
+      if (L_.vdouble) {
+        if (!s3_) CU(cudaStreamCreateWithFlags(&s3_, cudaStreamNonBlocking));
+        if (!ev_slice_) CU(cudaEventCreateWithFlags(&ev_slice_, cudaEventDisableTiming));
         if (!ev_fork_) CU(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
-        if (!ev_join_) CU(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
-        L_.pair_end = (uint32_t)npairs;
-        tc_ok_ = true;
+      }
+      L_.tw = (uint32_t)bs_tw_;
+      L_.l1p = bs_l1p_;
+      bs_grid_ = sm_count();
+      if (vall_) {
+        CU(launch_slice_all(L_, db_->words, W, d_rank_, s_));
+        ++launches_;
       }
     }
+    // ---- the pair cohort over every block at once, and its events
+    if (events_) {
+      void *pc = nullptr;
+      uint32_t *ev = nullptr, *hist = nullptr, *cursor = nullptr;
+      uint32_t *ev_off = nullptr, *ev_list = nullptr, *ev_pruned = nullptr;
+      const uint64_t S = stop_max64;
+      TRY(alloc((uint8_t **)&pc, (size_t)S * npairs * (pc_wide_ ? 4 : 2)));
+      TRY(alloc(&ev, npairs));
+      TRY(alloc(&hist, 2 * (S + 2)));
+      TRY(alloc(&cursor, S + 2));
+      TRY(alloc(&ev_off, S + 2));
+      TRY(alloc(&ev_list, npairs));
+      TRY(alloc(&ev_pruned, S + 1));
+      if (opt_.profile & DIC_PROFILE_GRAM) {
+        if (!eg0_) CU(cudaEventCreate(&eg0_));
+        if (!eg1_) CU(cudaEventCreate(&eg1_));
+        CU(cudaEventRecord(eg0_, s_));
+      }
+      CU(launch_gram_all_blocks(L_, pc, pc_wide_, s_));
+      if (opt_.profile & DIC_PROFILE_GRAM) CU(cudaEventRecord(eg1_, s_));
+      CU(launch_pair_events(L_, pc, pc_wide_, ev, hist, ev_off, cursor, ev_list, ev_pruned, s_));
+      launches_ += 4;
+      path_launches_[DIC_COUNT_TENSOR]++;
+      drop((uint8_t *)pc); drop(ev); drop(hist); drop(cursor);
+      L_.pair_events = 1;
+      L_.ev_off = ev_off;
+      L_.ev_list = ev_list;
+      L_.ev_pruned = ev_pruned;
+    }
+    pdl_ = vall_;  // one stream per stop: kernels chained by programmatic launch
 
     has_loop_ = true;
   }
@@ -910,6 +1007,7 @@ dic_status Miner::recover() {
     int b = rows_width_bucket(h_ctrl_->max_k, wc);
     nw_ = b ? (uint32_t)b : 0;
     cur_path_ = count_path_for_stop();
+    if (cur_path_ == DIC_COUNT_ROWS) TRY(ensure_rows());
   }
   while (h_ctrl_->stall) {
     const uint32_t st = h_ctrl_->stall;
@@ -918,6 +1016,7 @@ dic_status Miner::recover() {
       int b = rows_width_bucket(h_ctrl_->max_k, wc);
       nw_ = b ? (uint32_t)b : 0;
       cur_path_ = count_path_for_stop();
+      if (cur_path_ == DIC_COUNT_ROWS) TRY(ensure_rows());
       phase = PH_COUNT;
     } else if (st == ST_HASH || st == ST_HASH_COUNT) {
       TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live + h_ctrl_->n_newbox));
@@ -948,8 +1047,8 @@ dic_status Miner::launch_stop() {
   const bool fast = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
   StopGraph key;
   key.path = cur_path_;
-  key.gram = cur_path_ == DIC_COUNT_TENSOR && pred_step_ <= L_.stop_max;
-  key.slice = fast && !next_v_ready_;
+  key.gram = cur_path_ == DIC_COUNT_TENSOR && !L_.pair_events && pred_step_ <= L_.stop_max;
+  key.slice = fast && !next_v_ready_ && !L_.vall;
   key.kre = fast ? kr_bucket(std::max<uint32_t>(h_ctrl_->max_k, 4)) : 0;
   key.direct = fast && direct_;
   key.nw = cur_path_ == DIC_COUNT_ROWS ? nw_ : 0;
@@ -1059,12 +1158,14 @@ dic_status Miner::loop() {
     int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
     nw_ = bucket ? (uint32_t)bucket : 0;
     cur_path_ = count_path_for_stop();
+    if (cur_path_ == DIC_COUNT_ROWS) TRY(ensure_rows());
     pred_step_ = h_ctrl_->step;
     {
       // the window the BITSLICE kernel counts (the pair cohort aside while
       // the tensor path has it); small ones take the direct form
       const Ctrl &c = *h_ctrl_;
       const uint32_t skip = (L_.pair_end && c.step <= L_.stop_max) ? L_.pair_end : 0u;
+      // (pair_end is set whenever the tensor path has the pair cohort)
       const uint32_t lo = skip > c.head ? std::min(skip, c.tail) : c.head;
       direct_ = opt_.count_form == 2 ||
                 (opt_.count_form == 0 && c.tail - lo <= BS_DIRECT_HOST_MAX);
@@ -1154,6 +1255,13 @@ dic_status Miner::collect(dic_result **out) {
   res->stats.frequent = order.size();
   res->stats.kernel_launches = launches_;
   for (int i = 0; i < 4; ++i) res->stats.path_launches[i] = path_launches_[i];
+  if (eg0_ && eg1_) {  // the all-blocks pair GEMM (once per mine)
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, eg0_, eg1_) == cudaSuccess) {
+      gram_ms_ += ms;
+      ++gram_timed_;
+    }
+  }
   if (opt_.profile) {
     res->stats.count_ms = count_ms_;
     res->stats.count_launches = count_timed_;
@@ -1192,6 +1300,7 @@ static dic_status check_options(const dic_options &o) {
   if (o.count_path > DIC_COUNT_TENSOR)
     return fail(DIC_EINVAL, "unknown count_path %u", o.count_path);
   if (o.algorithm > 1) return fail(DIC_EINVAL, "algorithm must be 0 or 1 (got %u)", o.algorithm);
+  if (o.prestage > 1) return fail(DIC_EINVAL, "prestage must be 0 or 1 (got %u)", o.prestage);
   return DIC_OK;
 }
 

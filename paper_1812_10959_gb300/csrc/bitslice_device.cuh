@@ -76,22 +76,30 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
                                                 uint32_t &pruned, uint32_t &solid,
                                                 unsigned long long &work) {
   constexpr uint32_t ST = bs_stride(TW);
+  static_assert(KRMAX == 16, "ranks are loaded as two 16-byte words");
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint32_t *__restrict__ V = vcols(L, g);
   const uint32_t l1p = L.l1p;
   for (uint64_t c = lo + (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < hi;
        c += nwarps) {
-    // the record's state is loaded up front with its ranks (no load of the
-    // count pass waits on PRUNE's operands)
+    // the record's state and all its ranks in one round of independent loads
+    // (lane 0 keeps what PRUNE needs; the ranks are broadcast from the same
+    // two 16-byte words)
     const uint8_t sh = L.cshape[c];
-    const uint32_t k = sh == SH_NIL ? 0u : (uint32_t)L.ck[c];
+    const uint32_t k8 = L.ck[c];
+    const uint4 *rk4 = reinterpret_cast<const uint4 *>(L.cranks + c * KRMAX);
+    const uint4 ra = __ldg(rk4);
+    const uint4 rb = KRE > 8 ? __ldg(rk4 + 1) : make_uint4(0u, 0u, 0u, 0u);
+    uint32_t supp0 = 0, birth = 0;
+    if (lane == 0) { supp0 = L.csupp[c]; birth = L.cbirth[c]; }
+    const uint32_t k = sh == SH_NIL ? 0u : k8;
     if (k == 0) continue;  // uniform over the warp
-    const uint32_t supp0 = L.csupp[c], birth = L.cbirth[c];
-    const uint16_t *rk = L.cranks + c * KRMAX;
+    const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
     uint32_t r[KRE];
 #pragma unroll
-    for (int q = 0; q < KRE; ++q) r[q] = (uint32_t)q < k ? (uint32_t)rk[q] : 0u;
+    for (int q = 0; q < KRE; ++q)
+      r[q] = (uint32_t)q < k ? (rw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu : 0u;
     uint32_t cnt = 0;
 #pragma unroll 8
     for (uint32_t w = lane; w < nw32; w += 32) {

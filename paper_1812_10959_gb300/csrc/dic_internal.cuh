@@ -135,12 +135,46 @@ struct Lattice {
   // (the first pass's pair join); 0 for classic DIC, whose pairs are
   // generated one by one
   uint32_t pairs_lex;
+  // 1: V holds the columns of every block of the pass (block b at
+  // V + b * vwords), transposed once before the loop
+  uint32_t vall;
+  // 1: the pair cohort [0, pair_end) is counted over every block before the
+  // loop (tensor GEMM) and its promotions and prunes are precomputed per
+  // stop: at stop g <= stop_max the records ev_list[ev_off[g] ..
+  // ev_off[g+1]) are promoted, ev_pruned[g] pairs are dropped by the bound,
+  // and at stop_max ev_pruned[0] pair boxes complete their pass. Their
+  // supports hold the full-pass totals from the start.
+  uint32_t pair_events;
   uint32_t pad3;
+  const uint32_t *ev_off;     // [stop_max + 2]
+  const uint32_t *ev_list;    // [pair_end]
+  const uint32_t *ev_pruned;  // [stop_max + 1]
 };
 
 // The column buffer of stop g's block.
 __device__ __forceinline__ uint32_t *vcols(const Lattice &L, uint32_t g) {
+  if (L.vall) return L.V + (uint64_t)((g - 1) % L.stop_max) * L.vwords;
   return L.V + ((L.vdouble && (g & 1u)) ? L.vwords : 0ull);
+}
+
+// First record of the window [head, tail) that the count kernels of stop g
+// count themselves: the pair cohort is skipped while the tensor path handles
+// it (per-stop GEMM beside the BITSLICE count, or precomputed events).
+__device__ __forceinline__ uint32_t counted_lo(const Lattice &L, uint32_t head, uint32_t tail,
+                                               uint32_t g, bool bitslice) {
+  const uint32_t skip =
+      (L.pair_end && g <= L.stop_max && (bitslice || L.pair_events)) ? L.pair_end : 0u;
+  return skip > head ? (skip < tail ? skip : tail) : head;
+}
+
+// Programmatic dependent launch: every kernel of the stop loop waits for the
+// grid before it in the stream (no-op when launched without the attribute)
+// and lets the next grid start launching at once.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // The pair-cohort kernels of the TENSOR path (GEMM and its PRUNE, which run
@@ -176,6 +210,32 @@ __host__ __device__ inline void block_of(uint32_t g, uint32_t stop_max, uint64_t
 // Set the thread-local text returned by dic_last_error().
 void set_last_error(const char *msg);
 
+// Whether the stop-loop launchers give their kernels the programmatic
+// dependent launch attribute (a per-host-thread setting: the single-query
+// loop turns it on while it enqueues stops that run on one stream, where
+// every kernel waits for the one before it with pdl_wait()).
+bool &pdl_enabled();
+
+// Launch through cudaLaunchKernelEx with the stop loop's attributes; returns
+// this launch's own status.
+template <class... KArgs, class... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  if (pdl_enabled()) {
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
 // ---- kernel launchers (kernels_*.cu) ----
 cudaError_t launch_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_t m,
                               uint32_t *cnt, cudaStream_t s);
@@ -201,6 +261,20 @@ cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
                                  uint32_t *out_count, cudaStream_t s);
 cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
                                 uint32_t *supp, cudaStream_t s);
+
+// Columns of every block of the pass (L.vall), transposed once from the
+// original rows B[n][W] (item p -> rank rank_of[p], -1 = not frequent).
+cudaError_t launch_slice_all(Lattice L, const uint64_t *B, uint32_t W, const int32_t *rank_of,
+                             cudaStream_t s);
+// All-blocks pair GEMM (L.vall, pairs_lex): pc[b][record] = the pair's count
+// over block b (uint32 when `wide`, else uint16: blocks below 65,536 rows).
+cudaError_t launch_gram_all_blocks(Lattice L, void *pc, bool wide, cudaStream_t s);
+// Pair events from those counts (Lattice pair_events): ev[npairs], hist
+// [2 (stop_max + 2)], ev_off [stop_max + 2], cursor [stop_max + 2],
+// ev_list [npairs], ev_pruned [stop_max + 1]; writes the pairs' totals.
+cudaError_t launch_pair_events(Lattice L, const void *pc, bool wide, uint32_t *ev,
+                               uint32_t *hist, uint32_t *ev_off, uint32_t *cursor,
+                               uint32_t *ev_list, uint32_t *ev_pruned, cudaStream_t s);
 
 // BITSLICE path (kernels_count_bitslice.cu). V holds the stop's block as
 // per-rank bit columns, tile-major: tile t covers rows first+32*TW*t ..,

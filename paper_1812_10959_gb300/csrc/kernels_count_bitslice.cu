@@ -45,6 +45,8 @@ constexpr int BS_THREADS = 1024;
 // double-buffered columns, the next stop's block while this one is counted
 // (otherwise the previous stop's generate kernel transposes it).
 __global__ void __launch_bounds__(256) k_slice_block(Lattice L, uint32_t ahead) {
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   slice_block_warps(L, C->step + ahead,
@@ -62,7 +64,55 @@ cudaError_t launch_slice_block(Lattice L, uint32_t ahead, cudaStream_t s) {
   uint64_t want = (items + 7) / 8;
   int grid = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
   if (grid < 1) grid = 1;
-  k_slice_block<<<grid, 256, 0, s>>>(L, ahead);
+  return launch_k(k_slice_block, grid, 256, 0, s, L, ahead);
+}
+
+// Every block of the pass at once (L.vall): warp item (block b, 32-row word
+// w of the block, word j of the original rows); bit i of source word j is
+// item 64j + i, kept at rank rank_of[64j + i] when frequent. Rows past a
+// block's end read as 0, so every word of every rank row of every tile is
+// written. An index outside V is recorded in Ctrl.error and skipped.
+__global__ void __launch_bounds__(256) k_slice_all(Lattice L, const uint64_t *__restrict__ B,
+                                                   uint32_t W, const int32_t *__restrict__ rank_of) {
+  const uint32_t tw = L.tw, l1p = L.l1p, st = bs_stride((int)tw);
+  const uint64_t blockmax = L.M < L.n ? L.M : L.n;
+  const uint32_t ntiles = (uint32_t)(((blockmax + 31) / 32 + tw - 1) / tw);
+  const uint64_t per_block = (uint64_t)ntiles * tw * W;
+  const uint64_t items = per_block * L.stop_max;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
+       it += nwarps) {
+    const uint64_t b = it / per_block, rem = it % per_block;
+    const uint32_t w = (uint32_t)(rem / W), j = (uint32_t)(rem % W);
+    const uint64_t first = b * L.M;
+    const uint64_t last = first + L.M < L.n ? first + L.M : L.n;
+    const uint64_t row = first + 32ull * w + lane;
+    const uint64_t x = row < last ? __ldg(B + row * W + j) : 0ull;
+    const uint32_t lo = warp_transpose32((uint32_t)x);
+    const uint32_t hi = warp_transpose32((uint32_t)(x >> 32));
+    const int32_t r0 = __ldg(rank_of + j * 64 + lane), r1 = __ldg(rank_of + j * 64 + 32 + lane);
+    const uint32_t t = w / tw, wi = w % tw;
+    uint32_t *Vb = L.V + b * L.vwords;
+    if (r0 >= 0) {
+      const uint64_t i0 = ((uint64_t)t * l1p + (uint32_t)r0) * st + wi;
+      if (i0 < L.vwords && (uint32_t)r0 < l1p) Vb[i0] = lo;
+      else L.ctrl->error = DIC_INTERNAL_BOUNDS;
+    }
+    if (r1 >= 0) {
+      const uint64_t i1 = ((uint64_t)t * l1p + (uint32_t)r1) * st + wi;
+      if (i1 < L.vwords && (uint32_t)r1 < l1p) Vb[i1] = hi;
+      else L.ctrl->error = DIC_INTERNAL_BOUNDS;
+    }
+  }
+}
+
+cudaError_t launch_slice_all(Lattice L, const uint64_t *B, uint32_t W, const int32_t *rank_of,
+                             cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_slice_all<<<sms * 8, 256, 0, s>>>(L, B, W, rank_of);
   return cudaGetLastError();
 }
 
@@ -91,6 +141,8 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
                                                                uint32_t l1p, uint32_t chunk_cap,
                                                                uint64_t vwords) {
   extern __shared__ __align__(16) uint32_t sm[];
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   if (!bs_checks<KRE>(L, C, blockIdx.x == 0)) return;
@@ -98,14 +150,18 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   uint32_t nw32, ntiles;
   if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
   const uint32_t head = C->head, tail = C->tail;
-  // records below `skip` (the pair cohort while the tensor path counts it)
-  // are counted and pruned by the tensor path; this kernel counts [lo, tail)
-  const uint32_t skip = (L.pair_end && g <= L.stop_max) ? L.pair_end : 0u;
-  const uint32_t lo = skip > head ? (skip < tail ? skip : tail) : head;
+  // records below the pair cohort's end, while the tensor path has it, are
+  // counted and pruned there; this kernel counts [lo, tail)
+  const uint32_t lo = counted_lo(L, head, tail, g, true);
   const uint32_t ncand = tail - lo;
   uint32_t pruned = 0, solid = 0;
   unsigned long long work = 0;
-  if (ncand == 0) return;
+  apply_pair_events(L, C, g, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                    (uint64_t)gridDim.x * blockDim.x, pruned, solid);
+  if (ncand == 0) {
+    block_add_tallies(C, pruned, solid, work);
+    return;
+  }
   if (ncand <= BS_DIRECT_MAX) {
     // few candidates: no shared tiles; a warp per candidate ANDs its columns
     // straight from the (L2-resident) column buffer
@@ -132,6 +188,8 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
 // share SMs with the pair-cohort GEMM of the same stop.
 template <int TW, int KRE>
 __global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   if (!bs_checks<KRE>(L, C, blockIdx.x == 0)) return;
@@ -139,12 +197,12 @@ __global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
   uint32_t nw32, ntiles;
   if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
   const uint32_t head = C->head, tail = C->tail;
-  const uint32_t skip = (L.pair_end && g <= L.stop_max) ? L.pair_end : 0u;
-  const uint32_t lo = skip > head ? (skip < tail ? skip : tail) : head;
-  if (lo >= tail) return;
+  const uint32_t lo = counted_lo(L, head, tail, g, true);
   uint32_t pruned = 0, solid = 0;
   unsigned long long work = 0;
-  bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid, work);
+  apply_pair_events(L, C, g, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                    (uint64_t)gridDim.x * blockDim.x, pruned, solid);
+  if (lo < tail) bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid, work);
   block_add_tallies(C, pruned, solid, work);
 }
 
@@ -152,6 +210,8 @@ __global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
 // this stop's counts: four records per thread, every load issued before any
 // record is examined.
 __global__ void __launch_bounds__(256) k_settle_pairs(Lattice L, uint32_t kre) {
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (!L.pair_end || !gram_may_run(L, C, kre)) return;
   const uint32_t g = C->step;
@@ -180,23 +240,18 @@ __global__ void __launch_bounds__(256) k_settle_pairs(Lattice L, uint32_t kre) {
 }
 
 cudaError_t launch_settle_pairs(Lattice L, int grid, uint32_t kre, cudaStream_t s) {
-  k_settle_pairs<<<grid, 256, 0, s>>>(L, kre);
-  return cudaGetLastError();
+  return launch_k(k_settle_pairs, grid, 256, 0, s, L, kre);
 }
 
 template <int TW, int KRE>
 static cudaError_t go(Lattice L, const uint32_t *V, uint32_t l1p, uint32_t chunk, uint64_t vw,
                       int grid, bool direct, cudaStream_t s) {
-  if (direct) {
-    k_count_direct<TW, KRE><<<grid, 256, 0, s>>>(L);
-    return cudaGetLastError();
-  }
+  if (direct) return launch_k(k_count_direct<TW, KRE>, grid, 256, 0, s, L);
   const size_t smem = bitslice_smem(TW, KRE, l1p, chunk);
   cudaError_t e = cudaFuncSetAttribute(k_count_bitslice<TW, KRE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_count_bitslice<TW, KRE><<<grid, BS_THREADS, smem, s>>>(L, V, l1p, chunk, vw);
-  return cudaGetLastError();
+  return launch_k(k_count_bitslice<TW, KRE>, grid, BS_THREADS, smem, s, L, V, l1p, chunk, vw);
 }
 
 template <int TW>

@@ -25,6 +25,8 @@ constexpr int ROWS_THREADS = 256;
 template <int NW>
 __global__ void __launch_bounds__(ROWS_THREADS) k_count_rows(Lattice L, uint32_t rch) {
   extern __shared__ uint32_t srow[];
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   const uint32_t wc = L.wc, hw = 2 * wc;
@@ -35,7 +37,9 @@ __global__ void __launch_bounds__(ROWS_THREADS) k_count_rows(Lattice L, uint32_t
       return;
     }
   }
-  const uint32_t g = C->step, head = C->head, tail = C->tail;
+  const uint32_t g = C->step, tail = C->tail;
+  // (the pair cohort is skipped while its outcome is precomputed)
+  const uint32_t head = counted_lo(L, C->head, tail, g, false);
   uint32_t stop;
   uint64_t first, last;
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
@@ -117,10 +121,13 @@ __global__ void __launch_bounds__(ROWS_THREADS) k_count_rows(Lattice L, uint32_t
 // Generic width: any number of halves, mask words read from global memory.
 __global__ void __launch_bounds__(ROWS_THREADS) k_count_rows_dense(Lattice L, uint32_t rch) {
   extern __shared__ uint32_t srow[];
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   const uint32_t wc = L.wc;
-  const uint32_t g = C->step, head = C->head, tail = C->tail;
+  const uint32_t g = C->step, tail = C->tail;
+  const uint32_t head = counted_lo(L, C->head, tail, g, false);
   uint32_t stop;
   uint64_t first, last;
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
@@ -192,8 +199,7 @@ static cudaError_t go(Lattice L, int grid, uint32_t rch, size_t smem, cudaStream
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_count_rows<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-  k_count_rows<NW><<<grid, ROWS_THREADS, smem, s>>>(L, rch);
-  return cudaGetLastError();
+  return launch_k(k_count_rows<NW>, grid, ROWS_THREADS, smem, s, L, rch);
 }
 
 cudaError_t launch_count_rows(Lattice L, int nw, int grid, cudaStream_t s) {
@@ -209,8 +215,7 @@ cudaError_t launch_count_rows(Lattice L, int nw, int grid, cudaStream_t s) {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_count_rows_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-      k_count_rows_dense<<<grid, ROWS_THREADS, smem, s>>>(L, rch);
-      return cudaGetLastError();
+      return launch_k(k_count_rows_dense, grid, ROWS_THREADS, smem, s, L, rch);
   }
 }
 

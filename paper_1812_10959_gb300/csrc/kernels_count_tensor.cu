@@ -131,24 +131,38 @@ __host__ __device__ __forceinline__ uint32_t gram_pairs_of(uint32_t na, uint32_t
   return p;
 }
 
+// ALL = false: the pair cohort's counts over stop g's block are added to its
+// counters (atomics; `nsplit` CTAs split each tile pair's rows).
+// ALL = true: CTA (block b, tile pair) writes the pairs' counts over block b
+// of the pass to pc[b * pairs + record] (plain stores; every pair of frequent
+// ranks gets one, zeros included), for all blocks in one launch.
+template <bool ALL, class T>
 __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint32_t nsplit,
-                                                                uint32_t kre) {
+                                                                uint32_t kre, T *pc) {
   extern __shared__ __align__(1024) uint8_t gsm[];
   __shared__ __align__(8) uint64_t full[GSTAGES], empty[GSTAGES], done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile uint32_t failed;
   Ctrl *C = L.ctrl;
-  if (!gram_may_run(L, C, kre)) return;
-  const uint32_t g = C->step;
+  if (!ALL) {
+    pdl_wait();
+    pdl_trigger();
+    if (!gram_may_run(L, C, kre)) return;
+  }
+  const uint32_t na = (L.l1 + GM - 1) / GM, nb = (L.l1 + GN - 1) / GN;
+  const uint32_t ntp = gram_pairs_of(na, nb);
+  // stop g whose block this CTA counts (ALL: the stop of pass block b)
+  const uint32_t g = ALL ? blockIdx.x / ntp + 1 : C->step;
   uint32_t stop;
   uint64_t first, last;
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
   const uint32_t nrows = (uint32_t)(last - first);
-  if (blockIdx.x == 0 && threadIdx.x == 0) C->gram_rows += nrows;
+  if (!ALL && blockIdx.x == 0 && threadIdx.x == 0) C->gram_rows += nrows;
   const uint32_t nkc = (nrows + GK - 1) / GK;
   // which tile pair (A tile ti, B tile tj >= ti / 2) and which K split
-  const uint32_t na = (L.l1 + GM - 1) / GM, nb = (L.l1 + GN - 1) / GN;
-  const uint32_t pair = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+  const uint32_t pair = ALL ? blockIdx.x % ntp : blockIdx.x / nsplit;
+  const uint32_t split = ALL ? 0u : blockIdx.x % nsplit;
+  if (ALL) nsplit = 1;
   uint32_t ti = 0, rem = pair;
   while (ti < na && rem >= nb - ti / 2) { rem -= nb - ti / 2; ++ti; }
   if (ti >= na) return;
@@ -261,6 +275,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
     // rings are idle once `done` has fired) so that a warp's adds go to 32
     // consecutive counters: lane q adds count (a, b0 + q) of row a.
     const uint64_t l1 = L.l1;
+    T *pc_out = ALL ? pc + (uint64_t)(g - 1) * (l1 * (l1 - 1) / 2) : pc;
     uint32_t *stage = reinterpret_cast<uint32_t *>(gsm) + warp * (32 * 33);
     const uint32_t lq = warp % 4;
     const uint64_t a0 = (uint64_t)ti * GM + lq * 32;
@@ -288,7 +303,11 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
       for (uint32_t r = 0; r < rmax; ++r) {
         const uint64_t a = a0 + r;
         const uint32_t cnt = stage[r * 33 + lane];
-        if (b > a && b < l1 && cnt) atomicAdd(&L.csupp[pair_record(a, b, l1)], cnt);
+        if (ALL) {
+          if (b > a && b < l1) pc_out[pair_record(a, b, l1)] = (T)cnt;
+        } else if (b > a && b < l1 && cnt) {
+          atomicAdd(&L.csupp[pair_record(a, b, l1)], cnt);
+        }
       }
       __syncwarp();
     }
@@ -308,10 +327,135 @@ uint32_t gram_chunks(uint64_t rows) { return (uint32_t)((rows + GK - 1) / GK); }
 cudaError_t launch_gram_pairs(Lattice L, uint32_t nsplit, uint32_t kre, cudaStream_t s) {
   const uint32_t npairs = gram_tile_pairs(L.l1);
   const size_t smem = GSTAGES * (GTILE_A + GTILE_B);  // the A and B rings
+  auto kern = k_gram_pairs<false, uint32_t>;
   cudaError_t e =
-      cudaFuncSetAttribute(k_gram_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_pairs<<<npairs * nsplit, GRAM_THREADS, smem, s>>>(L, nsplit, kre);
+  kern<<<npairs * nsplit, GRAM_THREADS, smem, s>>>(L, nsplit, kre, (uint32_t *)nullptr);
+  return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t gram_all(Lattice L, T *pc, cudaStream_t s) {
+  const uint64_t grid = (uint64_t)gram_tile_pairs(L.l1) * L.stop_max;
+  if (grid == 0 || grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  const size_t smem = GSTAGES * (GTILE_A + GTILE_B);
+  auto kern = k_gram_pairs<true, T>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, GRAM_THREADS, smem, s>>>(L, 1u, 0u, pc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_all_blocks(Lattice L, void *pc, bool wide, cudaStream_t s) {
+  if (!L.vall) return cudaErrorInvalidValue;
+  return wide ? gram_all<uint32_t>(L, (uint32_t *)pc, s) : gram_all<uint16_t>(L, (uint16_t *)pc, s);
+}
+
+// ---------------------------------------------------------- pair events
+// Algorithm 4 for the pair cohort over its whole pass, from the per-block
+// counts pc[b][record] of the all-blocks GEMM: pair c (born before stop 1) is
+// promoted at the first stop g with support >= minsup, or dropped at the
+// first stop where its bound support + M * (stop_max - g) is below minsup
+// (exactly one of the two happens by stop_max). Its counter receives the
+// full-pass total; ev[c] = 2g + 1 (promoted at g) or 2g (dropped at g);
+// hist[g] / hist[stop_max + 2 + g] count promotions / drops per stop.
+template <class T>
+__global__ void __launch_bounds__(256) k_pair_events(Lattice L, const T *__restrict__ pc,
+                                                     uint32_t *ev, uint32_t *hist) {
+  extern __shared__ uint32_t sh[];
+  const uint32_t S = L.stop_max, H = 2 * (S + 2);
+  const bool local = H <= 4096;
+  if (local) {
+    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+  }
+  const uint64_t np = (uint64_t)L.l1 * (L.l1 - 1) / 2;
+  const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < np) {
+    uint64_t cum = 0;
+    uint32_t e = 0;
+    for (uint32_t g = 1; g <= S; ++g) {
+      cum += pc[(uint64_t)(g - 1) * np + c];
+      if (e) continue;
+      if (cum >= L.minsup) e = 2 * g + 1;
+      else if (cum + L.M * (uint64_t)(S - g) < (uint64_t)L.minsup) e = 2 * g;
+    }
+    L.csupp[c] = (uint32_t)cum;
+    ev[c] = e;
+    const uint32_t slot = (e & 1u) ? (e >> 1) : S + 2 + (e >> 1);
+    if (local) atomicAdd(&sh[slot], 1u);
+    else atomicAdd(&hist[slot], 1u);
+  }
+  if (local) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x)
+      if (sh[i]) atomicAdd(&hist[i], sh[i]);
+  }
+}
+
+// One CTA: ev_off[g] = promotions before stop g (exclusive scan over stops
+// 1..stop_max, ev_off[stop_max + 1] = all of them), a cursor copy for the
+// scatter, ev_pruned[g] = drops at g, ev_pruned[0] = all promotions.
+__global__ void __launch_bounds__(1024) k_pair_events_scan(Lattice L, const uint32_t *hist,
+                                                           uint32_t *ev_off, uint32_t *cursor,
+                                                           uint32_t *ev_pruned) {
+  __shared__ uint32_t part[1024];
+  const uint32_t S = L.stop_max;
+  const uint32_t per = (S + 1023) / 1024;
+  const uint32_t g0 = 1 + threadIdx.x * per;
+  uint32_t sum = 0;
+  for (uint32_t g = g0; g < g0 + per && g <= S; ++g) sum += hist[g];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < 1024; ++i) { const uint32_t v = part[i]; part[i] = run; run += v; }
+    ev_off[0] = 0;
+    ev_off[S + 1] = run;
+    ev_pruned[0] = run;
+  }
+  __syncthreads();
+  uint32_t run = part[threadIdx.x];
+  for (uint32_t g = g0; g < g0 + per && g <= S; ++g) {
+    ev_off[g] = run;
+    cursor[g] = run;
+    ev_pruned[g] = hist[S + 2 + g];
+    run += hist[g];
+  }
+}
+
+// The promoted pairs grouped by promotion stop (order within a stop is
+// irrelevant: MAKECANDIDATES depends only on the set).
+__global__ void __launch_bounds__(256) k_pair_events_scatter(Lattice L, const uint32_t *ev,
+                                                             uint32_t *cursor, uint32_t *ev_list) {
+  const uint64_t np = (uint64_t)L.l1 * (L.l1 - 1) / 2;
+  const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= np) return;
+  const uint32_t e = ev[c];
+  if (e & 1u) ev_list[atomicAdd(&cursor[e >> 1], 1u)] = (uint32_t)c;
+}
+
+cudaError_t launch_pair_events(Lattice L, const void *pc, bool wide, uint32_t *ev,
+                               uint32_t *hist, uint32_t *ev_off, uint32_t *cursor,
+                               uint32_t *ev_list, uint32_t *ev_pruned, cudaStream_t s) {
+  const uint64_t np = (uint64_t)L.l1 * (L.l1 - 1) / 2;
+  if (np == 0) return cudaSuccess;
+  const uint64_t grid = (np + 255) / 256;
+  if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  const uint32_t H = 2 * (L.stop_max + 2);
+  const size_t smem = H <= 4096 ? (size_t)H * 4 : 0;
+  cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)H * 4, s);
+  if (e != cudaSuccess) return e;
+  if (wide)
+    k_pair_events<uint32_t><<<(unsigned)grid, 256, smem, s>>>(L, (const uint32_t *)pc, ev, hist);
+  else
+    k_pair_events<uint16_t><<<(unsigned)grid, 256, smem, s>>>(L, (const uint16_t *)pc, ev, hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_pair_events_scan<<<1, 1024, 0, s>>>(L, hist, ev_off, cursor, ev_pruned);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_pair_events_scatter<<<(unsigned)grid, 256, 0, s>>>(L, ev, cursor, ev_list);
   return cudaGetLastError();
 }
 

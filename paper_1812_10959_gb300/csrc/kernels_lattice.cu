@@ -8,6 +8,7 @@
 // leaves DASHED for SOLID, Algorithm 5) all at once, so DASHED is the window
 // [head, tail) and solidifying is advancing `head` past whole cohorts. PRUNE
 // erases records in place (shape NIL); the count kernels skip them.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -18,39 +19,57 @@ namespace dic {
 
 // --------------------------------------------------------- first pass
 // supp1[i] = number of rows with bit i set, over all n rows (FIRSTPASS of
-// Section 4.2). Flat over the n*W words; each thread walks the set bits of
-// its words. Counters are privatised in shared memory when m fits.
-__global__ void __launch_bounds__(512) k_item_count(const uint64_t *__restrict__ B,
-                                                    uint64_t nwords, uint32_t W, uint32_t m,
-                                                    uint32_t *__restrict__ cnt, int use_smem) {
-  extern __shared__ uint32_t sc[];
-  if (use_smem) {
-    for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) sc[j] = 0;
-    __syncthreads();
+// Section 4.2). A warp takes 32 rows at a time and up to ICHUNK of their
+// 64-bit words: each word, transposed across the warp (lane t ends with the
+// 32 rows' bits of items 64j+t and 64j+32+t), adds two popcounts to the
+// lane's registers; a warp walks many row groups of the same words, then
+// adds its 2*ICHUNK counters once.
+constexpr uint32_t ICHUNK = 8;
+
+__device__ __forceinline__ uint32_t warp_transpose32_fp(uint32_t x) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lo_masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const uint32_t j = 16u >> st, mlo = lo_masks[st];
+    const uint32_t v = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~mlo) | ((v >> j) & mlo)) : ((x & mlo) | ((v << j) & ~mlo));
   }
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t col = (uint32_t)(i % W);
-  const uint32_t step_col = (uint32_t)(stride % W);
-  for (; i < nwords; i += stride) {
-    uint64_t x = __ldcs(B + i);
-    const uint32_t base = col * 64u;
-    while (x) {
-      const uint32_t b = (uint32_t)(__ffsll((long long)x) - 1);
-      x &= x - 1;
-      const uint32_t item = base + b;
-      if (item < m) {
-        if (use_smem) atomicAdd(&sc[item], 1u);
-        else atomicAdd(&cnt[item], 1u);
-      }
+  return x;
+}
+
+__global__ void __launch_bounds__(256) k_item_count(const uint64_t *__restrict__ B, uint64_t n,
+                                                    uint32_t W, uint32_t m,
+                                                    uint32_t *__restrict__ cnt) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t njc = (W + ICHUNK - 1) / ICHUNK;
+  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t wpc = nw / njc;  // warps per word chunk (the launch makes it >= 1)
+  if (gw / njc >= wpc) return;
+  const uint32_t j0 = (uint32_t)(gw % njc) * ICHUNK;
+  const uint64_t ngroups = (n + 31) / 32;
+  uint32_t acc[2 * ICHUNK];
+#pragma unroll
+  for (int q = 0; q < 2 * (int)ICHUNK; ++q) acc[q] = 0;
+  for (uint64_t rg = gw / njc; rg < ngroups; rg += wpc) {
+    const uint64_t row = rg * 32 + lane;
+    const uint64_t *p = B + row * W + j0;
+    uint64_t x[ICHUNK];
+#pragma unroll
+    for (uint32_t q = 0; q < ICHUNK; ++q)
+      x[q] = (row < n && j0 + q < W) ? __ldcs(p + q) : 0ull;
+#pragma unroll
+    for (uint32_t q = 0; q < ICHUNK; ++q) {
+      acc[2 * q] += __popc(warp_transpose32_fp((uint32_t)x[q]));
+      acc[2 * q + 1] += __popc(warp_transpose32_fp((uint32_t)(x[q] >> 32)));
     }
-    col += step_col;
-    if (col >= W) col -= W;
   }
-  if (use_smem) {
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < m; j += blockDim.x)
-      if (sc[j]) atomicAdd(&cnt[j], sc[j]);
+#pragma unroll
+  for (uint32_t q = 0; q < ICHUNK; ++q) {
+    const uint32_t i0 = (j0 + q) * 64 + lane, i1 = i0 + 32;
+    if (i0 < m && acc[2 * q]) atomicAdd(&cnt[i0], acc[2 * q]);
+    if (i1 < m && acc[2 * q + 1]) atomicAdd(&cnt[i1], acc[2 * q + 1]);
   }
 }
 
@@ -59,16 +78,18 @@ cudaError_t launch_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int use_smem = m <= 16384;
-  const size_t smem = use_smem ? (size_t)m * 4 : 0;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_item_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaMemsetAsync(cnt, 0, (size_t)m * 4, s);
-  const uint64_t nwords = n * W;
-  if (nwords == 0) return cudaGetLastError();
-  uint64_t want = (nwords + 511) / 512;
-  int grid = (int)(want < (uint64_t)sms * 3 ? want : (uint64_t)sms * 3);
-  k_item_count<<<grid, 512, smem, s>>>(B, nwords, W, m, cnt, use_smem);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)m * 4, s);
+  if (e != cudaSuccess || n == 0) return e;
+  const uint32_t njc = (W + ICHUNK - 1) / ICHUNK;
+  const uint64_t groups = (n + 31) / 32;
+  // enough warps to cover every word chunk, at most one warp per row group
+  // and chunk, at most 8 CTAs of 8 warps per SM
+  uint64_t warps = std::min<uint64_t>((uint64_t)sms * 64, groups * njc);
+  warps = std::max<uint64_t>(warps, njc);
+  warps = (warps + njc - 1) / njc * njc;
+  const uint64_t grid = (warps + 7) / 8;
+  if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  k_item_count<<<(unsigned)grid, 256, 0, s>>>(B, n, W, m, cnt);
   return cudaGetLastError();
 }
 
@@ -169,33 +190,32 @@ __device__ __forceinline__ uint64_t pair_off(uint64_t a, uint64_t l1) {
   return a * (2 * l1 - a - 1) / 2;  // pairs whose first rank is < a
 }
 
-__global__ void k_pair_join(Lattice L, uint64_t npairs) {
-  const uint64_t total = npairs * L.wc;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+// CTA per first rank a: the records of pairs {a, b}, b = a+1 .. l1-1, are
+// the contiguous range pair_off(a) + (b - a - 1), so their mask words and
+// fields are written with consecutive addresses.
+__global__ void __launch_bounds__(256) k_pair_join(Lattice L) {
   const uint64_t l1 = L.l1;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const uint64_t p = i / L.wc;
-    const uint32_t w = (uint32_t)(i % L.wc);
-    const double q = (double)(2 * l1 - 1);
-    double disc = q * q - 8.0 * (double)p;
-    if (disc < 0) disc = 0;
-    int64_t a = (int64_t)((q - sqrt(disc)) * 0.5);
-    if (a < 0) a = 0;
-    if (a > (int64_t)l1 - 2) a = (int64_t)l1 - 2;
-    while (a > 0 && pair_off((uint64_t)a, l1) > p) --a;
-    while ((uint64_t)a + 1 < l1 - 1 && pair_off((uint64_t)a + 1, l1) <= p) ++a;
-    const uint64_t b = (uint64_t)a + 1 + (p - pair_off((uint64_t)a, l1));
-    uint64_t word = 0;
-    if ((uint64_t)a >> 6 == w) word |= 1ull << (a & 63);
-    if (b >> 6 == w) word |= 1ull << (b & 63);
-    L.cmask[p * L.wc + w] = word;
-    if (w == 0) {
+  const uint32_t wc = L.wc;
+  for (uint64_t a = blockIdx.x; a + 1 < l1; a += gridDim.x) {
+    const uint64_t p0 = pair_off(a, l1), cnt = l1 - a - 1;
+    uint64_t *mk = L.cmask + p0 * wc;
+    for (uint64_t e = threadIdx.x; e < cnt * wc; e += blockDim.x) {
+      const uint64_t b = a + 1 + e / wc;
+      const uint32_t w = (uint32_t)(e % wc);
+      uint64_t word = 0;
+      if ((a >> 6) == w) word |= 1ull << (a & 63);
+      if ((b >> 6) == w) word |= 1ull << (b & 63);
+      mk[e] = word;
+    }
+    for (uint64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+      const uint64_t p = p0 + q, b = a + 1 + q;
       L.csupp[p] = 0;
       L.cbirth[p] = 0;
       L.cshape[p] = SH_CIRCLE;
       L.ck[p] = 2;
-      L.cranks[p * KRMAX + 0] = (uint16_t)a;
-      L.cranks[p * KRMAX + 1] = (uint16_t)b;
+      uint4 *rk = reinterpret_cast<uint4 *>(L.cranks + p * KRMAX);
+      rk[0] = make_uint4((uint32_t)a | ((uint32_t)b << 16), 0u, 0u, 0u);
+      rk[1] = make_uint4(0u, 0u, 0u, 0u);
     }
   }
 }
@@ -228,9 +248,12 @@ cudaError_t launch_singleton_join(Lattice L, cudaStream_t s) {
 
 cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s) {
   if (npairs == 0) return cudaSuccess;
-  uint64_t want = (npairs * L.wc + 255) / 256;
-  int grid = (int)(want < 65535ull * 8 ? want : 65535ull * 8);
-  k_pair_join<<<grid, 256, 0, s>>>(L, npairs);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t rows = (uint64_t)L.l1 - 1;
+  const int grid = (int)(rows < (uint64_t)sms * 8 ? rows : (uint64_t)sms * 8);
+  k_pair_join<<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -242,10 +265,16 @@ cudaError_t launch_pair_join(Lattice L, uint64_t npairs, cudaStream_t s) {
 // circle has no dashed superset and the loop could only match the record
 // itself.
 __global__ void __launch_bounds__(256) k_promote(Lattice L) {
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
-  const uint32_t g = C->step, head = C->head, tail = C->tail;
+  const uint32_t g = C->step, tail = C->tail;
+  const uint32_t head = counted_lo(L, C->head, tail, g, false);
   uint32_t pruned = 0, solid = 0;
+  // (k_hash_insert inserts this stop's new boxes, the pairs' included)
+  apply_pair_events(L, C, g, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                    (uint64_t)gridDim.x * blockDim.x, pruned, solid, false);
   for (uint32_t c = head + blockIdx.x * blockDim.x + threadIdx.x; c < tail;
        c += gridDim.x * blockDim.x)
     settle_record(L, C, c, L.csupp[c], g, false, pruned, solid);
@@ -253,8 +282,7 @@ __global__ void __launch_bounds__(256) k_promote(Lattice L) {
 }
 
 cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s) {
-  k_promote<<<grid, 256, 0, s>>>(L);
-  return cudaGetLastError();
+  return launch_k(k_promote, grid, 256, 0, s, L);
 }
 
 // -------------------------------------------------------------- box set
@@ -262,6 +290,8 @@ cudaError_t launch_promote(Lattice L, int grid, cudaStream_t s) {
 // before any insert and reads only values this kernel does not change, so
 // every block takes the same decision.
 __global__ void __launch_bounds__(256) k_hash_insert(Lattice L) {
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   const uint32_t P = C->n_newbox;
@@ -278,8 +308,7 @@ __global__ void __launch_bounds__(256) k_hash_insert(Lattice L) {
 }
 
 cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s) {
-  k_hash_insert<<<grid, 256, 0, s>>>(L);
-  return cudaGetLastError();
+  return launch_k(k_hash_insert, grid, 256, 0, s, L);
 }
 
 // Rebuild the box set into a larger table.
@@ -309,6 +338,8 @@ cudaError_t launch_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap, cudaS
 // the new cohort, CHECKFULLPASS (cohorts whose full pass is complete leave
 // the window [head, tail)), |DASHED| and the loop test of Algorithm 2.
 __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_next) {
+  pdl_wait();
+  pdl_trigger();
   Ctrl *C = L.ctrl;
   if (C->stall || C->done) return;
   if (slice_next)  // the columns of stop g+1 (count of stop g is complete)
@@ -338,8 +369,7 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_ne
 }
 
 cudaError_t launch_generate_finish(Lattice L, int grid, bool slice_next, cudaStream_t s) {
-  k_generate_finish<<<grid, 256, 0, s>>>(L, slice_next ? 1 : 0);
-  return cudaGetLastError();
+  return launch_k(k_generate_finish, grid, 256, 0, s, L, slice_next ? 1 : 0);
 }
 
 // --------------------------------------------------------------- output

@@ -108,6 +108,26 @@ __device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_
   settle_loaded(L, C, c, sh, L.cbirth[c], s, g, insert, pruned, solid);
 }
 
+// Stop g's precomputed PRUNE outcome for the pair cohort (Lattice
+// pair_events): the pairs listed for g are promoted (box set insert, the
+// list MAKECANDIDATES reads); the pairs dropped by the bound at g, and at
+// stop_max the pair boxes completing their pass, are added to the caller's
+// tallies by thread 0. Threads tid = 0 .. nthreads-1 share the work.
+// `insert`: as for promote_record (false where a later kernel inserts the
+// stop's new boxes).
+__device__ __forceinline__ void apply_pair_events(const Lattice &L, Ctrl *C, uint32_t g,
+                                                  uint64_t tid, uint64_t nthreads,
+                                                  uint32_t &pruned, uint32_t &solid,
+                                                  bool insert = true) {
+  if (!L.pair_events || g > L.stop_max) return;
+  const uint32_t a = L.ev_off[g], b = L.ev_off[g + 1];
+  for (uint64_t i = a + tid; i < b; i += nthreads) promote_record(L, C, L.ev_list[i], g, insert);
+  if (tid == 0) {
+    pruned += L.ev_pruned[g];
+    if (g == L.stop_max) solid += L.ev_pruned[0];
+  }
+}
+
 // MAKECANDIDATES for one (record promoted at g, rank r) pair: C = A | r is
 // emitted iff every C \ {j} is a box and no j < r has C \ {j} promoted at g
 // (the canonical parent). New records go to base + n_gen; past the capacity

@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
                 ("profile_every", ctypes.c_uint32), ("tile_words", ctypes.c_uint32),
                 ("count_form", ctypes.c_uint32), ("algorithm", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("prestage", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -259,10 +259,13 @@ COUNT_FORMS = {"auto": 0, "tiled": 1, "direct": 2}
 ALGORITHMS = {"paralleldic": 0, "classic": 1}
 
 
+PRESTAGE = {"auto": 0, "off": 1}
+
+
 def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
             profile=False, max_candidates: int = 0, profile_every: int = 0,
             tile_words: int = 0, count_form: str = "auto",
-            algorithm: str = "paralleldic") -> Options:
+            algorithm: str = "paralleldic", prestage: str = "auto") -> Options:
     o = Options()
     _lib.dic_options_init(ctypes.byref(o))
     o.count_path = PATHS[path]
@@ -273,6 +276,7 @@ def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
     o.tile_words = tile_words
     o.count_form = COUNT_FORMS[count_form]
     o.algorithm = ALGORITHMS[algorithm]
+    o.prestage = PRESTAGE[prestage]
     o.max_candidates = max_candidates
     return o
 
@@ -280,12 +284,15 @@ def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
 def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
          profile=False, steps_per_sync: int = 0, use_graph: bool = True,
          max_candidates: int = 0, profile_every: int = 0, tile_words: int = 0,
-         count_form: str = "auto", algorithm: str = "paralleldic") -> Result:
+         count_form: str = "auto", algorithm: str = "paralleldic",
+         prestage: str = "auto") -> Result:
     """All itemsets with support >= minsup (integer count), blocks of M rows.
     algorithm: "paralleldic" (Algorithm 2, first pass then pairs) or
-    "classic" (Algorithm 1, every 1-itemset a dashed circle)."""
+    "classic" (Algorithm 1, every 1-itemset a dashed circle). prestage:
+    "auto" (stage every block's columns, and count the pair cohort over the
+    whole pass, before the loop when they fit) or "off" (per stop)."""
     o = options(path, steps_per_sync, use_graph, profile, max_candidates, profile_every,
-                tile_words, count_form, algorithm)
+                tile_words, count_form, algorithm, prestage)
     h = ctypes.c_void_p()
     _check(_lib.dic_mine_ex(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
                             ctypes.byref(h)))
