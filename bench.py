@@ -55,7 +55,7 @@ COUNT_KERNELS = {1: "k_count_rows", 2: "k_count_direct", 3: "k_count_direct"}  #
 FP8_PER_BF16 = 2.0
 # the timed steps bracket the dominant kernel kind with CUDA events on one
 # stop in this many
-PROFILE_EVERY = 8
+PROFILE_EVERY = 16
 # timed kinds of the stop loop: stats key prefix -> profile name, kernels
 KINDS = {"count": "count", "gram": "gram", "settle": "settle", "gen": "gen"}
 KIND_KERNELS = {"gram": "k_gram_pairs", "settle": "k_settle_pairs",
@@ -225,6 +225,57 @@ def cpu_sample_desc(db):
     return (f"oracle (serial C++ ParallelDIC) on the same database: first pass over all "
             f"{db.n} rows + the first stop of all pair candidates over a {CPU_SAMPLE_M}-row "
             f"block (M={CPU_SAMPLE_M} instead of {db.M} to bound the sample)")
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# The multi-core baseline's sample of the paper-scale workload: the first
+# pass over all rows and the first stops of the loop at the workload's own M.
+PDIC_SAMPLE_STOPS = 2
+
+
+def cpu_paralleldic(db):
+    """The paper's own parallel design (ParallelDIC with OpenMP, Algorithms
+    2-5 with the loop interchange and nested balancing of Figures 2-3) on
+    every host core: the complete planted-small mine (its result checked
+    against the serial oracle) and a bounded sample of `db`."""
+    import oracle
+    small = synth.planted_small()
+    t0 = time.perf_counter()
+    r1, used = oracle.paralleldic(small.row_ptr, small.items, small.n, small.m, small.minsup,
+                                  small.M)
+    c1_s = time.perf_counter() - t0
+    ref = oracle.dic(small.row_ptr, small.items, small.n, small.m, small.minsup, small.M,
+                     superset_loop=False)
+    same = r1.itemsets == ref.itemsets and r1.trace.tolist() == ref.trace.tolist()
+    t0 = time.perf_counter()
+    r2, _ = oracle.paralleldic(db.row_ptr, db.items, db.n, db.m, db.minsup, db.M,
+                               max_stops=PDIC_SAMPLE_STOPS)
+    dt = time.perf_counter() - t0
+    return {"value": r2.tests / dt, "unit": UNIT, "cores": used, "cpu_model": cpu_model(),
+            "nproc": os.cpu_count(), "kind": "ParallelDIC, OpenMP (the paper's design)",
+            "sample": (f"{db.name}: first pass over all {db.n} rows + the first "
+                       f"{PDIC_SAMPLE_STOPS} stops at M={db.M} ({r2.tests} tests in {dt:.1f} s)"),
+            "planted_small_full_mine_ms": 1000 * c1_s,
+            "planted_small_tests_per_s": r1.tests / c1_s,
+            "planted_small_equal_to_oracle": bool(same)}
 
 
 def aggregate_replicas(seconds: float, tests: float, device: str):
@@ -569,11 +620,13 @@ def main():
     roofline = roofline_of(kind, stats, shares_ms, sum(ms), db, kw.get("count_form", "auto"),
                            res.trace, alu_peak)
 
-    cpu = None
+    cpu = pdic = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, t, dt = cpu_sample(db)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": cpu_sample_desc(db) + f" ({t} tests in {dt:.1f} s)"}
+               "sample": cpu_sample_desc(db) + f" ({t} tests in {dt:.1f} s)",
+               "cpu_model": cpu_model()}
+        pdic = cpu_paralleldic(db)
 
     launches = sum(s["kernel_launches"] for s in stats)
     if rank == 0:
@@ -596,6 +649,7 @@ def main():
             "autotune": ({"choice": tuned.kwargs(), "candidates_s": tuned.timings}
                          if tuned else None),
             "cpu_baseline": cpu,
+            "cpu_paralleldic": pdic,
             "clocks": clk,
             "stats": stats[0],
         }

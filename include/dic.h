@@ -208,10 +208,31 @@ void dic_options_init(dic_options *opt);
  * The result owns host copies of the itemsets (see dic_result_copy). */
 dic_status dic_mine(const dic_db *db, uint32_t minsup_count, uint64_t M, dic_result **out);
 
-/* As dic_mine, with options and a caller stream (cudaStream_t or NULL for
- * an internal stream). Returns when the result is on the host. */
+/* As dic_mine, with options and a caller stream (cudaStream_t or NULL).
+ * The device work runs on an internal stream that first waits for the work
+ * enqueued on the caller's stream before the call; the caller's stream then
+ * waits for the mine. Returns when the result is on the host. */
 dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint64_t M,
                        const dic_options *opt, void *stream, dic_result **out);
+
+/* Asynchronous mining: the same mine as dic_mine_ex, started on a worker
+ * thread of the library so that the call returns at once; several mines may
+ * be in flight together (on different streams they overlap on the device).
+ * Its device work runs on an internal stream behind whatever the caller
+ * enqueued on `stream` (cudaStream_t, or NULL) before the call; the
+ * result is consumed through dic_mine_wait.
+ * `db` stays busy (dic_db_free gives DIC_EBUSY) until the mine ends. On
+ * DIC_OK *job identifies the mine; every job must be waited exactly once.
+ * Same inputs, checks and errors as dic_mine_ex (reported by dic_mine_wait
+ * for failures after the start). */
+typedef struct dic_mine_job dic_mine_job;
+dic_status dic_mine_async(const dic_db *db, uint32_t minsup_count, uint64_t M,
+                          const dic_options *opt, void *stream, dic_mine_job **job);
+/* Wait for a job (timeout_ms < 0: no limit). DIC_ETIMEOUT if it has not
+ * finished within timeout_ms: the job stays valid and can be waited again.
+ * Otherwise the job is released and its status returned; on DIC_OK *out
+ * owns the result. */
+dic_status dic_mine_wait(dic_mine_job *job, int64_t timeout_ms, dic_result **out);
 
 /* Mine `count` independent queries (dbs[i], minsup[i], M[i]) together: all
  * lattices advance one stop per round and every count phase of a round is

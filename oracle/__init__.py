@@ -14,6 +14,9 @@ Every function wraps a plain serial routine of ``dic_oracle.cpp``:
   * :func:`pack`         BitMask of Section 4.1
   * :func:`rules`        association rules from frequent itemsets (Section 1's
                          second subtask), plain Python loops
+  * :func:`paralleldic`  the paper's own parallel design on the host cores
+                         (``paralleldic_omp.cpp``, OpenMP): the benchmark's
+                         multi-core CPU baseline, pinned to :func:`dic`
 Results are lists of ``(items_tuple, support)`` in canonical order (size, then
 lexicographic), plus a per-stop trace for the DIC forms.
 
@@ -33,6 +36,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dic_oracle.cpp")
 _LIB = os.path.join(_HERE, "_oracle.so")
 _lib = None
+_PSRC = os.path.join(_HERE, "paralleldic_omp.cpp")
+_PLIB = os.path.join(_HERE, "_paralleldic.so")
+_plib = None
 
 TRACE_COLUMNS = ("step", "stop", "first", "last", "dashed", "promoted", "pruned", "generated",
                  "solidified")
@@ -45,6 +51,68 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_paralleldic(force: bool = False) -> str:
+    """Compile paralleldic_omp.cpp into _paralleldic.so (g++ -O3 -fopenmp)."""
+    if force or not os.path.exists(_PLIB) or os.path.getmtime(_PLIB) < os.path.getmtime(_PSRC):
+        tmp = _PLIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O3", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _PSRC,
+                               "-o", tmp])
+        os.replace(tmp, _PLIB)
+    return _PLIB
+
+
+def _pload():
+    global _plib
+    if _plib is None:
+        lib = ctypes.CDLL(build_paralleldic())
+        u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+        lib.pdic_mine.argtypes = [vp, vp, u64, u32, u32, u64, u64, ctypes.c_int,
+                                  ctypes.POINTER(vp)]
+        lib.pdic_mine.restype = ctypes.c_int
+        for name in ("pdic_result_count", "pdic_result_nitems", "pdic_result_trace_len",
+                     "pdic_result_tests"):
+            f = getattr(lib, name)
+            f.argtypes = [vp]
+            f.restype = u64
+        lib.pdic_result_threads.argtypes = [vp]
+        lib.pdic_result_threads.restype = ctypes.c_int
+        lib.pdic_result_copy.argtypes = [vp, vp, vp, vp]
+        lib.pdic_result_trace.argtypes = [vp, vp]
+        lib.pdic_result_free.argtypes = [vp]
+        _plib = lib
+    return _plib
+
+
+def paralleldic(row_ptr, items, n: int, m: int, minsup: int, M: int, max_stops: int = 0,
+                threads: int = 0):
+    """ParallelDIC with OpenMP on `threads` host threads (0 = all): Algorithm
+    2 with the loop interchange and nested balancing of Algorithm 3 (Figures
+    2-3), the same readings as :func:`dic`. Returns (OracleResult, threads)."""
+    lib = _pload()
+    rp, it = _csr(row_ptr, items)
+    h = ctypes.c_void_p()
+    if lib.pdic_mine(rp.ctypes.data, it.ctypes.data, n, m, minsup, M, max_stops, threads,
+                     ctypes.byref(h)) != 0:
+        raise ValueError("paralleldic: invalid arguments")
+    cnt = lib.pdic_result_count(h)
+    nit = lib.pdic_result_nitems(h)
+    k = np.zeros(max(cnt, 1), dtype=np.uint32)
+    items_out = np.zeros(max(nit, 1), dtype=np.uint32)
+    sp = np.zeros(max(cnt, 1), dtype=np.uint64)
+    lib.pdic_result_copy(h, k.ctypes.data, items_out.ctypes.data, sp.ctypes.data)
+    out, p = [], 0
+    for i in range(cnt):
+        out.append((tuple(int(x) for x in items_out[p:p + k[i]]), int(sp[i])))
+        p += int(k[i])
+    tl = lib.pdic_result_trace_len(h)
+    tr = np.zeros((max(tl, 1), len(TRACE_COLUMNS)), dtype=np.uint64)
+    lib.pdic_result_trace(h, tr.ctypes.data)
+    res = OracleResult(out, tr[:tl], int(lib.pdic_result_tests(h)), 0)
+    used = int(lib.pdic_result_threads(h))
+    lib.pdic_result_free(h)
+    return res, used
 
 
 def _load():

@@ -7,8 +7,8 @@ module (``paper_1812_10959_gb300.build``) can be imported before libdic.so
 exists; using the binding without the library raises ImportError."""
 import importlib
 
-_EXPORTS = ("Database", "DicError", "Result", "Server", "load_db", "load_db_csr",
-            "load_db_device", "mine", "mine_batch", "minsup_count", "rules")
+_EXPORTS = ("Database", "DicError", "MineJob", "Result", "Server", "load_db", "load_db_csr",
+            "load_db_device", "mine", "mine_async", "mine_batch", "minsup_count", "rules")
 __all__ = list(_EXPORTS) + ["dic"]
 
 

@@ -394,6 +394,7 @@ class Miner {
   // CUDA graphs: one captured stop per variant, replayed stop after stop
   struct StopGraph {
     int path = 0, kre = 0;
+    uint32_t nstops = 1;  // stops captured back to back in this graph
     bool gram = false, slice = false, direct = false;
     uint32_t profile = 0;  // DIC_PROFILE_* bits captured as event nodes
     uint32_t nw = 0;
@@ -407,8 +408,11 @@ class Miner {
   };
   std::vector<StopGraph> graphs_;
   uint64_t lat_version_ = 1;  // bumped whenever a buffer of the lattice changes
-  dic_status launch_stop();   // one stop: graph replay or direct launches
+  // `nstops` stops: one graph replay (captured once per shape) or direct
+  // launches
+  dic_status launch_stop(uint32_t nstops = 1);
   int grid_ = 0;
+  int gen_grid_ = 0;  // MAKECANDIDATES CTAs when no transposition rides along
   uint32_t launches_ = 0;
   uint32_t path_launches_[4] = {0, 0, 0, 0};
   uint64_t candidates_cap_limit_ = 0xFFFFFFF0ull;
@@ -595,7 +599,8 @@ dic_status Miner::launch_phase(int phase) {
       const bool fast = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
       if (prof(DIC_PROFILE_GEN)) TRY(iv_open(IV_GEN, s_));
       // (with double-buffered or staged columns the next block is ready)
-      e = launch_generate_finish(L_, grid_, fast && !L_.vdouble && !L_.vall, s_);
+      e = launch_generate_finish(L_, L_.vall ? gen_grid_ : grid_, fast && !L_.vdouble && !L_.vall,
+                                 s_);
       if (prof(DIC_PROFILE_GEN)) TRY(iv_close(s_));
       next_v_ready_ = fast;
       ++pred_step_;
@@ -643,6 +648,7 @@ dic_status Miner::grow_candidates(uint32_t need) {
   TRY(alloc(&N.cranks, (size_t)ncap * KRMAX));
   TRY(alloc(&N.cpromo, ncap));
   TRY(alloc(&N.newbox, ncap));
+  TRY(alloc(&N.newinfo, ncap));
   TRY(alloc(&N.newhash, ncap));
   CU(cudaMemcpyAsync(N.cpromo, L_.cpromo, (size_t)keep * 4, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.ck, L_.ck, (size_t)keep, cudaMemcpyDeviceToDevice, s_));
@@ -652,8 +658,10 @@ dic_status Miner::grow_candidates(uint32_t need) {
   CU(cudaMemcpyAsync(N.cbirth, L_.cbirth, (size_t)keep * 4, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.cshape, L_.cshape, (size_t)keep, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.newbox, L_.newbox, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s_));
+  CU(cudaMemcpyAsync(N.newinfo, L_.newinfo, (size_t)nb * 8, cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.newhash, L_.newhash, (size_t)nb * 8, cudaMemcpyDeviceToDevice, s_));
   drop(L_.cmask); drop(L_.csupp); drop(L_.cbirth); drop(L_.cshape); drop(L_.newbox);
+  drop(L_.newinfo);
   drop(L_.newhash); drop(L_.ck); drop(L_.cranks); drop(L_.cpromo);
   L_ = N;
   ++lat_version_;
@@ -716,6 +724,7 @@ dic_status Miner::begin() {
   res_->W = db_->W;
   res_->stats.words = db_->W;
   grid_ = sm_count() * 4;
+  gen_grid_ = sm_count() * 2;
   if (n_ == 0) return DIC_OK;
   if (M_ > n_) M_ = n_;
   stop_max64_ = (n_ + M_ - 1) / M_;
@@ -846,6 +855,7 @@ dic_status Miner::prepare() {
     TRY(alloc(&L_.cranks, (size_t)cap * KRMAX));
     TRY(alloc(&L_.cpromo, cap));
     TRY(alloc(&L_.newbox, cap));
+    TRY(alloc(&L_.newinfo, cap));
     TRY(alloc(&L_.newhash, cap));
     L_.hcap = 1u << 12;
     while ((uint64_t)L_.hcap < npairs * 4 && L_.hcap < (1u << 31)) L_.hcap <<= 1;
@@ -964,6 +974,9 @@ dic_status Miner::prepare() {
 
 // ---- phase 3: the stop loop of Algorithm 2 for this query alone
 // Stops the newest cohort still needs (more may follow if cohorts appear).
+// Stops captured into one graph where the loop allows it.
+constexpr uint32_t kStopsPerGraph = 8;
+
 static uint32_t stops_needed(const Ctrl &c, uint32_t stop_max, uint32_t cap) {
   const uint64_t end = (uint64_t)c.last_birth + stop_max + 1;
   const uint64_t need = end > c.step ? end - c.step : 1;
@@ -1040,10 +1053,13 @@ dic_status Miner::recover() {
   return DIC_OK;
 }
 
-dic_status Miner::launch_stop() {
+dic_status Miner::launch_stop(uint32_t nstops) {
   prof_now_ = (opt_.profile_every <= 1 || pred_step_ % opt_.profile_every == 0) ? opt_.profile
                                                                                : 0u;
-  if (!opt_.use_graph) return launch_stop_from(PH_COUNT);
+  if (!opt_.use_graph) {
+    for (uint32_t i = 0; i < nstops; ++i) TRY(launch_stop_from(PH_COUNT));
+    return DIC_OK;
+  }
   const bool fast = cur_path_ == DIC_COUNT_BITSLICE || cur_path_ == DIC_COUNT_TENSOR;
   StopGraph key;
   key.path = cur_path_;
@@ -1054,10 +1070,11 @@ dic_status Miner::launch_stop() {
   key.nw = cur_path_ == DIC_COUNT_ROWS ? nw_ : 0;
   key.profile = prof_now_;
   key.version = lat_version_;
+  key.nstops = nstops;
   StopGraph *sg = nullptr;
   for (auto &g : graphs_)
     if (g.path == key.path && g.gram == key.gram && g.slice == key.slice && g.kre == key.kre &&
-        g.direct == key.direct &&
+        g.direct == key.direct && g.nstops == key.nstops &&
         g.nw == key.nw && g.profile == key.profile && g.version == key.version)
       sg = &g;
   const uint32_t pred0 = pred_step_;
@@ -1075,7 +1092,8 @@ dic_status Miner::launch_stop() {
     std::memcpy(p0, path_launches_, sizeof p0);
     const bool v0 = next_v_ready_;
     CU(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal));
-    dic_status st = launch_stop_from(PH_COUNT);
+    dic_status st = DIC_OK;
+    for (uint32_t i = 0; i < nstops && st == DIC_OK; ++i) st = launch_stop_from(PH_COUNT);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(s_, &graph);
     cudaError_t ie = cudaErrorUnknown;
@@ -1091,7 +1109,8 @@ dic_status Miner::launch_stop() {
       next_v_ready_ = v0;
       pred_step_ = pred0;
       opt_.use_graph = 0;
-      return launch_stop_from(PH_COUNT);
+      for (uint32_t i = 0; i < nstops; ++i) TRY(launch_stop_from(PH_COUNT));
+      return DIC_OK;
     }
     key.graph = graph;
     key.kernels = launches_ - l0;
@@ -1142,7 +1161,7 @@ dic_status Miner::launch_stop() {
   launches_ += sg->kernels;
   for (int i = 0; i < 4; ++i) path_launches_[i] += sg->path_counts[i];
   next_v_ready_ = fast;
-  pred_step_ = pred0 + 1;
+  pred_step_ = pred0 + nstops;
   return DIC_OK;
 }
 
@@ -1170,7 +1189,24 @@ dic_status Miner::loop() {
       direct_ = opt_.count_form == 2 ||
                 (opt_.count_form == 0 && c.tail - lo <= BS_DIRECT_HOST_MAX);
     }
-    for (uint32_t i = 0; i < group; ++i) TRY(launch_stop());
+    // with staged columns and no per-stop host state, runs of stops are
+    // captured together (stops without profiling events only)
+    const bool multi = L_.vall && opt_.use_graph && (cur_path_ != DIC_COUNT_TENSOR ||
+                                                     L_.pair_events);
+    for (uint32_t i = 0; i < group;) {
+      // the run ends before the next stop that carries profiling events
+      uint32_t u = 1;
+      if (multi) {
+        const uint32_t cap = std::min<uint32_t>(kStopsPerGraph, group - i);
+        u = 0;
+        while (u < cap && !(opt_.profile && (opt_.profile_every <= 1 ||
+                                             (pred_step_ + u) % opt_.profile_every == 0)))
+          ++u;
+        if (u == 0) u = 1;  // the profiled stop itself, alone
+      }
+      TRY(launch_stop(u));
+      i += u;
+    }
     TRY(sync_ctrl());
     TRY(recover());
   }
@@ -1318,14 +1354,24 @@ extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint6
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != db->device) cudaSetDevice(db->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  bool own = false;
-  if (!s) {
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      if (prev != db->device) cudaSetDevice(prev);
-      return fail(DIC_ECUDA, "stream creation failed");
-    }
-    own = true;
+  // The mine runs on a stream of its own (it captures graphs there, which a
+  // stream shared with other host threads would not allow), ordered after
+  // the caller's stream by an event and rejoining it at the end.
+  cudaStream_t s = nullptr, user = (cudaStream_t)stream;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess && user) {
+    e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in, 0);
+  }
+  if (e != cudaSuccess) {
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (s) cudaStreamDestroy(s);
+    if (prev != db->device) cudaSetDevice(prev);
+    return fail(DIC_ECUDA, "stream setup: %s", cudaGetErrorString(e));
   }
   const_cast<dic_db *>(db)->busy.fetch_add(1);
   dic_status st;
@@ -1334,8 +1380,14 @@ extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint6
     st = mn.run(out);
   }
   if (st != DIC_OK) cudaStreamSynchronize(s);
+  if (user) {  // the caller's later work waits for the mine
+    cudaEventRecord(ev_out, s);
+    cudaStreamWaitEvent(user, ev_out, 0);
+    cudaEventDestroy(ev_in);
+    cudaEventDestroy(ev_out);
+  }
   const_cast<dic_db *>(db)->busy.fetch_sub(1);
-  if (own) cudaStreamDestroy(s);
+  cudaStreamDestroy(s);
   if (prev != db->device) cudaSetDevice(prev);
   return st;
 }
@@ -1343,6 +1395,78 @@ extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint6
 extern "C" dic_status dic_mine(const dic_db *db, uint32_t minsup_count, uint64_t M,
                                dic_result **out) {
   return dic_mine_ex(db, minsup_count, M, nullptr, nullptr, out);
+}
+
+// ------------------------------------------------------------ async mining
+// A mine whose host side (the group loop of Algorithm 2: enqueue stops, read
+// the loop state back, grow buffers) runs on a worker thread of its own, so
+// the caller gets control back at once and several mines can be in flight on
+// different streams.
+struct dic_mine_job {
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool finished = false;
+  dic_status status = DIC_OK;
+  std::string error;
+  dic_result *result = nullptr;
+};
+
+extern "C" dic_status dic_mine_async(const dic_db *db, uint32_t minsup_count, uint64_t M,
+                                     const dic_options *opt, void *stream, dic_mine_job **out) {
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!db) return fail(DIC_EINVAL, "db is NULL");
+  if (minsup_count == 0) return fail(DIC_EINVAL, "minsup_count must be >= 1");
+  if (M == 0) return fail(DIC_EINVAL, "M must be >= 1");
+  dic_options o;
+  dic_options_init(&o);
+  if (opt) std::memcpy(&o, opt, std::min<size_t>(sizeof o, opt->struct_size ? opt->struct_size : sizeof o));
+  TRY(check_options(o));
+  std::unique_ptr<dic_mine_job> job(new (std::nothrow) dic_mine_job());
+  if (!job) return fail(DIC_ENOMEM, "host allocation");
+  dic_mine_job *j = job.get();
+  const_cast<dic_db *>(db)->busy.fetch_add(1);  // held until the worker ends
+  try {
+    j->worker = std::thread([j, db, minsup_count, M, o, stream]() {
+      cudaSetDevice(db->device);
+      dic_result *res = nullptr;
+      const dic_status st = dic_mine_ex(db, minsup_count, M, &o, stream, &res);
+      const std::string err = st == DIC_OK ? std::string() : std::string(dic_last_error());
+      const_cast<dic_db *>(db)->busy.fetch_sub(1);
+      std::lock_guard<std::mutex> lk(j->mu);
+      j->status = st;
+      j->error = err;
+      j->result = res;
+      j->finished = true;
+      j->cv.notify_all();
+    });
+  } catch (...) {
+    const_cast<dic_db *>(db)->busy.fetch_sub(1);
+    return fail(DIC_ENOMEM, "could not start the mining thread");
+  }
+  *out = job.release();
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_mine_wait(dic_mine_job *job, int64_t timeout_ms, dic_result **out) {
+  if (!job || !out) return fail(DIC_EINVAL, "NULL argument");
+  *out = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(job->mu);
+    auto ready = [&] { return job->finished; };
+    if (timeout_ms < 0) job->cv.wait(lk, ready);
+    else if (!job->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+      return fail(DIC_ETIMEOUT, "mining job not finished after %lld ms", (long long)timeout_ms);
+  }
+  job->worker.join();
+  const dic_status st = job->status;
+  dic_result *res = job->result;
+  const std::string err = job->error;
+  delete job;
+  if (st != DIC_OK) return fail(st, "%s", err.c_str());
+  *out = res;
+  return DIC_OK;
 }
 
 

@@ -29,16 +29,80 @@ constexpr uint8_t KSKIP = 255;
 // record to be promoted. Reads only values no count kernel changes, so all
 // CTAs of a launch decide alike. `report` lets one thread raise the stall.
 template <int KRE>
-__device__ __forceinline__ bool bs_checks(const Lattice &L, Ctrl *C, bool report) {
-  if (C->max_k > (uint32_t)KRE) {
+__device__ __forceinline__ bool bs_checks_v(const Lattice &L, Ctrl *C, uint32_t max_k,
+                                            uint32_t hash_used, uint32_t n_live, bool report) {
+  if (max_k > (uint32_t)KRE) {
     if (report && threadIdx.x == 0) C->stall = ST_WIDTH;
     return false;
   }
-  if ((uint64_t)(C->hash_used + C->n_live) * 2 > L.hcap) {
+  if ((uint64_t)(hash_used + n_live) * 2 > L.hcap) {
     if (report && threadIdx.x == 0) C->stall = ST_HASH_COUNT;
     return false;
   }
   return true;
+}
+template <int KRE>
+__device__ __forceinline__ bool bs_checks(const Lattice &L, Ctrl *C, bool report) {
+  return bs_checks_v<KRE>(L, C, C->max_k, C->hash_used, C->n_live, report);
+}
+
+// The loop-state fields a stop kernel decides on, read in one round of
+// independent loads (none of them changes while a count kernel runs).
+struct StopState {
+  uint32_t stall, done, step, head, tail, max_k, hash_used, n_live;
+};
+__device__ __forceinline__ StopState load_stop_state(const Ctrl *C) {
+  StopState s;
+  s.stall = C->stall; s.done = C->done; s.step = C->step; s.head = C->head;
+  s.tail = C->tail; s.max_k = C->max_k; s.hash_used = C->hash_used; s.n_live = C->n_live;
+  return s;
+}
+
+// The same, read by one thread per CTA and broadcast through shared memory
+// together with the stop's pair-event range (lines every warp of a large
+// grid would otherwise request from L2 at once, which serialises there).
+// ev[0..2] = first and end index of the stop's promoted pairs and the
+// number of pairs dropped at the stop (zeros without pair events). The
+// whole CTA must call this.
+__device__ __forceinline__ StopState cta_stop_state(const Lattice &L, const Ctrl *C,
+                                                    uint32_t ev[3]) {
+  __shared__ StopState s_st;
+  __shared__ uint32_t s_ev[3];
+  if (threadIdx.x == 0) {
+    const StopState st = load_stop_state(C);
+    // both slots, loaded with the rest (no load waits on the stop number)
+    uint32_t es[2], en[6];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) es[i] = C->ev_stop[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) en[i] = C->ev_next[i];
+    uint32_t e0 = 0, e1 = 0, e2 = 0;
+    if (L.pair_events && st.step <= L.stop_max && !st.stall && !st.done) {
+      const uint32_t sl = st.step & 1u;
+      if (es[sl] == st.step) {  // set by the previous stop's count
+        e0 = en[3 * sl]; e1 = en[3 * sl + 1]; e2 = en[3 * sl + 2];
+      } else {
+        e0 = L.ev_off[st.step];
+        e1 = L.ev_off[st.step + 1];
+        e2 = L.ev_pruned[st.step];
+      }
+    }
+    s_st = st;
+    s_ev[0] = e0; s_ev[1] = e1; s_ev[2] = e2;
+  }
+  __syncthreads();
+  ev[0] = s_ev[0]; ev[1] = s_ev[1]; ev[2] = s_ev[2];
+  return s_st;
+}
+
+// One thread of the count kernel of stop g records the next stop's pair
+// event range in the loop state (off the critical path of that stop).
+__device__ __forceinline__ void stage_next_events(const Lattice &L, Ctrl *C, uint32_t g) {
+  if (!L.pair_events || g + 1 > L.stop_max) return;
+  const uint32_t e0 = L.ev_off[g + 1], e1 = L.ev_off[g + 2], e2 = L.ev_pruned[g + 1];
+  const uint32_t sl = (g + 1) & 1u;
+  C->ev_next[3 * sl] = e0; C->ev_next[3 * sl + 1] = e1; C->ev_next[3 * sl + 2] = e2;
+  C->ev_stop[sl] = g + 1;
 }
 
 // 32-row words and tiles of stop g's block; false (error recorded) if they
@@ -100,16 +164,34 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
 #pragma unroll
     for (int q = 0; q < KRE; ++q)
       r[q] = (uint32_t)q < k ? (rw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu : 0u;
+    // 16-byte loads: lane j takes words 4j .. 4j+3 of every rank column
+    // (a tile row holds TW = 4, 8 or 16 words, so the four share a tile;
+    // words past the block's rows are zero in the buffer). UJ loads per
+    // rank are issued before any AND.
+    constexpr uint32_t UJ = 4;
+    const uint32_t nv = (nw32 + 3) / 4;
     uint32_t cnt = 0;
-#pragma unroll 8
-    for (uint32_t w = lane; w < nw32; w += 32) {
-      const uint32_t tb = (w / TW) * l1p;
-      const uint32_t wi = w % TW;
-      uint32_t acc = __ldg(V + (uint64_t)(tb + r[0]) * ST + wi);
+    for (uint32_t j0 = 0; j0 < nv; j0 += 32 * UJ) {
+      uint4 acc[UJ];
 #pragma unroll
-      for (int q = 1; q < KRE; ++q)
-        if ((uint32_t)q < k) acc &= __ldg(V + (uint64_t)(tb + r[q]) * ST + wi);
-      cnt += __popc(acc);
+      for (uint32_t u = 0; u < UJ; ++u) {
+        const uint32_t j = j0 + 32 * u + lane;
+        const uint32_t w = 4 * j;
+        const uint64_t base = (uint64_t)(w / TW) * l1p;
+        const uint32_t wi = w % TW;
+        acc[u] = j < nv ? __ldg(reinterpret_cast<const uint4 *>(V + (base + r[0]) * ST + wi))
+                        : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int q = 1; q < KRE; ++q) {
+          if ((uint32_t)q < k && j < nv) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(V + (base + r[q]) * ST + wi));
+            acc[u].x &= x.x; acc[u].y &= x.y; acc[u].z &= x.z; acc[u].w &= x.w;
+          }
+        }
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < UJ; ++u)
+        cnt += __popc(acc[u].x) + __popc(acc[u].y) + __popc(acc[u].z) + __popc(acc[u].w);
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
     if (lane == 0) {

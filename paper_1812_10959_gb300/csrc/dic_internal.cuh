@@ -50,6 +50,13 @@ struct Ctrl {
   uint32_t blocks_done;  // ticket of the generate kernel's last-block step
   uint32_t last_birth;   // creation stop of the newest cohort
   uint32_t solo;         // 1: the batched kernels leave this query alone
+  uint32_t head_birth;   // creation stop of the oldest cohort in the window
+  // pair events of stop ev_stop[s] in slot s = stop % 2 (set one stop ahead
+  // by the count kernel, for stop 1 by the event build; the slot a stop
+  // reads is never the one its own count kernel writes): first and end
+  // index into ev_list and the pairs dropped at that stop
+  uint32_t ev_stop[2];
+  uint32_t ev_next[6];
   unsigned long long tests;  // candidate-transaction tests so far
   unsigned long long work;   // algorithmic integer ops of the count kernels
   unsigned long long gram_rows;  // block rows whose pair cohort the GEMM counted
@@ -100,8 +107,10 @@ struct Lattice {
   uint8_t *ck;         // [cap] itemset size (saturates at 255)
   uint16_t *cranks;    // [cap][KRMAX] ascending ranks (first KRMAX of them)
   uint32_t *newbox;    // [cap] records promoted at this stop
+  uint64_t *newinfo;   // [cap] their size | first rank << 8 | second rank << 24
   uint64_t *newhash;   // [cap] hash pre-image sums of those records
-  uint32_t *cpromo;    // [cap] stop at which a box was promoted
+  uint32_t *cpromo;    // [cap] stop at which a box was promoted; ~0 while
+                       // the record is not a box (set at its creation)
   uint32_t cap;
   // box set: open addressing over record indices (slot = index + 1, 0 =
   // empty); keys are the records' masks, values their promotion stops

@@ -144,20 +144,23 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
   pdl_wait();
   pdl_trigger();
   Ctrl *C = L.ctrl;
-  if (C->stall || C->done) return;
-  if (!bs_checks<KRE>(L, C, blockIdx.x == 0)) return;
-  const uint32_t g = C->step;
+  uint32_t ev[3];
+  const StopState cs = cta_stop_state(L, C, ev);
+  if (cs.stall || cs.done) return;
+  if (!bs_checks_v<KRE>(L, C, cs.max_k, cs.hash_used, cs.n_live, blockIdx.x == 0)) return;
+  const uint32_t g = cs.step;
   uint32_t nw32, ntiles;
   if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
-  const uint32_t head = C->head, tail = C->tail;
+  const uint32_t head = cs.head, tail = cs.tail;
   // records below the pair cohort's end, while the tensor path has it, are
   // counted and pruned there; this kernel counts [lo, tail)
   const uint32_t lo = counted_lo(L, head, tail, g, true);
   const uint32_t ncand = tail - lo;
   uint32_t pruned = 0, solid = 0;
   unsigned long long work = 0;
-  apply_pair_events(L, C, g, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                    (uint64_t)gridDim.x * blockDim.x, pruned, solid);
+  apply_pair_events_range(L, C, g, ev, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                          (uint64_t)gridDim.x * blockDim.x, pruned, solid);
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) stage_next_events(L, C, g);
   if (ncand == 0) {
     block_add_tallies(C, pruned, solid, work);
     return;
@@ -191,17 +194,20 @@ __global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
   pdl_wait();
   pdl_trigger();
   Ctrl *C = L.ctrl;
-  if (C->stall || C->done) return;
-  if (!bs_checks<KRE>(L, C, blockIdx.x == 0)) return;
-  const uint32_t g = C->step;
+  uint32_t ev[3];
+  const StopState cs = cta_stop_state(L, C, ev);
+  if (cs.stall || cs.done) return;
+  if (!bs_checks_v<KRE>(L, C, cs.max_k, cs.hash_used, cs.n_live, blockIdx.x == 0)) return;
+  const uint32_t g = cs.step;
   uint32_t nw32, ntiles;
   if (!bs_block_tiles<TW>(L, C, g, &nw32, &ntiles)) return;
-  const uint32_t head = C->head, tail = C->tail;
+  const uint32_t head = cs.head, tail = cs.tail;
   const uint32_t lo = counted_lo(L, head, tail, g, true);
   uint32_t pruned = 0, solid = 0;
   unsigned long long work = 0;
-  apply_pair_events(L, C, g, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                    (uint64_t)gridDim.x * blockDim.x, pruned, solid);
+  apply_pair_events_range(L, C, g, ev, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                          (uint64_t)gridDim.x * blockDim.x, pruned, solid);
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) stage_next_events(L, C, g);
   if (lo < tail) bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid, work);
   block_add_tallies(C, pruned, solid, work);
 }

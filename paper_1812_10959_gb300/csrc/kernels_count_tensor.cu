@@ -424,6 +424,14 @@ __global__ void __launch_bounds__(1024) k_pair_events_scan(Lattice L, const uint
     ev_pruned[g] = hist[S + 2 + g];
     run += hist[g];
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // stop 1's range, read by its count kernel
+    Ctrl *C = L.ctrl;
+    C->ev_next[3] = ev_off[1];
+    C->ev_next[4] = ev_off[2];
+    C->ev_next[5] = ev_pruned[1];
+    C->ev_stop[1] = 1;
+  }
 }
 
 // The promoted pairs grouped by promotion stop (order within a stop is

@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(256) k_pair_join(Lattice L) {
       L.csupp[p] = 0;
       L.cbirth[p] = 0;
       L.cshape[p] = SH_CIRCLE;
+      L.cpromo[p] = ~0u;
       L.ck[p] = 2;
       uint4 *rk = reinterpret_cast<uint4 *>(L.cranks + p * KRMAX);
       rk[0] = make_uint4((uint32_t)a | ((uint32_t)b << 16), 0u, 0u, 0u);
@@ -232,6 +233,7 @@ __global__ void k_singleton_join(Lattice L) {
       L.csupp[r] = 0;
       L.cbirth[r] = 0;
       L.cshape[r] = SH_CIRCLE;
+      L.cpromo[r] = ~0u;
       L.ck[r] = 1;
       L.cranks[(uint64_t)r * KRMAX] = (uint16_t)r;
     }
@@ -272,9 +274,8 @@ __global__ void __launch_bounds__(256) k_promote(Lattice L) {
   const uint32_t g = C->step, tail = C->tail;
   const uint32_t head = counted_lo(L, C->head, tail, g, false);
   uint32_t pruned = 0, solid = 0;
-  // (k_hash_insert inserts this stop's new boxes, the pairs' included)
   apply_pair_events(L, C, g, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                    (uint64_t)gridDim.x * blockDim.x, pruned, solid, false);
+                    (uint64_t)gridDim.x * blockDim.x, pruned, solid);
   for (uint32_t c = head + blockIdx.x * blockDim.x + threadIdx.x; c < tail;
        c += gridDim.x * blockDim.x)
     settle_record(L, C, c, L.csupp[c], g, false, pruned, solid);
@@ -341,15 +342,28 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_ne
   pdl_wait();
   pdl_trigger();
   Ctrl *C = L.ctrl;
-  if (C->stall || C->done) return;
-  if (slice_next)  // the columns of stop g+1 (count of stop g is complete)
-    slice_block_warps(L, C->step + 1,
-                      (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
-                      (uint64_t)gridDim.x * (blockDim.x >> 5));
-  const uint32_t P = C->n_newbox;
-  const uint32_t g = C->step, base = C->tail, l1 = L.l1, wc = L.wc;
-  const uint64_t total = (uint64_t)P * l1;
+  // the fields this kernel decides on, read by one thread per CTA (every
+  // warp asking L2 for the same line at once would serialise there)
+  __shared__ uint32_t s_f[5];
+  if (threadIdx.x == 0) {
+    s_f[0] = C->stall; s_f[1] = C->done; s_f[2] = C->n_newbox; s_f[3] = C->step;
+    s_f[4] = C->tail;
+  }
+  __syncthreads();
+  const uint32_t P = s_f[2], g = s_f[3], base = s_f[4], l1 = L.l1;
+  if (s_f[0] || s_f[1]) return;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slice_next)  // the columns of stop g+1 (count of stop g is complete)
+    slice_block_warps(L, g + 1, tid >> 5, stride >> 5);
+  if (L.vall) {
+    // bring the next stop's columns into L2 ahead of its count (one
+    // 128-byte line per thread)
+    const uint32_t *nv = vcols(L, g + 1);
+    for (uint64_t i = tid * 32; i < L.vwords; i += stride * 32)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(nv + i));
+  }
+  const uint64_t total = (uint64_t)P * l1;
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
     gen_candidate(L, C, (uint32_t)(w / l1), (uint32_t)(w % l1), g, base);
   }

@@ -66,10 +66,15 @@ __device__ __forceinline__ uint32_t box_lookup(const Lattice &L, const uint64_t 
 // MAKECANDIDATES reads, and (when `insert`) the box set.
 __device__ __forceinline__ void promote_record(const Lattice &L, Ctrl *C, uint32_t c, uint32_t g,
                                                bool insert) {
+  // the size and first two ranks MAKECANDIDATES needs, loaded beside the
+  // slot reservation
+  const uint32_t k = L.ck[c];
+  const uint32_t r01 = *reinterpret_cast<const uint32_t *>(L.cranks + (uint64_t)c * KRMAX);
   L.cshape[c] = SH_BOX;
   L.cpromo[c] = g;
   const uint32_t at = atomicAdd(&C->n_newbox, 1u);
   L.newbox[at] = c;
+  L.newinfo[at] = (uint64_t)k | ((uint64_t)(r01 & 0xFFFFu) << 8) | ((uint64_t)(r01 >> 16) << 24);
   if (insert) {
     const uint64_t sum = mask_hash_sum(L.cmask + (uint64_t)c * L.wc, L.wc);
     L.newhash[at] = sum;
@@ -108,24 +113,37 @@ __device__ __forceinline__ void settle_record(const Lattice &L, Ctrl *C, uint32_
   settle_loaded(L, C, c, sh, L.cbirth[c], s, g, insert, pruned, solid);
 }
 
+// apply_pair_events (below) with the stop's event range already read
+// (ev[0..2] = first and end index into ev_list, pairs dropped at g); thread
+// 0 also adds the pair boxes completing their pass at stop_max.
+__device__ __forceinline__ void apply_pair_events_range(const Lattice &L, Ctrl *C, uint32_t g,
+                                                        const uint32_t ev[3], uint64_t tid,
+                                                        uint64_t nthreads, uint32_t &pruned,
+                                                        uint32_t &solid) {
+  if (!L.pair_events || g > L.stop_max) return;
+  for (uint64_t i = ev[0] + tid; i < ev[1]; i += nthreads)
+    promote_record(L, C, L.ev_list[i], g, false);
+  if (tid == 0) {
+    pruned += ev[2];
+    if (g == L.stop_max) solid += L.ev_pruned[0];
+  }
+}
+
 // Stop g's precomputed PRUNE outcome for the pair cohort (Lattice
 // pair_events): the pairs listed for g are promoted (box set insert, the
 // list MAKECANDIDATES reads); the pairs dropped by the bound at g, and at
 // stop_max the pair boxes completing their pass, are added to the caller's
 // tallies by thread 0. Threads tid = 0 .. nthreads-1 share the work.
-// `insert`: as for promote_record (false where a later kernel inserts the
-// stop's new boxes).
+// The pairs are not inserted into the box set: with the first pass's
+// lexicographic pair records (the only case with pair events),
+// MAKECANDIDATES reads a pair's shape and promotion stop from its record and
+// probes the box set only for subsets of three or more items.
 __device__ __forceinline__ void apply_pair_events(const Lattice &L, Ctrl *C, uint32_t g,
                                                   uint64_t tid, uint64_t nthreads,
-                                                  uint32_t &pruned, uint32_t &solid,
-                                                  bool insert = true) {
+                                                  uint32_t &pruned, uint32_t &solid) {
   if (!L.pair_events || g > L.stop_max) return;
-  const uint32_t a = L.ev_off[g], b = L.ev_off[g + 1];
-  for (uint64_t i = a + tid; i < b; i += nthreads) promote_record(L, C, L.ev_list[i], g, insert);
-  if (tid == 0) {
-    pruned += L.ev_pruned[g];
-    if (g == L.stop_max) solid += L.ev_pruned[0];
-  }
+  const uint32_t ev[3] = {L.ev_off[g], L.ev_off[g + 1], L.ev_pruned[g]};
+  apply_pair_events_range(L, C, g, ev, tid, nthreads, pruned, solid);
 }
 
 // MAKECANDIDATES for one (record promoted at g, rank r) pair: C = A | r is
@@ -144,20 +162,23 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
                                               uint32_t g, uint32_t base) {
   const uint32_t wc = L.wc;
   const uint32_t cA = L.newbox[p];
-  const uint32_t kA = L.ck[cA];
+  const uint64_t info = L.newinfo[p];
+  const uint32_t kA = (uint32_t)(info & 0xFFu);
   if (L.pairs_lex && kA >= 2) {
-    const uint32_t a0 = L.cranks[(uint64_t)cA * KRMAX], a1 = L.cranks[(uint64_t)cA * KRMAX + 1];
+    const uint32_t a0 = (uint32_t)(info >> 8) & 0xFFFFu, a1 = (uint32_t)(info >> 24) & 0xFFFFu;
     if (r == a0 || r == a1) return;  // r in A
     const uint64_t l1 = L.l1;
     const uint64_t i0 = r < a0 ? pair_record(r, a0, l1) : pair_record(a0, r, l1);
     const uint64_t i1 = r < a1 ? pair_record(r, a1, l1) : pair_record(a1, r, l1);
-    if (L.cshape[i0] != SH_BOX || L.cshape[i1] != SH_BOX) return;
+    // promotion stops (~0: not a box)
+    const uint32_t p0 = L.cpromo[i0], p1 = L.cpromo[i1];
+    if (p0 == ~0u || p1 == ~0u) return;
     if (kA == 2) {
       // A = {a0, a1}: the 2-subsets of C other than A are the pair records
       // {a1, r} = C \ {a0} and {a0, r} = C \ {a1}, both boxes by the check
       // above, so only the canonical-parent rule remains (no box-set probe)
-      if (a0 < r && L.cpromo[i1] == g) return;
-      if (a1 < r && L.cpromo[i0] == g) return;
+      if (a0 < r && p1 == g) return;
+      if (a1 < r && p0 == g) return;
       const uint32_t pos = base + atomicAdd(&C->n_gen, 1u);
       if (pos >= L.cap) {
         C->stall = ST_CAND;
@@ -177,6 +198,7 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
       L.csupp[pos] = 0;
       L.cbirth[pos] = g;
       L.cshape[pos] = SH_CIRCLE;
+      L.cpromo[pos] = ~0u;
       L.ck[pos] = 3;
       atomicMax(&C->max_k, 3u);
       return;
@@ -218,6 +240,7 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
   L.csupp[pos] = 0;
   L.cbirth[pos] = g;
   L.cshape[pos] = SH_CIRCLE;
+  L.cpromo[pos] = ~0u;
   L.ck[pos] = (uint8_t)(k + 1 < 255 ? k + 1 : 255);
   atomicMax(&C->max_k, k + 1);
 }
@@ -255,11 +278,17 @@ __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
   // window (a cohort born now never does: its birth + stop_max > g)
   // (head = the first remaining cohort's start; the new cohort, if any,
   // starts at the old tail, and so does an empty window)
-  uint32_t ch = c.cohort_head, head = c.tail;
-  while (ch < c.n_cohorts) {
-    const uint32_t birth = L.cohort_birth[ch], start = L.cohort_start[ch];
-    if (birth + L.stop_max > g) { head = start; break; }
-    ++ch;
+  // (the oldest live cohort's birth is kept in the loop state, so a stop
+  // that retires nothing reads no cohort record)
+  uint32_t ch = c.cohort_head, head = c.head, hb = c.head_birth;
+  if (hb + L.stop_max <= g) {
+    head = c.tail;  // every old cohort retired: the window starts at the new one
+    hb = g;
+    while (ch < c.n_cohorts) {
+      const uint32_t birth = L.cohort_birth[ch], start = L.cohort_start[ch];
+      if (birth + L.stop_max > g) { head = start; hb = birth; break; }
+      ++ch;
+    }
   }
   C->tests = c.tests + (unsigned long long)c.n_live * (last - first);
   C->n_cohorts = n_cohorts;
@@ -268,6 +297,7 @@ __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
   C->n_live = n_live;
   C->cohort_head = ch;
   C->head = head;
+  C->head_birth = hb;
   C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->n_gen = 0;
   C->n_trace = c.n_trace + 1;
   C->step = g + 1;

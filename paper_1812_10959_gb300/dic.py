@@ -83,6 +83,8 @@ def _load():
         "dic_mine": ([vp, u32, u64, pvp], i32),
         "dic_mine_ex": ([vp, u32, u64, ctypes.POINTER(Options), vp, pvp], i32),
         "dic_mine_batch": ([vp, vp, vp, u32, ctypes.POINTER(Options), vp], i32),
+        "dic_mine_async": ([vp, u32, u64, ctypes.POINTER(Options), vp, pvp], i32),
+        "dic_mine_wait": ([vp, ctypes.c_int64, pvp], i32),
         "dic_result_count": ([vp], u64),
         "dic_result_words": ([vp], u32),
         "dic_result_copy": ([vp, vp, vp, vp], i32),
@@ -297,6 +299,46 @@ def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
     _check(_lib.dic_mine_ex(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
                             ctypes.byref(h)))
     return _result(h)
+
+
+class MineJob:
+    """A mine running on the library's worker thread (dic_mine_async)."""
+
+    def __init__(self, handle, db):
+        self._h = handle
+        self._db = db  # kept alive while the job runs
+
+    def wait(self, timeout_ms: int = -1) -> Result:
+        """The result; DicError(DIC_ETIMEOUT) if not finished in time (the
+        job can be waited again)."""
+        if not self._h:
+            raise DicError(DIC_EINVAL, "job already waited")
+        h = ctypes.c_void_p()
+        rc = _lib.dic_mine_wait(self._h, timeout_ms, ctypes.byref(h))
+        if rc == DIC_ETIMEOUT:
+            _check(rc)
+        self._h = None
+        _check(rc)
+        return _result(h)
+
+    def __del__(self):
+        try:
+            if self._h:
+                h = ctypes.c_void_p()
+                if _lib.dic_mine_wait(self._h, -1, ctypes.byref(h)) == DIC_OK:
+                    _lib.dic_result_free(h)
+        except Exception:
+            pass
+
+
+def mine_async(db: Database, minsup: int, M: int, stream=None, **kw) -> MineJob:
+    """Start a mine on the library's worker thread (dic_mine_async); the
+    keyword arguments are those of mine()."""
+    o = options(**kw)
+    h = ctypes.c_void_p()
+    _check(_lib.dic_mine_async(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
+                               ctypes.byref(h)))
+    return MineJob(h, db)
 
 
 def mine_batch(dbs, minsups, Ms, path: str = "auto", profile=False, tile_words: int = 0,

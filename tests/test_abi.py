@@ -29,7 +29,8 @@ def libpath():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("dic_load_db", "dic_load_db_csr", "dic_load_db_device", "dic_mine",
-                 "dic_mine_ex", "dic_mine_batch", "dic_result_copy", "dic_result_trace",
+                 "dic_mine_ex", "dic_mine_async", "dic_mine_wait", "dic_mine_batch",
+                 "dic_result_copy", "dic_result_trace",
                  "dic_db_free", "dic_result_free", "dic_last_error"):
         assert must in names
 
