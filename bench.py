@@ -115,7 +115,9 @@ def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=No
                     peak_source=f"{pk['source']} bf16 burst x {FP8_PER_BF16} (fp8 e4m3)",
                     flops_per_launch=flops, **common)
     if kind == "count":
-        ops = sum(s["count_ops"] for s in stats) / max(nl, 1)
+        # work of the launches the events bracketed (the stops whose count
+        # kernel was timed), per launch
+        ops = sum(s["count_ops_timed"] for s in stats) / max(nl, 1)
         ach = ops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
         pl = st["path_launches"]
         kern = COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])]
@@ -575,8 +577,8 @@ def main():
             # the dominant kernel kind is bracketed by events inside the step,
             # on one stop in PROFILE_EVERY (each timed stop adds two event
             # records to its graph)
-            res = dic.mine(handle, db.minsup, db.M, **kw, stream=stream, profile=kind,
-                           profile_every=PROFILE_EVERY)
+            res = dic.mine(handle, db.minsup, db.M, **kw, stream=stream,
+                           profile=[kind, "gram"], profile_every=PROFILE_EVERY)
             b.record(stream)
             evs.append((a, b))
             stats.append(res.stats)
@@ -619,6 +621,10 @@ def main():
         alu_peak = None
     roofline = roofline_of(kind, stats, shares_ms, sum(ms), db, kw.get("count_form", "auto"),
                            res.trace, alu_peak)
+    # the pair-cohort GEMM (one launch per mine when the pass is staged) is
+    # timed in every step as well
+    roofline_gram = (roofline_of("gram", stats, shares_ms, sum(ms), db) if kind != "gram" and
+                     sum(s["gram_launches"] for s in stats) else None)
 
     cpu = pdic = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -646,6 +652,7 @@ def main():
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "roofline": roofline,
+            "roofline_gram": roofline_gram,
             "autotune": ({"choice": tuned.kwargs(), "candidates_s": tuned.timings}
                          if tuned else None),
             "cpu_baseline": cpu,

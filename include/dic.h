@@ -151,7 +151,15 @@ typedef struct {
   uint64_t gen_launches;    /* generate/finish kernels timed               */
   uint64_t gram_flops;      /* algorithmic tensor work: 2 * pairs * rows
                                summed over the stops counted by the GEMM   */
-  uint64_t reserved[5];
+  uint64_t count_ops_timed; /* count_ops of the stops whose count kernel was
+                               timed (DIC_PROFILE_COUNT, profile_every)    */
+  double setup_ms;          /* host wall time from the call to the first
+                               stop being enqueued                         */
+  double graph_ms;          /* host time spent capturing and instantiating
+                               stop graphs                                 */
+  double collect_ms;        /* host wall time from the last stop's check to
+                               the result being ready                      */
+  uint64_t reserved[1];
 } dic_stats;
 
 /* Columns of one trace row (one per iteration of Algorithm 2's loop). */

@@ -82,6 +82,91 @@ struct dic_result {
   dic_stats stats{};
 };
 
+// Page-locked host blocks are kept for reuse by later calls: allocating and
+// releasing them (cudaMallocHost / cudaFreeHost) costs far more than a mine's
+// own device work at small sizes. Blocks are reused by size class (powers of
+// two from 256 bytes) and live until the process exits.
+namespace {
+std::mutex g_pinned_mu;
+std::unordered_map<size_t, std::vector<void *>> g_pinned_free;
+size_t pinned_class(size_t bytes) {
+  size_t c = 256;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+}  // namespace
+
+static cudaError_t pinned_alloc(void **p, size_t bytes) {
+  const size_t c = pinned_class(bytes);
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned_free.find(c);
+    if (it != g_pinned_free.end() && !it->second.empty()) {
+      *p = it->second.back();
+      it->second.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost(p, c);
+}
+
+static void pinned_free(void *p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free[pinned_class(bytes)].push_back(p);
+}
+
+// Graphs and events of finished mines are destroyed by a later call, after
+// it has started its first-pass kernel (the destruction then overlaps device
+// work instead of delaying the finished mine's result).
+namespace {
+std::mutex g_retire_mu;
+std::vector<std::pair<cudaGraphExec_t, cudaGraph_t>> g_retired_graphs;
+std::vector<cudaEvent_t> g_retired_events;
+// Streams of finished calls, for reuse (one call at a time per stream).
+std::mutex g_stream_mu;
+std::vector<std::pair<int, cudaStream_t>> g_free_streams;
+}  // namespace
+
+static void retire_graph(cudaGraphExec_t e, cudaGraph_t g) {
+  std::lock_guard<std::mutex> lk(g_retire_mu);
+  g_retired_graphs.push_back({e, g});
+}
+static void retire_event(cudaEvent_t e) {
+  std::lock_guard<std::mutex> lk(g_retire_mu);
+  g_retired_events.push_back(e);
+}
+static void drain_retired() {
+  std::vector<std::pair<cudaGraphExec_t, cudaGraph_t>> gs;
+  std::vector<cudaEvent_t> es;
+  {
+    std::lock_guard<std::mutex> lk(g_retire_mu);
+    gs.swap(g_retired_graphs);
+    es.swap(g_retired_events);
+  }
+  for (auto &p : gs) {
+    if (p.first) cudaGraphExecDestroy(p.first);
+    if (p.second) cudaGraphDestroy(p.second);
+  }
+  for (cudaEvent_t e : es) cudaEventDestroy(e);
+}
+static cudaError_t take_stream(int dev, cudaStream_t *s) {
+  {
+    std::lock_guard<std::mutex> lk(g_stream_mu);
+    for (size_t i = 0; i < g_free_streams.size(); ++i)
+      if (g_free_streams[i].first == dev) {
+        *s = g_free_streams[i].second;
+        g_free_streams.erase(g_free_streams.begin() + i);
+        return cudaSuccess;
+      }
+  }
+  return cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+}
+static void give_stream(int dev, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_stream_mu);
+  g_free_streams.push_back({dev, s});
+}
+
 static void init_pool(int dev) {
   static std::atomic<uint64_t> done_mask{0};
   if (dev < 64 && (done_mask.load() >> dev) & 1) return;
@@ -311,16 +396,13 @@ class Miner {
   void release() {
     for (void *p : bufs_) cudaFreeAsync(p, s_);
     bufs_.clear();
-    for (auto &sg : graphs_) {
-      if (sg.exec) cudaGraphExecDestroy(sg.exec);
-      if (sg.graph) cudaGraphDestroy(sg.graph);
-    }
+    for (auto &sg : graphs_) retire_graph(sg.exec, sg.graph);
     graphs_.clear();
-    for (cudaEvent_t ev : ev_pool_) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : ev_pool_) retire_event(ev);
     ev_pool_.clear();
     ev_used_ = 0;
-    if (h_ctrl_ && own_h_ctrl_) { cudaFreeHost(h_ctrl_); h_ctrl_ = nullptr; }
-    if (h_cnt1_) { cudaFreeHost(h_cnt1_); h_cnt1_ = nullptr; }
+    if (h_ctrl_ && own_h_ctrl_) { pinned_free(h_ctrl_, sizeof(Ctrl)); h_ctrl_ = nullptr; }
+    if (h_cnt1_) { pinned_free(h_cnt1_, (size_t)db_->m * 4); h_cnt1_ = nullptr; }
     if (fa_) { cudaEventDestroy(fa_); fa_ = nullptr; }
     if (fb_) { cudaEventDestroy(fb_); fb_ = nullptr; }
     if (ev_fork_) { cudaEventDestroy(ev_fork_); ev_fork_ = nullptr; }
@@ -436,6 +518,7 @@ class Miner {
   int32_t *d_rank_ = nullptr;  // rank of each item (-1: not frequent)
   bool rows_ready_ = false;    // L_.rows (compacted rows) built
   cudaEvent_t eg0_ = nullptr, eg1_ = nullptr;  // the all-blocks GEMM, profiled
+  double setup_ms_ = 0, graph_ms_ = 0;         // host timings (dic_stats)
   dic_status ensure_rows();
 };
 
@@ -690,6 +773,9 @@ dic_status Miner::grow_trace(uint32_t need) {
   Lattice N = L_;
   N.tcap = ncap;
   TRY(alloc(&N.trace, (size_t)ncap * TRACE_COLS));
+  TRY(alloc(&N.trace_work, (size_t)ncap));
+  CU(cudaMemcpyAsync(N.trace_work, L_.trace_work, (size_t)L_.tcap * 8, cudaMemcpyDeviceToDevice,
+                     s_));
   TRY(alloc(&N.cohort_start, (size_t)ncap + 2));
   TRY(alloc(&N.cohort_birth, (size_t)ncap + 2));
   CU(cudaMemcpyAsync(N.trace, L_.trace, (size_t)L_.tcap * TRACE_COLS * 8,
@@ -698,7 +784,7 @@ dic_status Miner::grow_trace(uint32_t need) {
                      cudaMemcpyDeviceToDevice, s_));
   CU(cudaMemcpyAsync(N.cohort_birth, L_.cohort_birth, ((size_t)L_.tcap + 2) * 4,
                      cudaMemcpyDeviceToDevice, s_));
-  drop(L_.trace); drop(L_.cohort_start); drop(L_.cohort_birth);
+  drop(L_.trace); drop(L_.trace_work); drop(L_.cohort_start); drop(L_.cohort_birth);
   L_ = N;
   ++lat_version_;
   return DIC_OK;
@@ -729,11 +815,11 @@ dic_status Miner::begin() {
   if (M_ > n_) M_ = n_;
   stop_max64_ = (n_ + M_ - 1) / M_;
   if (!h_ctrl_) {
-    CU(cudaMallocHost((void **)&h_ctrl_, sizeof(Ctrl)));
+    CU(pinned_alloc((void **)&h_ctrl_, sizeof(Ctrl)));
     own_h_ctrl_ = true;
   }
   if (opt_.algorithm == 1) return DIC_OK;  // classic DIC: no first pass
-  CU(cudaMallocHost((void **)&h_cnt1_, (size_t)db_->m * 4));
+  CU(pinned_alloc((void **)&h_cnt1_, (size_t)db_->m * 4));
   uint32_t *d_cnt1 = nullptr;
   TRY(alloc(&d_cnt1, db_->m));
   if (opt_.profile) {
@@ -743,6 +829,7 @@ dic_status Miner::begin() {
   }
   CU(launch_item_count(db_->words, n_, db_->W, db_->m, d_cnt1, s_));
   ++launches_;
+  drain_retired();  // earlier mines' graphs, while the first pass runs
   if (opt_.profile) CU(cudaEventRecord(fb_, s_));
   CU(cudaMemcpyAsync(h_cnt1_, d_cnt1, (size_t)db_->m * 4, cudaMemcpyDeviceToHost, s_));
   return DIC_OK;
@@ -862,6 +949,7 @@ dic_status Miner::prepare() {
     TRY(alloc(&L_.hslot, L_.hcap, true));
     L_.tcap = std::max<uint32_t>(64, (uint32_t)std::min<uint64_t>(stop_max64 * 3 + 16, 1u << 20));
     TRY(alloc(&L_.trace, (size_t)L_.tcap * TRACE_COLS));
+    TRY(alloc(&L_.trace_work, (size_t)L_.tcap));
     TRY(alloc(&L_.cohort_start, (size_t)L_.tcap + 2));
     TRY(alloc(&L_.cohort_birth, (size_t)L_.tcap + 2, true));
     CU(cudaMemsetAsync(L_.cohort_start, 0, ((size_t)L_.tcap + 2) * 4, s_));
@@ -1079,6 +1167,15 @@ dic_status Miner::launch_stop(uint32_t nstops) {
       sg = &g;
   const uint32_t pred0 = pred_step_;
   if (!sg) {
+    const auto tg0 = std::chrono::steady_clock::now();
+    struct GraphTimer {  // host time of the capture and instantiation
+      std::chrono::steady_clock::time_point t;
+      double *acc;
+      ~GraphTimer() {
+        *acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t)
+                    .count();
+      }
+    } gtimer{tg0, &graph_ms_};
     // capture this stop's launches once (the host-side bookkeeping of the
     // capture is undone; every replay applies it)
     for (size_t i = 0; i < 8; ++i) {  // pool events used by the capture
@@ -1167,6 +1264,8 @@ dic_status Miner::launch_stop(uint32_t nstops) {
 
 dic_status Miner::loop() {
   if (!has_loop_) return DIC_OK;
+  setup_ms_ = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_)
+                  .count();
   const uint32_t wc = L_.wc;
   // stops enqueued per group: those the newest cohort still needs, at most
   // 64 between host checks
@@ -1215,6 +1314,7 @@ dic_status Miner::loop() {
 
 // ---- phase 4: SOLID boxes to the host, canonical order
 dic_status Miner::collect(dic_result **out) {
+  const auto tc0 = std::chrono::steady_clock::now();
   const uint32_t W = db_->W;
   std::unique_ptr<dic_result> res(std::move(res_));
   std::vector<std::vector<uint32_t>> &sets = sets_;
@@ -1257,6 +1357,18 @@ dic_status Miner::collect(dic_result **out) {
     CU(cudaStreamSynchronize(s_));
     res->trace.assign(tr.begin(), tr.end());
     res->stats.stops = ntr;
+    if (ntr && (opt_.profile & DIC_PROFILE_COUNT)) {
+      // count work of the stops whose count kernel was bracketed by events
+      std::vector<unsigned long long> tw(ntr);
+      CU(cudaMemcpy(tw.data(), L_.trace_work, (size_t)ntr * 8, cudaMemcpyDeviceToHost));
+      uint64_t timed = 0;
+      for (uint32_t i = 0; i < ntr; ++i) {
+        const uint64_t step = tr[(size_t)i * TRACE_COLS];
+        const bool profiled = opt_.profile_every <= 1 || step % opt_.profile_every == 0;
+        if (profiled) timed += tw[i] - (i ? tw[i - 1] : 0ull);
+      }
+      res->stats.count_ops_timed = timed;
+    }
     for (uint32_t q = 0; q < nbox; ++q) {
       std::vector<uint32_t> v;
       for (uint32_t w = 0; w < wc; ++w) {
@@ -1310,8 +1422,11 @@ dic_status Miner::collect(dic_result **out) {
   release();
   cudaError_t e = cudaStreamSynchronize(s_);
   if (e != cudaSuccess) return fail(DIC_ECUDA, "finalise: %s", cudaGetErrorString(e));
-  res->stats.mine_ms =
-      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_).count();
+  const auto tend = std::chrono::steady_clock::now();
+  res->stats.mine_ms = std::chrono::duration<double, std::milli>(tend - t0_).count();
+  res->stats.setup_ms = setup_ms_;
+  res->stats.graph_ms = graph_ms_;
+  res->stats.collect_ms = std::chrono::duration<double, std::milli>(tend - tc0).count();
   *out = res.release();
   return DIC_OK;
 }
@@ -1359,7 +1474,7 @@ extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint6
   // the caller's stream by an event and rejoining it at the end.
   cudaStream_t s = nullptr, user = (cudaStream_t)stream;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  cudaError_t e = take_stream(db->device, &s);
   if (e == cudaSuccess && user) {
     e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming);
@@ -1369,7 +1484,7 @@ extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint6
   if (e != cudaSuccess) {
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
-    if (s) cudaStreamDestroy(s);
+    if (s) give_stream(db->device, s);
     if (prev != db->device) cudaSetDevice(prev);
     return fail(DIC_ECUDA, "stream setup: %s", cudaGetErrorString(e));
   }
@@ -1383,11 +1498,12 @@ extern "C" dic_status dic_mine_ex(const dic_db *db, uint32_t minsup_count, uint6
   if (user) {  // the caller's later work waits for the mine
     cudaEventRecord(ev_out, s);
     cudaStreamWaitEvent(user, ev_out, 0);
-    cudaEventDestroy(ev_in);
-    cudaEventDestroy(ev_out);
+    retire_event(ev_in);
+    retire_event(ev_out);
   }
   const_cast<dic_db *>(db)->busy.fetch_sub(1);
-  cudaStreamDestroy(s);
+  cudaStreamSynchronize(s);
+  give_stream(db->device, s);
   if (prev != db->device) cudaSetDevice(prev);
   return st;
 }
@@ -1487,8 +1603,8 @@ class BatchMiner {
     ms_.clear();
     for (void *p : bufs_) cudaFreeAsync(p, s_);
     cudaStreamSynchronize(s_);
-    if (h_ctrls_) cudaFreeHost(h_ctrls_);
-    if (h_Ls_) cudaFreeHost(h_Ls_);
+    if (h_ctrls_) pinned_free(h_ctrls_, (size_t)Q_ * sizeof(Ctrl));
+    if (h_Ls_) pinned_free(h_Ls_, (size_t)Q_ * sizeof(Lattice));
   }
   dic_status run(dic_result **out);
   uint32_t batch_launches() const { return launches_; }
@@ -1534,8 +1650,8 @@ dic_status BatchMiner::sync_ctrls() {
 
 dic_status BatchMiner::run(dic_result **out) {
   const uint32_t Q = Q_;
-  CU(cudaMallocHost((void **)&h_ctrls_, (size_t)Q * sizeof(Ctrl)));
-  CU(cudaMallocHost((void **)&h_Ls_, (size_t)Q * sizeof(Lattice)));
+  CU(pinned_alloc((void **)&h_ctrls_, (size_t)Q * sizeof(Ctrl)));
+  CU(pinned_alloc((void **)&h_Ls_, (size_t)Q * sizeof(Lattice)));
   TRY(alloc(&d_ctrls_, Q));
   TRY(alloc(&d_Ls_, Q));
   uint32_t *d_items = nullptr, *d_chunk = nullptr;

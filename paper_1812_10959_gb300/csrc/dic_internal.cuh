@@ -120,6 +120,7 @@ struct Lattice {
   uint32_t *cohort_start;
   uint32_t *cohort_birth;
   unsigned long long *trace;  // [tcap][TRACE_COLS]
+  unsigned long long *trace_work;  // [tcap] Ctrl.work after each stop's count
   uint32_t tcap;
   // the problem
   const uint64_t *rows;  // compact rows [n][wc]

@@ -13,7 +13,7 @@
 // transposition, 32 rows per word): for every 128-row chunk, twelve
 // expander warps (a thread per rank row) load each rank's four column words
 // (a few chunks ahead, one 16-byte load) and write them to shared memory as
-// e4m3 0/1 bytes (1.0 = 0x38) in the K-major no-swizzle core-matrix layout
+// e4m3 bytes (0, or 0x08 = 2^-6 for a set bit) in the K-major no-swizzle core-matrix layout
 // of tcgen05 (8 ranks x 16 rows per 128-byte core matrix), through a
 // 4-stage ring guarded by mbarriers; one thread of a seventeenth warp issues
 // tcgen05.mma.kind::f8f6f4 (M = 128, N = 256, K = 32 per instruction, fp32
@@ -21,8 +21,9 @@
 // out with tcgen05.ld, turn its rows through shared memory and add the
 // counts of pairs a < b to 32 consecutive records per warp instruction.
 //
-// Exactness: every product is 0 or 1 and a tile's sum over one split is at
-// most its rows (< 2^24), so fp32 accumulation is exact.
+// Exactness: every product is 0 or 2^-12 and a tile's sum over one split is
+// at most its rows (< 2^24) times 2^-12, so fp32 accumulation is exact and
+// the epilogue's scaling by 2^12 returns the integer count.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up records
 // DIC_ETIMEOUT in the loop state, lets the tensor instructions already
@@ -48,7 +49,10 @@ constexpr uint32_t GEXP_THREADS = GEXP_WARPS * 32;
 constexpr uint32_t GRAM_THREADS = GEXP_THREADS + 32;  // + the MMA warp
 static_assert((GM + GN) % 32 == 0 && GLOAD_WARPS <= GEXP_WARPS, "expander warps");
 constexpr long long WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz before giving up
-constexpr uint8_t E4M3_ONE = 0x38;
+// The 0/1 operands are 0 and e4m3 0x08 = 2^-6 (a normal number): products
+// are 0 or 2^-12 and a count c accumulates to c * 2^-12, exact in fp32 for
+// c < 2^24; the epilogue scales back by 2^12.
+constexpr float GRAM_UNIT_INV = 4096.0f;
 
 // Byte offset of element (rank r, row k) inside a tile of 128-row chunks:
 // core matrix (r/8, k/16) at (r/8)*1024 + (k/16)*128, element (r%8)*16 +
@@ -57,10 +61,17 @@ __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t k) {
   return (r >> 3) * 1024u + (k >> 4) * 128u + (r & 7u) * 16u + (k & 15u);
 }
 
-// Four 0/1 bits -> four bytes of 0 or e4m3 1.0: the multiply places bit q at
-// bit 8q (its other copies land on bits the mask clears; no carries).
+// Four 0/1 bits -> four bytes of 0 or 0x08: the multiply adds the nibble
+// shifted by 3, 10, 17 and 24 bits (disjoint ranges, no carries), which puts
+// bit q at bit 8q + 3 in the copy shifted by 3 + 7q; the mask keeps those.
 __device__ __forceinline__ uint32_t expand4(uint32_t nib) {
-  return ((nib * 0x00204081u) & 0x01010101u) * (uint32_t)E4M3_ONE;
+  return (nib * 0x01020408u) & 0x08080808u;
+}
+// Bits [pos, pos + 4) of x.
+__device__ __forceinline__ uint32_t nibble(uint32_t x, uint32_t pos) {
+  uint32_t r;
+  asm("bfe.u32 %0, %1, %2, 4;" : "=r"(r) : "r"(x), "r"(pos));
+  return r;
 }
 
 // ---------------------------------------------------------- PTX helpers
@@ -236,10 +247,10 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (uint32_t h = 0; h < 8; ++h) {  // 16 rows each: core matrix column h
-          const uint32_t x = ws[h >> 1] >> (16 * (h & 1));
+          const uint32_t x = ws[h >> 1], b = 16 * (h & 1);
           *reinterpret_cast<uint4 *>(dst + h * 128u) =
-              make_uint4(expand4(x & 0xFu), expand4((x >> 4) & 0xFu),
-                         expand4((x >> 8) & 0xFu), expand4((x >> 12) & 0xFu));
+              make_uint4(expand4(nibble(x, b)), expand4(nibble(x, b + 4)),
+                         expand4(nibble(x, b + 8)), expand4(nibble(x, b + 12)));
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -297,7 +308,8 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
       const uint64_t b = (uint64_t)tj * GN + c0 + lane;
       if (a0 >= l1 || (uint64_t)tj * GN + c0 + 31 <= a0) continue;  // all b <= a (warp-uniform)
 #pragma unroll
-      for (int k = 0; k < 32; ++k) stage[lane * 33 + k] = (uint32_t)__uint_as_float(v[k]);
+      for (int k = 0; k < 32; ++k)
+        stage[lane * 33 + k] = (uint32_t)(__uint_as_float(v[k]) * GRAM_UNIT_INV);
       __syncwarp();
       const uint32_t rmax = l1 - a0 < 32 ? (uint32_t)(l1 - a0) : 32u;
       for (uint32_t r = 0; r < rmax; ++r) {

@@ -265,6 +265,7 @@ __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
   row[0] = g; row[1] = stop; row[2] = first; row[3] = last;
   row[4] = c.n_live; row[5] = c.n_newbox; row[6] = c.n_pruned; row[7] = c.n_gen;
   row[8] = c.n_solid;
+  if (L.trace_work) L.trace_work[c.n_trace] = c.work;
   uint32_t n_cohorts = c.n_cohorts;
   if (c.n_gen) {
     L.cohort_start[n_cohorts] = c.tail;

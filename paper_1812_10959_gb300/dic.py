@@ -45,7 +45,9 @@ class Stats(ctypes.Structure):
                 ("gram_ms", ctypes.c_double), ("gram_launches", ctypes.c_uint64),
                 ("settle_ms", ctypes.c_double), ("gen_ms", ctypes.c_double),
                 ("gen_launches", ctypes.c_uint64), ("gram_flops", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint64 * 5)]
+                ("count_ops_timed", ctypes.c_uint64), ("setup_ms", ctypes.c_double),
+                ("graph_ms", ctypes.c_double), ("collect_ms", ctypes.c_double),
+                ("reserved", ctypes.c_uint64 * 1)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "path_launches")}
