@@ -339,6 +339,19 @@ void dic_rules_free(dic_rules *r);
  * No counterpart in the paper. DIC_EINVAL for NULL; DIC_ECUDA on failure. */
 dic_status dic_measure_alu_peak(double *tera_ops_per_s);
 
+/* ------------------------------------------------------- test support */
+
+/* Failure injection on the host, for tests of the error paths: the calling
+ * thread's next `after` working-buffer allocations of mining calls succeed
+ * and the one after them fails as an out-of-memory would (the call returns
+ * DIC_ENOMEM having released everything it held); later allocations succeed.
+ * after < 0 cancels. No counterpart in the paper. Always DIC_OK. */
+dic_status dic_debug_fail_device_alloc(int64_t after);
+/* Bytes in use in the current device's default stream-ordered memory pool,
+ * from which the mining calls take their working buffers (so a test can
+ * check that a failed call released them). DIC_EINVAL for NULL; DIC_ECUDA. */
+dic_status dic_debug_pool_used(uint64_t *bytes);
+
 /* ------------------------------------------------ allocation-free count */
 
 /* Size of the scratch array of dic_count_support_noalloc, in 32-bit words

@@ -116,6 +116,20 @@ static void pinned_free(void *p, size_t bytes) {
   g_pinned_free[pinned_class(bytes)].push_back(p);
 }
 
+// Allocation-failure injection (dic_debug_fail_device_alloc): the calling
+// thread's next `after` working-buffer allocations succeed, the one after
+// them fails as if the device were out of memory, later ones succeed.
+static thread_local int64_t g_fail_alloc_after = -1;
+static bool injected_alloc_failure() {
+  if (g_fail_alloc_after < 0) return false;
+  if (g_fail_alloc_after == 0) {
+    g_fail_alloc_after = -1;
+    return true;
+  }
+  --g_fail_alloc_after;
+  return false;
+}
+
 // Graphs and events of finished mines are destroyed by a later call, after
 // it has started its first-pass kernel (the destruction then overlaps device
 // work instead of delaying the finished mine's result).
@@ -379,6 +393,8 @@ class Miner {
   template <class T>
   dic_status alloc(T **p, size_t count, bool zero = false) {
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (injected_alloc_failure())
+      return fail(DIC_ENOMEM, "device allocation of %zu bytes: injected failure", bytes);
     cudaError_t e = cudaMallocAsync((void **)p, bytes, s_);
     if (e != cudaSuccess) return fail(DIC_ENOMEM, "device allocation of %zu bytes: %s", bytes,
                                       cudaGetErrorString(e));
@@ -505,7 +521,9 @@ class Miner {
   uint32_t *h_cnt1_ = nullptr;
   cudaEvent_t fa_ = nullptr, fb_ = nullptr;
   std::vector<uint32_t> l1items_;
-  std::vector<std::vector<uint32_t>> sets_;
+  // result itemsets, flat: items of itemset q at set_items_[set_off_[q] ..
+  // set_off_[q + 1]) in ascending order, its support supps_[q]
+  std::vector<uint32_t> set_items_, set_off_;
   std::vector<uint32_t> supps_;
   bool has_loop_ = false;
   Ctrl *ext_ctrl_ = nullptr;
@@ -797,11 +815,6 @@ static dic_status device_error(uint32_t code) {
   return fail((dic_status)code, "device reported status %u", code);
 }
 
-static bool canon_less(const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) {
-  if (a.size() != b.size()) return a.size() < b.size();
-  return a < b;
-}
-
 // ---- phase 1: first pass launched, its counts copied to pinned memory
 dic_status Miner::begin() {
   t0_ = std::chrono::steady_clock::now();
@@ -864,7 +877,11 @@ dic_status Miner::prepare() {
   res_->stats.words_compact = wc;
   tests_ = classic ? 0 : (uint64_t)m * n;
   if (!classic)
-    for (uint32_t i : l1items) { sets_.push_back({i}); supps_.push_back(h_cnt1_[i]); }
+    for (uint32_t i : l1items) {
+      set_off_.push_back((uint32_t)set_items_.size());
+      set_items_.push_back(i);
+      supps_.push_back(h_cnt1_[i]);
+    }
   // the first cohort: all pairs of frequent ranks, or (classic) all 1-itemsets
   const uint64_t npairs = classic ? (uint64_t)l1 : (uint64_t)l1 * (l1 - (l1 ? 1 : 0)) / 2;
   if (npairs > 0) {
@@ -1317,7 +1334,6 @@ dic_status Miner::collect(dic_result **out) {
   const auto tc0 = std::chrono::steady_clock::now();
   const uint32_t W = db_->W;
   std::unique_ptr<dic_result> res(std::move(res_));
-  std::vector<std::vector<uint32_t>> &sets = sets_;
   std::vector<uint32_t> &supps = supps_;
   const std::vector<uint32_t> &l1items = l1items_;
   uint64_t tests = tests_;
@@ -1369,35 +1385,40 @@ dic_status Miner::collect(dic_result **out) {
       }
       res->stats.count_ops_timed = timed;
     }
+    // ranks -> item ids (rank order is item order, so items come out sorted)
+    set_items_.reserve(set_items_.size() + (size_t)nbox * 4);
     for (uint32_t q = 0; q < nbox; ++q) {
-      std::vector<uint32_t> v;
-      for (uint32_t w = 0; w < wc; ++w) {
-        uint64_t x = hm[(size_t)q * wc + w];
-        while (x) {
-          int b = __builtin_ctzll(x);
-          x &= x - 1;
-          v.push_back(l1items[w * 64 + b]);
-        }
-      }
-      sets.push_back(std::move(v));
+      set_off_.push_back((uint32_t)set_items_.size());
+      for (uint32_t w = 0; w < wc; ++w)
+        for (uint64_t x = hm[(size_t)q * wc + w]; x; x &= x - 1)
+          set_items_.push_back(l1items[w * 64 + (uint32_t)__builtin_ctzll(x)]);
       supps.push_back(hs[q]);
     }
   } else {
     res->stats.candidates = 0;
   }
-  // ---- canonical order, original item space
-  std::vector<uint32_t> order(sets.size());
-  for (uint32_t i = 0; i < order.size(); ++i) order[i] = i;
-  std::sort(order.begin(), order.end(),
-            [&](uint32_t a, uint32_t b) { return canon_less(sets[a], sets[b]); });
-  res->masks.assign(order.size() * W, 0);
-  res->k.resize(order.size());
-  res->supp.resize(order.size());
-  for (size_t q = 0; q < order.size(); ++q) {
-    const auto &v = sets[order[q]];
-    for (uint32_t it : v) res->masks[q * W + (it >> 6)] |= 1ull << (it & 63);
-    res->k[q] = (uint32_t)v.size();
-    res->supp[q] = supps[order[q]];
+  // ---- canonical order (size, then lexicographic), original item space
+  const size_t nset = set_off_.size();
+  set_off_.push_back((uint32_t)set_items_.size());
+  const uint32_t *items = set_items_.data();
+  const uint32_t *off = set_off_.data();
+  std::vector<uint32_t> order(nset);
+  for (uint32_t i = 0; i < nset; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+    const uint32_t ka = off[a + 1] - off[a], kb = off[b + 1] - off[b];
+    if (ka != kb) return ka < kb;
+    return std::lexicographical_compare(items + off[a], items + off[a + 1], items + off[b],
+                                        items + off[b + 1]);
+  });
+  res->masks.assign(nset * W, 0);
+  res->k.resize(nset);
+  res->supp.resize(nset);
+  for (size_t q = 0; q < nset; ++q) {
+    const uint32_t o = order[q];
+    for (uint32_t j = off[o]; j < off[o + 1]; ++j)
+      res->masks[q * W + (items[j] >> 6)] |= 1ull << (items[j] & 63);
+    res->k[q] = off[o + 1] - off[o];
+    res->supp[q] = supps[o];
   }
   res->stats.tests = tests;
   res->stats.frequent = order.size();
@@ -1612,6 +1633,7 @@ class BatchMiner {
  private:
   template <class T>
   dic_status alloc(T **p, size_t count) {
+    if (injected_alloc_failure()) return fail(DIC_ENOMEM, "batch allocation: injected failure");
     cudaError_t e = cudaMallocAsync((void **)p, std::max<size_t>(count * sizeof(T), 16), s_);
     if (e != cudaSuccess) return fail(DIC_ENOMEM, "batch allocation: %s", cudaGetErrorString(e));
     bufs_.push_back(*p);
@@ -2369,6 +2391,24 @@ extern "C" void dic_rules_free(dic_rules *r) { delete r; }
 // -------------------------------------------------------------------- misc
 namespace dic {
 cudaError_t measure_alu_peak(double *tops);
+}
+
+extern "C" dic_status dic_debug_fail_device_alloc(int64_t after) {
+  g_fail_alloc_after = after < 0 ? -1 : after;
+  return DIC_OK;
+}
+
+extern "C" dic_status dic_debug_pool_used(uint64_t *bytes) {
+  if (!bytes) return fail(DIC_EINVAL, "out is NULL");
+  *bytes = 0;
+  int dev = 0;
+  cudaMemPool_t pool;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t used = 0;
+  CU(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  *bytes = used;
+  return DIC_OK;
 }
 
 extern "C" dic_status dic_measure_alu_peak(double *tera_ops_per_s) {

@@ -108,6 +108,8 @@ def _load():
         "dic_rules_copy": ([vp, vp, vp, vp, vp], i32),
         "dic_rules_free": ([vp], None),
         "dic_measure_alu_peak": ([ctypes.POINTER(ctypes.c_double)], i32),
+        "dic_debug_fail_device_alloc": ([ctypes.c_int64], i32),
+        "dic_debug_pool_used": ([ctypes.POINTER(u64)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -396,6 +398,19 @@ def measure_alu_peak() -> float:
     """Measured integer-ALU (lop3) issue rate of the current device, Top/s."""
     v = ctypes.c_double(0.0)
     _check(_lib.dic_measure_alu_peak(ctypes.byref(v)))
+    return v.value
+
+
+def debug_fail_device_alloc(after: int):
+    """Test support: the calling thread's allocation number `after` (0-based)
+    of the next mining calls fails as out of memory; -1 cancels."""
+    _check(_lib.dic_debug_fail_device_alloc(after))
+
+
+def debug_pool_used() -> int:
+    """Test support: bytes in use in the device's stream-ordered pool."""
+    v = ctypes.c_uint64(0)
+    _check(_lib.dic_debug_pool_used(ctypes.byref(v)))
     return v.value
 
 
