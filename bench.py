@@ -380,11 +380,15 @@ def run_batched(args, dic, torch):
             t += time.perf_counter() - t0
         return out, t / steps
 
+    # the tile width common to the batch's rounds, timed on the batch itself
+    from paper_1812_10959_gb300 import autotune
+    tuned = autotune.Tuner(repeats=1).tune_batch(hs, ms, Ms)
+    tw = tuned.tile_words
     for _ in range(args.warmup):
-        res = dic.mine_batch(hs, ms, Ms)
+        res = dic.mine_batch(hs, ms, Ms, tile_words=tw)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    res, t_batch = timed(lambda: dic.mine_batch(hs, ms, Ms), args.steps)
+    res, t_batch = timed(lambda: dic.mine_batch(hs, ms, Ms, tile_words=tw), args.steps)
     clk = clocks.stop()
     tests = sum(r.stats["tests"] for r in res)
     single, t_single = timed(lambda: [dic.mine(h, m_, M_) for h, m_, M_ in zip(hs, ms, Ms)], 1)
@@ -403,6 +407,7 @@ def run_batched(args, dic, torch):
         "single_query_fast_path": {"queries_per_s": n_db / t_single, "ms": 1000 * t_single},
         "plain_per_query_gpu_dic": {"queries_per_s": n_db / t_plain, "ms": 1000 * t_plain},
         "identical_results": bool(same),
+        "autotune": {"tile_words": tw, "candidates_s": tuned.timings},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -466,7 +471,12 @@ def run_served(args, dic, torch):
     t0 = time.perf_counter()
     plain = [dic.mine(hs[db], ms, M, path="rows") for _, db, ms, M in qs[:k]]
     t_plain = time.perf_counter() - t0
-    same = all(a.itemsets() == b.itemsets() for a, b in zip(res[:k], plain))
+    # the single-query fast path, one query after another, on the same sample
+    t0 = time.perf_counter()
+    fast = [dic.mine(hs[db], ms, M) for _, db, ms, M in qs[:k]]
+    t_fast = time.perf_counter() - t0
+    same = all(a.itemsets() == b.itemsets() == c.itemsets()
+               for a, b, c in zip(res[:k], plain, fast))
     tests = sum(r.stats["tests"] for r in res)
     line = {
         "metric": METRIC, "value": tests / el, "unit": UNIT, "n_gpus": 1, "steps": 1,
@@ -481,6 +491,8 @@ def run_served(args, dic, torch):
         "capacity": {"queries_per_s": len(qs) / el_cap, "p50_ms": st_cap["p50_ms"],
                      "p99_ms": st_cap["p99_ms"], "peak_slots": st_cap["peak_slots"]},
         "plain_per_query_gpu_dic": {"queries_per_s": k / t_plain, "sample": k},
+        "single_query_fast_path": {"queries_per_s": k / t_fast, "sample": k},
+        "solo_queries": st["solo"],
         "identical_results_on_sample": bool(same),
         "clocks": clk,
     }

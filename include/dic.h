@@ -118,7 +118,11 @@ typedef struct {
                                each stop's block and count the pairs per
                                stop. Single queries only; same result.
                                Other values: DIC_EINVAL                    */
-  uint32_t reserved[5];
+  uint32_t solo_rows;       /* request server: queries on databases of at
+                               least this many rows are mined alone by the
+                               single-query path on a thread of their own,
+                               beside the batched rounds; 0 = 2^19        */
+  uint32_t reserved[4];
 } dic_options;
 
 /* Per-run statistics (dic_result_stats). */
@@ -256,8 +260,11 @@ dic_status dic_mine_batch(const dic_db *const *dbs, const uint32_t *minsup, cons
  * server admits waiting queries while a slot is free and their estimated
  * device footprint fits `hbm_budget_bytes`; all admitted queries advance one
  * stop of Algorithm 2 per round through launches shared by all of them, and
- * a query that finishes frees its slot and memory immediately. Results are
- * exactly those of dic_mine. The databases must outlive their queries. */
+ * a query that finishes frees its slot and memory immediately. Queries on
+ * databases of at least dic_options.solo_rows rows take no slot: each is
+ * mined alone by the single-query path on a thread of its own, beside the
+ * rounds (admitted against the same budget). Results are exactly those of
+ * dic_mine. The databases must outlive their queries. */
 typedef struct dic_server dic_server;
 typedef struct {
   uint64_t submitted, completed;
@@ -267,7 +274,8 @@ typedef struct {
   uint64_t peak_bytes;      /* largest estimated footprint admitted at once */
   double p50_ms, p99_ms, mean_ms;  /* submit-to-result latency              */
   double qps;               /* completed / (last completion - first submit) */
-  uint32_t reserved[8];
+  uint64_t solo;            /* queries mined alone (dic_options.solo_rows)  */
+  uint32_t reserved[6];
 } dic_server_metrics;
 
 dic_status dic_server_create(uint64_t hbm_budget_bytes, uint32_t max_slots,

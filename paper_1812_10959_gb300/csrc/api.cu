@@ -9,6 +9,7 @@
 // (to stop when DASHED is empty, or to grow a buffer a kernel found short).
 #include <algorithm>
 #include <atomic>
+#include <cstddef>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -1607,6 +1608,95 @@ extern "C" dic_status dic_mine_wait(dic_mine_job *job, int64_t timeout_ms, dic_r
 }
 
 
+// --------------------------------------------------- batched round graphs
+// The four launches of a batched round (count, generation plan, generation,
+// plan) read every argument from device arrays, so a run of rounds is
+// captured once per shape (tile width, rank width, chunk size, shared memory,
+// rounds) and replayed.
+namespace {
+
+struct RoundArgs {
+  const Lattice *Ls;
+  uint32_t Q;
+  int tw, kre;
+  uint32_t *items, *chunk;
+  uint64_t *gen, *slice;
+  uint32_t smem, chunk_cap;
+  int grid, gen_grid;
+};
+
+cudaError_t enqueue_round(const RoundArgs &a, cudaStream_t s) {
+  cudaError_t e = launch_batch_count(a.Ls, a.Q, a.tw, a.kre, a.items, a.chunk, a.smem, a.grid, s);
+  if (e == cudaSuccess) e = launch_batch_plan_gen(a.Ls, a.Q, 1, a.gen, a.slice, s);
+  if (e == cudaSuccess) e = launch_batch_gen(a.Ls, a.Q, 1, a.gen, a.slice, a.gen_grid, s);
+  if (e == cudaSuccess)
+    e = launch_batch_plan(a.Ls, a.Q, true, a.grid, a.chunk_cap, a.items, a.chunk, s);
+  return e;
+}
+
+class RoundGraphs {
+ public:
+  ~RoundGraphs() {
+    for (auto &g : cache_) retire_graph(g.exec, g.graph);
+  }
+  // `rounds` rounds on stream s: replays of captured runs of up to kRun
+  // rounds (direct launches if capture is not possible).
+  cudaError_t run(const RoundArgs &a, uint32_t rounds, cudaStream_t s) {
+    while (rounds > 0) {
+      const uint32_t u = rounds < kRun ? rounds : kRun;
+      cudaGraphExec_t ex = get(a, u, s);
+      cudaError_t e = cudaSuccess;
+      if (ex) {
+        e = cudaGraphLaunch(ex, s);
+      } else {
+        for (uint32_t i = 0; i < u && e == cudaSuccess; ++i) e = enqueue_round(a, s);
+      }
+      if (e != cudaSuccess) return e;
+      rounds -= u;
+    }
+    return cudaSuccess;
+  }
+
+ private:
+  static constexpr uint32_t kRun = 8;
+  struct Entry {
+    RoundArgs a;
+    uint32_t rounds;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Entry> cache_;
+  bool broken_ = false;
+  static bool same(const RoundArgs &x, const RoundArgs &y) {
+    return x.Ls == y.Ls && x.Q == y.Q && x.tw == y.tw && x.kre == y.kre && x.items == y.items &&
+           x.chunk == y.chunk && x.gen == y.gen && x.slice == y.slice && x.smem == y.smem &&
+           x.chunk_cap == y.chunk_cap && x.grid == y.grid && x.gen_grid == y.gen_grid;
+  }
+  cudaGraphExec_t get(const RoundArgs &a, uint32_t u, cudaStream_t s) {
+    if (broken_) return nullptr;
+    for (auto &g : cache_)
+      if (g.rounds == u && same(g.a, a)) return g.exec;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    cudaError_t le = cudaSuccess;
+    for (uint32_t i = 0; i < u && e == cudaSuccess && le == cudaSuccess; ++i)
+      le = enqueue_round(a, s);
+    if (e == cudaSuccess) e = cudaStreamEndCapture(s, &graph);
+    if (e == cudaSuccess && le == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess || le != cudaSuccess || !exec) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      broken_ = true;  // launch directly from now on
+      return nullptr;
+    }
+    cache_.push_back({a, u, graph, exec});
+    return exec;
+  }
+};
+
+}  // namespace
+
 // ------------------------------------------------------------ batch driver
 // Mines many queries together: every query keeps its own lattice; a round
 // advances every active query by one stop and each phase of a round is one
@@ -1653,6 +1743,7 @@ class BatchMiner {
   Ctrl *d_ctrls_ = nullptr, *h_ctrls_ = nullptr;
   Lattice *d_Ls_ = nullptr, *h_Ls_ = nullptr;
   uint32_t launches_ = 0;
+  RoundGraphs rounds_;
 };
 
 dic_status BatchMiner::upload_lattices() {
@@ -1751,13 +1842,10 @@ dic_status BatchMiner::run(dic_result **out) {
     const uint32_t smem = (uint32_t)bitslice_smem(tw, kre, max_l1p, chunk_cap);
     CU(launch_batch_plan(d_Ls_, Q, false, grid, chunk_cap, d_items, d_chunk, s_));
     ++launches_;
-    for (uint32_t r = 0; r < group; ++r) {
-      CU(launch_batch_count(d_Ls_, Q, tw, kre, d_items, d_chunk, smem, grid, s_));
-      CU(launch_batch_plan_gen(d_Ls_, Q, 1, d_gen, d_slice, s_));
-      CU(launch_batch_gen(d_Ls_, Q, 1, d_gen, d_slice, gen_grid, s_));
-      CU(launch_batch_plan(d_Ls_, Q, true, grid, chunk_cap, d_items, d_chunk, s_));
-      launches_ += 4;
-    }
+    const RoundArgs ra{d_Ls_, Q, tw, kre, d_items, d_chunk, d_gen, d_slice, smem, chunk_cap, grid,
+                       gen_grid};
+    CU(rounds_.run(ra, group, s_));
+    launches_ += 4 * group;
     TRY(sync_ctrls());
     bool changed = false;
     for (uint32_t q = 0; q < Q; ++q) {
@@ -1902,6 +1990,17 @@ struct dic_server {
   uint64_t *d_gen = nullptr, *d_slice = nullptr;
   std::vector<std::unique_ptr<Miner>> miner;
   std::vector<std::shared_ptr<ServerRequest>> req;
+  // queries on databases of at least solo_rows rows, each mined alone by the
+  // single-query path on a thread of its own (under mu: solo_running)
+  uint64_t solo_rows = 0;
+  uint32_t solo_running = 0;
+  uint64_t solo_served = 0;
+  struct Solo {
+    std::thread th;
+    std::shared_ptr<std::atomic<bool>> done;
+  };
+  std::vector<Solo> solos;  // worker-owned
+  std::unique_ptr<RoundGraphs> round_graphs;  // worker-owned
 };
 
 namespace {
@@ -2000,11 +2099,10 @@ dic_status server_step(dic_server *sv, const std::vector<std::shared_ptr<ServerR
   CU(launch_batch_plan_gen(sv->d_Ls, Q, 0, sv->d_gen, sv->d_slice, sv->s));
   CU(launch_batch_gen(sv->d_Ls, Q, 0, sv->d_gen, sv->d_slice, sms * 4, sv->s));
   CU(launch_batch_plan(sv->d_Ls, Q, false, sms, chunk_cap, sv->d_items, sv->d_chunk, sv->s));
-  for (uint32_t r = 0; r < group; ++r) {
-    CU(launch_batch_count(sv->d_Ls, Q, sv->tw, kre, sv->d_items, sv->d_chunk, smem, sms, sv->s));
-    CU(launch_batch_plan_gen(sv->d_Ls, Q, 1, sv->d_gen, sv->d_slice, sv->s));
-    CU(launch_batch_gen(sv->d_Ls, Q, 1, sv->d_gen, sv->d_slice, sms * 4, sv->s));
-    CU(launch_batch_plan(sv->d_Ls, Q, true, sms, chunk_cap, sv->d_items, sv->d_chunk, sv->s));
+  {
+    const RoundArgs ra{sv->d_Ls, Q, sv->tw, kre, sv->d_items, sv->d_chunk, sv->d_gen, sv->d_slice,
+                       smem, chunk_cap, sms, sms * 4};
+    CU(sv->round_graphs->run(ra, group, sv->s));
   }
   CU(cudaMemcpyAsync(sv->h_ctrls, sv->d_ctrls, (size_t)Q * sizeof(Ctrl), cudaMemcpyDeviceToHost,
                      sv->s));
@@ -2025,6 +2123,36 @@ dic_status server_step(dic_server *sv, const std::vector<std::shared_ptr<ServerR
   return DIC_OK;
 }
 
+// A query mined alone by the single-query path (every block staged, the pair
+// cohort counted over the whole pass on the tensor cores) on a thread of its
+// own, beside the batched rounds; it completes its own ticket.
+void server_solo(dic_server *sv, std::shared_ptr<ServerRequest> r,
+                 std::shared_ptr<std::atomic<bool>> done) {
+  cudaSetDevice(sv->device);
+  dic_result *res = nullptr;
+  const dic_status st = dic_mine_ex(r->db, r->minsup, r->M, &sv->opt, nullptr, &res);
+  const std::string err = st == DIC_OK ? std::string() : std::string(dic_last_error());
+  const_cast<dic_db *>(r->db)->busy.fetch_sub(1);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->done = true;
+    r->status = st;
+    r->error = err;
+    r->result = res;
+    r->t_done = std::chrono::steady_clock::now();
+    sv->used_bytes -= r->est_bytes;
+    sv->lat_ms.push_back(
+        std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    ++sv->completed;
+    ++sv->solo_served;
+    sv->t_last = r->t_done;
+    --sv->solo_running;
+    done->store(true);
+  }
+  sv->cv_done.notify_all();
+  sv->cv_work.notify_all();
+}
+
 void server_main(dic_server *sv) {
   cudaSetDevice(sv->device);
   const uint32_t Q = sv->max_slots;
@@ -2032,23 +2160,56 @@ void server_main(dic_server *sv) {
     std::vector<std::shared_ptr<ServerRequest>> adm;
     std::vector<uint32_t> slots;
     {
+      // join the threads of solo queries that have finished
+      for (size_t i = 0; i < sv->solos.size();) {
+        if (sv->solos[i].done->load()) {
+          sv->solos[i].th.join();
+          sv->solos[i] = std::move(sv->solos.back());
+          sv->solos.pop_back();
+        } else {
+          ++i;
+        }
+      }
       std::unique_lock<std::mutex> lk(sv->mu);
       bool any_active = false;
       for (uint32_t q = 0; q < Q; ++q) any_active |= (bool)sv->miner[q];
-      if (!any_active)
-        sv->cv_work.wait(lk, [&] { return sv->stopping || !sv->pending.empty(); });
-      if (sv->stopping && sv->pending.empty() && !any_active) return;
+      // the head request can start now: nothing at all is running, or its
+      // footprint fits the budget (all slots are free when none is active)
+      auto admissible = [&] {
+        if (sv->pending.empty()) return false;
+        if (!any_active && sv->solo_running == 0) return true;
+        return sv->used_bytes + sv->pending.front()->est_bytes <= sv->budget;
+      };
+      if (!any_active) {
+        while (!admissible()) {
+          if (sv->stopping && sv->pending.empty() && sv->solo_running == 0) {
+            lk.unlock();
+            for (auto &so : sv->solos) so.th.join();
+            sv->solos.clear();
+            return;
+          }
+          sv->cv_work.wait(lk);  // a submission, a solo query ending, or shutdown
+        }
+      }
       std::vector<uint32_t> free_slots;
       for (uint32_t q = 0; q < Q; ++q)
         if (!sv->miner[q]) free_slots.push_back(q);
       size_t f = 0;
-      while (!sv->pending.empty() && f < free_slots.size()) {
+      while (!sv->pending.empty()) {
         std::shared_ptr<ServerRequest> r = sv->pending.front();
-        const bool alone = !any_active && adm.empty();
+        const bool alone = !any_active && adm.empty() && sv->solo_running == 0;
         if (sv->used_bytes + r->est_bytes > sv->budget && !alone) break;  // wait for memory
+        const bool solo = r->db->n >= sv->solo_rows;
+        if (!solo && f >= free_slots.size()) break;  // wait for a slot
         sv->pending.pop_front();
         sv->used_bytes += r->est_bytes;
         sv->peak_bytes = std::max(sv->peak_bytes, sv->used_bytes);
+        if (solo) {
+          ++sv->solo_running;
+          auto done = std::make_shared<std::atomic<bool>>(false);
+          sv->solos.push_back({std::thread(server_solo, sv, r, done), done});
+          continue;
+        }
         adm.push_back(r);
         slots.push_back(free_slots[f++]);
       }
@@ -2076,6 +2237,10 @@ extern "C" dic_status dic_server_create(uint64_t hbm_budget_bytes, uint32_t max_
   if (!sv) return fail(DIC_ENOMEM, "host allocation");
   sv->budget = hbm_budget_bytes;
   sv->max_slots = max_slots;
+  sv->solo_rows = opt && opt->struct_size >= offsetof(dic_options, solo_rows) + 4 &&
+                          opt->solo_rows
+                      ? opt->solo_rows
+                      : (1ull << 19);
   dic_options_init(&sv->opt);
   if (opt) std::memcpy(&sv->opt, opt, std::min<size_t>(sizeof sv->opt, opt->struct_size ? opt->struct_size : sizeof sv->opt));
   TRY(check_options(sv->opt));
@@ -2099,6 +2264,7 @@ extern "C" dic_status dic_server_create(uint64_t hbm_budget_bytes, uint32_t max_
                 cudaMemcpyHostToDevice));
   sv->miner.resize(max_slots);
   sv->req.resize(max_slots);
+  sv->round_graphs.reset(new RoundGraphs());
   dic_server *p = sv.release();
   p->worker = std::thread(server_main, p);
   *out = p;
@@ -2162,6 +2328,7 @@ extern "C" dic_status dic_server_stats(dic_server *sv, dic_server_metrics *out) 
   out->rounds = sv->rounds;
   out->peak_slots = sv->peak_slots;
   out->peak_bytes = sv->peak_bytes;
+  out->solo = sv->solo_served;
   std::vector<double> v = sv->lat_ms;
   if (!v.empty()) {
     std::sort(v.begin(), v.end());

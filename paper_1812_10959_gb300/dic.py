@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
                 ("profile_every", ctypes.c_uint32), ("tile_words", ctypes.c_uint32),
                 ("count_form", ctypes.c_uint32), ("algorithm", ctypes.c_uint32),
-                ("prestage", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("prestage", ctypes.c_uint32), ("solo_rows", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +62,7 @@ class ServerMetrics(ctypes.Structure):
                 ("reserved0", ctypes.c_uint32), ("peak_bytes", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("qps", ctypes.c_double),
-                ("reserved", ctypes.c_uint32 * 8)]
+                ("solo", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 6)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
@@ -423,8 +424,11 @@ class Server:
     any thread, wait for their results by ticket."""
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, max_slots: int = 64,
-                 path: str = "auto", steps_per_sync: int = 0):
+                 path: str = "auto", steps_per_sync: int = 0, solo_rows: int = 0):
+        """solo_rows: queries on databases of at least this many rows are mined
+        alone by the single-query path (0 = the library's default, 2^19)."""
         o = options(path, steps_per_sync)
+        o.solo_rows = solo_rows
         h = ctypes.c_void_p()
         _check(_lib.dic_server_create(hbm_budget_bytes, max_slots, ctypes.byref(o),
                                       ctypes.byref(h)))

@@ -99,3 +99,23 @@ def test_server_errors(dic, dbs):
     with pytest.raises(dic.DicError):
         srv.wait(t)                      # a ticket is waited once
     srv.close()
+
+
+def test_large_databases_are_mined_alone_beside_the_rounds(dic, dbs):
+    """With solo_rows below some databases' size, their queries take no slot:
+    each is mined alone by the single-query path beside the batched rounds.
+    Every result still equals the query mined alone."""
+    raw, hs = dbs
+    qs = queries(raw, 40, seed=21)
+    srv = dic.Server(max_slots=8, solo_rows=8000)
+    ts = [srv.submit(hs[db], ms, M) for db, ms, M in qs]
+    got = [srv.wait(t) for t in ts]
+    st = srv.stats()
+    srv.close()
+    big = sum(1 for db, _, _ in qs if raw[db].n >= 8000)
+    assert 0 < big < len(qs)
+    assert st["solo"] == big and st["completed"] == len(qs)
+    for (db, ms, M), r in zip(qs, got):
+        alone = dic.mine(hs[db], ms, M)
+        assert r.itemsets() == alone.itemsets()
+        assert r.trace.tolist() == alone.trace.tolist()
