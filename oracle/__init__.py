@@ -63,6 +63,10 @@ def build_paralleldic(force: bool = False) -> str:
     return _PLIB
 
 
+_REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
+                              ctypes.c_uint64)
+
+
 def _pload():
     global _plib
     if _plib is None:
@@ -71,6 +75,10 @@ def _pload():
         lib.pdic_mine.argtypes = [vp, vp, u64, u32, u32, u64, u64, ctypes.c_int,
                                   ctypes.POINTER(vp)]
         lib.pdic_mine.restype = ctypes.c_int
+        lib.pdic_mine_sharded.argtypes = [vp, vp, u64, u32, u32, u64, u64, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, _REDUCE_FN, vp,
+                                          ctypes.POINTER(vp)]
+        lib.pdic_mine_sharded.restype = ctypes.c_int
         for name in ("pdic_result_count", "pdic_result_nitems", "pdic_result_trace_len",
                      "pdic_result_tests"):
             f = getattr(lib, name)
@@ -96,6 +104,38 @@ def paralleldic(row_ptr, items, n: int, m: int, minsup: int, M: int, max_stops: 
     if lib.pdic_mine(rp.ctypes.data, it.ctypes.data, n, m, minsup, M, max_stops, threads,
                      ctypes.byref(h)) != 0:
         raise ValueError("paralleldic: invalid arguments")
+    return _presult(lib, h)
+
+
+def paralleldic_sharded(row_ptr, items, n: int, m: int, minsup: int, M: int, rank: int,
+                        world: int, reduce, max_stops: int = 0, threads: int = 0):
+    """Transaction-sharded ParallelDIC (the data-distributed scheme of the
+    paper's related work): this rank counts its share of every block and
+    `reduce(counts)` must sum the uint64 numpy array `counts` across the
+    ranks in place (called for the first pass and once per stop). Every rank
+    returns the single-rank result and trace. Returns (OracleResult, threads)."""
+    lib = _pload()
+    rp, it = _csr(row_ptr, items)
+
+    def cb(_ctx, ptr, length):
+        try:
+            reduce(np.ctypeslib.as_array(ptr, shape=(int(length),)))
+            return 0
+        except Exception:  # noqa: BLE001 (reported to the C side as a failure)
+            return 1
+
+    fn = _REDUCE_FN(cb)
+    h = ctypes.c_void_p()
+    rc = lib.pdic_mine_sharded(rp.ctypes.data, it.ctypes.data, n, m, minsup, M, max_stops,
+                               threads, rank, world, fn, None, ctypes.byref(h))
+    if rc == -2:
+        raise RuntimeError("paralleldic_sharded: the counter reduction failed")
+    if rc != 0:
+        raise ValueError("paralleldic_sharded: invalid arguments")
+    return _presult(lib, h)
+
+
+def _presult(lib, h):
     cnt = lib.pdic_result_count(h)
     nit = lib.pdic_result_nitems(h)
     k = np.zeros(max(cnt, 1), dtype=np.uint32)

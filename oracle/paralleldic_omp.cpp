@@ -69,6 +69,24 @@ static inline bool contains(const uint64_t *T, const uint64_t *I, uint32_t W) {
   return miss == 0;
 }
 
+// Sums `len` counters across the ranks of a sharded mine, in place (every
+// rank calls it with its own partial counts and receives the totals);
+// returns 0 on success.
+typedef int (*pdic_reduce_fn)(void *ctx, uint64_t *counts, uint64_t len);
+
+// The rows of block [first, last) that rank `rank` of `world` counts: an
+// equal contiguous share of the block.
+static inline void shard_of(uint64_t first, uint64_t last, int rank, int world, uint64_t *lo,
+                            uint64_t *hi) {
+  const uint64_t len = last - first;
+  *lo = first + len * (uint64_t)rank / (uint64_t)world;
+  *hi = first + len * (uint64_t)(rank + 1) / (uint64_t)world;
+}
+
+static int mine_impl(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
+                     uint32_t minsup, uint64_t M, uint64_t max_stops, int threads, int rank,
+                     int world, pdic_reduce_fn reduce, void *ctx, pdic_result **out);
+
 extern "C" {
 
 // Mines rows given as CSR item lists with `threads` OpenMP threads (0 = the
@@ -77,6 +95,32 @@ extern "C" {
 // invalid argument.
 int pdic_mine(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
               uint32_t minsup, uint64_t M, uint64_t max_stops, int threads, pdic_result **out) {
+  return mine_impl(row_ptr, items, n, m, minsup, M, max_stops, threads, 0, 1, nullptr, nullptr,
+                   out);
+}
+
+// Transaction-sharded mine, the data-distributed scheme of the paper's
+// related work (Section 2: every processor counts the candidates over its
+// own part of the transactions and the counts are summed): rank `rank` of
+// `world` counts the first pass and every stop's dashed itemsets over its
+// share of each block only, `reduce` sums those counters across the ranks
+// (once for the first pass, once per stop), and every rank then runs PRUNE,
+// MAKECANDIDATES and CHECKFULLPASS on the same totals, so all ranks hold
+// the same lattice and return the single-rank result and trace. Returns 0,
+// -1 on an invalid argument, -2 if `reduce` failed.
+int pdic_mine_sharded(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
+                      uint32_t minsup, uint64_t M, uint64_t max_stops, int threads, int rank,
+                      int world, pdic_reduce_fn reduce, void *ctx, pdic_result **out) {
+  if (world < 1 || rank < 0 || rank >= world || (world > 1 && !reduce)) return -1;
+  return mine_impl(row_ptr, items, n, m, minsup, M, max_stops, threads, rank, world, reduce, ctx,
+                   out);
+}
+
+}  // extern "C"
+
+static int mine_impl(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32_t m,
+                     uint32_t minsup, uint64_t M, uint64_t max_stops, int threads, int rank,
+                     int world, pdic_reduce_fn reduce, void *ctx, pdic_result **out) {
   if (!out || m == 0 || minsup == 0 || M == 0) return -1;
   *out = nullptr;
   const uint32_t W = (m + 63) / 64;
@@ -87,12 +131,24 @@ int pdic_mine(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32
   if (n == 0) { *out = r; return 0; }
   if (M > n) M = n;
   const uint64_t stop_max = (n + M - 1) / M;
-  // BitMask of every transaction
+  // BitMask of every transaction this rank counts (its share of each block)
   std::vector<uint64_t> B((size_t)n * W, 0);
+  std::vector<uint8_t> mine((size_t)n, world == 1 ? 1 : 0);
+  if (world > 1)
+    for (uint64_t b = 0; b < stop_max; ++b) {
+      uint64_t lo, hi;
+      shard_of(b * M, std::min<uint64_t>((b + 1) * M, n), rank, world, &lo, &hi);
+      for (uint64_t t = lo; t < hi; ++t) mine[t] = 1;
+    }
 #pragma omp parallel for num_threads(threads) schedule(static)
   for (int64_t t = 0; t < (int64_t)n; ++t)
-    for (uint64_t j = row_ptr[t]; j < row_ptr[t + 1]; ++j)
-      B[(size_t)t * W + items[j] / 64] |= 1ull << (items[j] % 64);
+    if (mine[t])
+      for (uint64_t j = row_ptr[t]; j < row_ptr[t + 1]; ++j)
+        B[(size_t)t * W + items[j] / 64] |= 1ull << (items[j] % 64);
+  auto reduce_counts = [&](std::vector<uint64_t> &v) {
+    if (world == 1 || v.empty()) return true;
+    return reduce(ctx, v.data(), v.size()) == 0;
+  };
 
   // FIRSTPASS: every 1-itemset over all transactions (Algorithm 3's form:
   // threads over itemsets, each scanning the transactions)
@@ -105,6 +161,7 @@ int pdic_mine(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32
     for (uint64_t t = 0; t < n; ++t) c += (B[(size_t)t * W + w] & bit) != 0;
     supp1[i] = c;
   }
+  if (!reduce_counts(supp1)) { delete r; return -2; }
   r->tests = (uint64_t)m * n;
   std::vector<uint32_t> L1;
   for (uint32_t i = 0; i < m; ++i)
@@ -149,31 +206,36 @@ int pdic_mine(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32
     row[TR_DASHED] = DASHED.size();
     r->tests += (uint64_t)DASHED.size() * (last - first);
 
-    // COUNTSUPPORT (Algorithm 3, Figures 2 and 3)
+    // COUNTSUPPORT (Algorithm 3, Figures 2 and 3) over this rank's share of
+    // the block, then (sharded) one sum of the counters across the ranks
+    uint64_t lo = first, hi = last;
+    if (world > 1) shard_of(first, last, rank, world, &lo, &hi);
     const int64_t D = (int64_t)DASHED.size();
+    std::vector<uint64_t> part((size_t)D, 0);
     if (D >= threads) {
 #pragma omp parallel for num_threads(threads) schedule(dynamic, 64)
       for (int64_t q = 0; q < D; ++q) {
-        Itemset &I = DASHED[q];
-        I.stop += 1;
-        const uint64_t *mk = &pool[I.off];
+        const uint64_t *mk = &pool[DASHED[q].off];
         uint64_t c = 0;
-        for (uint64_t t = first; t < last; ++t) c += contains(&B[(size_t)t * W], mk, W);
-        I.supp += c;
+        for (uint64_t t = lo; t < hi; ++t) c += contains(&B[(size_t)t * W], mk, W);
+        part[q] = c;
       }
     } else {
       const int inner = (threads + (int)D - 1) / (int)D;
 #pragma omp parallel for num_threads((int)D) schedule(static, 1)
       for (int64_t q = 0; q < D; ++q) {
-        Itemset &I = DASHED[q];
-        I.stop += 1;
-        const uint64_t *mk = &pool[I.off];
+        const uint64_t *mk = &pool[DASHED[q].off];
         uint64_t c = 0;
 #pragma omp parallel for num_threads(inner) reduction(+ : c) schedule(static)
-        for (int64_t t = (int64_t)first; t < (int64_t)last; ++t)
+        for (int64_t t = (int64_t)lo; t < (int64_t)hi; ++t)
           c += contains(&B[(size_t)t * W], mk, W);
-        I.supp += c;
+        part[q] = c;
       }
+    }
+    if (!reduce_counts(part)) { delete r; return -2; }
+    for (int64_t q = 0; q < D; ++q) {
+      DASHED[q].stop += 1;
+      DASHED[q].supp += part[q];
     }
 
     // PRUNE (Algorithm 4)
@@ -285,6 +347,8 @@ int pdic_mine(const uint64_t *row_ptr, const uint32_t *items, uint64_t n, uint32
   *out = r;
   return 0;
 }
+
+extern "C" {
 
 uint64_t pdic_result_count(const pdic_result *r) { return r->sets.size(); }
 uint64_t pdic_result_nitems(const pdic_result *r) {
