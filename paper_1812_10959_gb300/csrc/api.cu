@@ -892,8 +892,18 @@ dic_status Miner::prepare() {
                   (unsigned long long)npairs);
     if (stop_max64 > 0x7FFFFFFFull) return fail(DIC_EINVAL, "too many blocks");
     // ---- ranks of the frequent items
-    std::vector<int32_t> rank_of((size_t)W * 64, -1);
+    // (followed by the first rank of every chunk of 512 items, for the
+    // all-blocks transposition)
+    const uint32_t nchunk = (W + 7) / 8;
+    std::vector<int32_t> rank_of((size_t)W * 64 + nchunk + 1, -1);
     for (uint32_t r = 0; r < l1; ++r) rank_of[l1items[r]] = (int32_t)r;
+    {
+      uint32_t r = 0;
+      for (uint32_t c = 0; c <= nchunk; ++c) {
+        while (r < l1 && l1items[r] < c * 512u) ++r;
+        rank_of[(size_t)W * 64 + c] = (int32_t)r;
+      }
+    }
     TRY(alloc(&d_rank_, rank_of.size()));
     CU(cudaMemcpyAsync(d_rank_, rank_of.data(), rank_of.size() * 4, cudaMemcpyHostToDevice, s_));
 
@@ -1038,7 +1048,8 @@ dic_status Miner::prepare() {
       L_.l1p = bs_l1p_;
       bs_grid_ = sm_count();
       if (vall_) {
-        CU(launch_slice_all(L_, db_->words, W, d_rank_, s_));
+        CU(launch_slice_all(L_, db_->words, W, d_rank_,
+                            reinterpret_cast<const uint32_t *>(d_rank_) + (size_t)W * 64, s_));
         ++launches_;
       }
     }

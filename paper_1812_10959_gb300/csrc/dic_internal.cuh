@@ -273,9 +273,11 @@ cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, ui
                                 uint32_t *supp, cudaStream_t s);
 
 // Columns of every block of the pass (L.vall), transposed once from the
-// original rows B[n][W] (item p -> rank rank_of[p], -1 = not frequent).
+// original rows B[n][W] (item p -> rank rank_of[p], -1 = not frequent);
+// chunk_lo[c] = the number of frequent items below item 512 c, for c = 0 ..
+// ceil(W / 8).
 cudaError_t launch_slice_all(Lattice L, const uint64_t *B, uint32_t W, const int32_t *rank_of,
-                             cudaStream_t s);
+                             const uint32_t *chunk_lo, cudaStream_t s);
 // All-blocks pair GEMM (L.vall, pairs_lex): pc[b][record] = the pair's count
 // over block b (uint32 when `wide`, else uint16: blocks below 65,536 rows).
 cudaError_t launch_gram_all_blocks(Lattice L, void *pc, bool wide, cudaStream_t s);

@@ -67,52 +67,87 @@ cudaError_t launch_slice_block(Lattice L, uint32_t ahead, cudaStream_t s) {
   return launch_k(k_slice_block, grid, 256, 0, s, L, ahead);
 }
 
-// Every block of the pass at once (L.vall): warp item (block b, 32-row word
-// w of the block, word j of the original rows); bit i of source word j is
-// item 64j + i, kept at rank rank_of[64j + i] when frequent. Rows past a
-// block's end read as 0, so every word of every rank row of every tile is
-// written. An index outside V is recorded in Ctrl.error and skipped.
+// Every block of the pass at once (L.vall). A CTA takes one (block b, tile t,
+// chunk of SJC source words) item: it stages the tile's TW*32 rows x SJC
+// words of the original rows B[n][W] in shared memory (row-contiguous,
+// coalesced loads; rows past the block's end read as 0), transposes each
+// 32-row word across a warp (bit i of source word j is item 64j + i), keeps
+// the columns of the frequent items at their ranks in a shared output tile,
+// and writes that tile's rank rows (TW words each) out contiguously. The
+// chunk's frequent items have the consecutive ranks chunk_lo[c] ..
+// chunk_lo[c+1] - 1 (rank order is item order). An index outside V is
+// recorded in Ctrl.error and skipped.
+constexpr uint32_t SJC = 8;                      // source words per chunk
+constexpr uint32_t SROWPAD = SJC + 1;            // padded staged row (words)
+constexpr uint32_t SRANKS = SJC * 64;            // items (at most ranks) per chunk
+
+size_t slice_all_smem(uint32_t tw) {
+  return (size_t)tw * 32 * SROWPAD * 8 + (size_t)SRANKS * (tw + 1) * 4 + SRANKS * 4;
+}
+
 __global__ void __launch_bounds__(256) k_slice_all(Lattice L, const uint64_t *__restrict__ B,
-                                                   uint32_t W, const int32_t *__restrict__ rank_of) {
+                                                   uint32_t W,
+                                                   const int32_t *__restrict__ rank_of,
+                                                   const uint32_t *__restrict__ chunk_lo) {
+  extern __shared__ __align__(16) uint8_t ssm[];
   const uint32_t tw = L.tw, l1p = L.l1p, st = bs_stride((int)tw);
+  const uint32_t rows_t = tw * 32;
+  uint64_t *sin = reinterpret_cast<uint64_t *>(ssm);                   // [rows_t][SROWPAD]
+  uint32_t *sout = reinterpret_cast<uint32_t *>(sin + (size_t)rows_t * SROWPAD);  // [SRANKS][tw+1]
+  int32_t *srank = reinterpret_cast<int32_t *>(sout + (size_t)SRANKS * (tw + 1));  // [SRANKS]
   const uint64_t blockmax = L.M < L.n ? L.M : L.n;
   const uint32_t ntiles = (uint32_t)(((blockmax + 31) / 32 + tw - 1) / tw);
-  const uint64_t per_block = (uint64_t)ntiles * tw * W;
-  const uint64_t items = per_block * L.stop_max;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
-       it += nwarps) {
-    const uint64_t b = it / per_block, rem = it % per_block;
-    const uint32_t w = (uint32_t)(rem / W), j = (uint32_t)(rem % W);
+  const uint32_t nch = (W + SJC - 1) / SJC;
+  const uint64_t items = (uint64_t)L.stop_max * ntiles * nch;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const uint64_t b = it / ((uint64_t)ntiles * nch);
+    const uint32_t rem = (uint32_t)(it % ((uint64_t)ntiles * nch));
+    const uint32_t t = rem / nch, c = rem % nch;
+    const uint32_t j0 = c * SJC;
     const uint64_t first = b * L.M;
     const uint64_t last = first + L.M < L.n ? first + L.M : L.n;
-    const uint64_t row = first + 32ull * w + lane;
-    const uint64_t x = row < last ? __ldg(B + row * W + j) : 0ull;
-    const uint32_t lo = warp_transpose32((uint32_t)x);
-    const uint32_t hi = warp_transpose32((uint32_t)(x >> 32));
-    const int32_t r0 = __ldg(rank_of + j * 64 + lane), r1 = __ldg(rank_of + j * 64 + 32 + lane);
-    const uint32_t t = w / tw, wi = w % tw;
-    uint32_t *Vb = L.V + b * L.vwords;
-    if (r0 >= 0) {
-      const uint64_t i0 = ((uint64_t)t * l1p + (uint32_t)r0) * st + wi;
-      if (i0 < L.vwords && (uint32_t)r0 < l1p) Vb[i0] = lo;
-      else L.ctrl->error = DIC_INTERNAL_BOUNDS;
+    const uint64_t row0 = first + (uint64_t)t * rows_t;
+    const uint32_t rlo = chunk_lo[c], rhi = chunk_lo[c + 1];
+    __syncthreads();  // the previous item's tiles are free
+    for (uint32_t e = threadIdx.x; e < rows_t * SJC; e += blockDim.x) {
+      const uint32_t r = e / SJC, w = e % SJC;
+      const uint64_t row = row0 + r;
+      sin[r * SROWPAD + w] = (row < last && j0 + w < W) ? __ldcs(B + row * W + j0 + w) : 0ull;
     }
-    if (r1 >= 0) {
-      const uint64_t i1 = ((uint64_t)t * l1p + (uint32_t)r1) * st + wi;
-      if (i1 < L.vwords && (uint32_t)r1 < l1p) Vb[i1] = hi;
+    for (uint32_t e = threadIdx.x; e < SRANKS; e += blockDim.x)
+      srank[e] = j0 * 64 + e < W * 64 ? __ldg(rank_of + j0 * 64 + e) : -1;
+    __syncthreads();
+    for (uint32_t q = warp; q < tw * SJC; q += nwarp) {
+      const uint32_t g = q / SJC, j = q % SJC;
+      const uint64_t x = sin[(g * 32 + lane) * SROWPAD + j];
+      const uint32_t lo = warp_transpose32((uint32_t)x);
+      const uint32_t hi = warp_transpose32((uint32_t)(x >> 32));
+      const int32_t r0 = srank[j * 64 + lane], r1 = srank[j * 64 + 32 + lane];
+      if (r0 >= 0) sout[((uint32_t)r0 - rlo) * (tw + 1) + g] = lo;
+      if (r1 >= 0) sout[((uint32_t)r1 - rlo) * (tw + 1) + g] = hi;
+    }
+    __syncthreads();
+    uint32_t *Vb = L.V + b * L.vwords;
+    for (uint32_t e = threadIdx.x; e < (rhi - rlo) * tw; e += blockDim.x) {
+      const uint32_t rr = e / tw, w = e % tw;
+      const uint64_t idx = ((uint64_t)t * l1p + rlo + rr) * st + w;
+      if (idx < L.vwords && rlo + rr < l1p && rr < SRANKS) Vb[idx] = sout[rr * (tw + 1) + w];
       else L.ctrl->error = DIC_INTERNAL_BOUNDS;
     }
   }
 }
 
 cudaError_t launch_slice_all(Lattice L, const uint64_t *B, uint32_t W, const int32_t *rank_of,
-                             cudaStream_t s) {
+                             const uint32_t *chunk_lo, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_slice_all<<<sms * 8, 256, 0, s>>>(L, B, W, rank_of);
+  const size_t smem = slice_all_smem(L.tw);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_slice_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_slice_all<<<sms * 3, 256, smem, s>>>(L, B, W, rank_of, chunk_lo);
   return cudaGetLastError();
 }
 

@@ -19,12 +19,15 @@ namespace dic {
 
 // --------------------------------------------------------- first pass
 // supp1[i] = number of rows with bit i set, over all n rows (FIRSTPASS of
-// Section 4.2). A warp takes 32 rows at a time and up to ICHUNK of their
-// 64-bit words: each word, transposed across the warp (lane t ends with the
-// 32 rows' bits of items 64j+t and 64j+32+t), adds two popcounts to the
-// lane's registers; a warp walks many row groups of the same words, then
-// adds its 2*ICHUNK counters once.
+// Section 4.2). A warp takes 32 rows at a time and ICHUNK of their 64-bit
+// words: it loads the 32 x ICHUNK words with row-contiguous 8-byte loads
+// into its own shared-memory tile, then lane t takes row t's words and each
+// word, transposed across the warp (lane t ends with the 32 rows' bits of
+// items 64j+t and 64j+32+t), adds two popcounts to the lane's registers. A
+// warp walks many row groups of the same words, then adds its 2*ICHUNK
+// counters once.
 constexpr uint32_t ICHUNK = 8;
+constexpr uint32_t ITILE = ICHUNK + 1;  // padded row of a warp's tile (words)
 
 __device__ __forceinline__ uint32_t warp_transpose32_fp(uint32_t x) {
   const uint32_t lane = threadIdx.x & 31;
@@ -41,9 +44,11 @@ __device__ __forceinline__ uint32_t warp_transpose32_fp(uint32_t x) {
 __global__ void __launch_bounds__(256) k_item_count(const uint64_t *__restrict__ B, uint64_t n,
                                                     uint32_t W, uint32_t m,
                                                     uint32_t *__restrict__ cnt) {
-  const uint32_t lane = threadIdx.x & 31;
+  __shared__ uint64_t tile[8][32 * ITILE];
+  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint64_t *tl = tile[wib];
   const uint32_t njc = (W + ICHUNK - 1) / ICHUNK;
-  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint64_t wpc = nw / njc;  // warps per word chunk (the launch makes it >= 1)
   if (gw / njc >= wpc) return;
@@ -52,18 +57,27 @@ __global__ void __launch_bounds__(256) k_item_count(const uint64_t *__restrict__
   uint32_t acc[2 * ICHUNK];
 #pragma unroll
   for (int q = 0; q < 2 * (int)ICHUNK; ++q) acc[q] = 0;
+  // load pattern: lane l takes word l % 8 of rows l / 8, 4 + l / 8, ...
+  const uint32_t lw = lane % ICHUNK, lr = lane / ICHUNK;
+  const bool wok = j0 + lw < W;
   for (uint64_t rg = gw / njc; rg < ngroups; rg += wpc) {
-    const uint64_t row = rg * 32 + lane;
-    const uint64_t *p = B + row * W + j0;
-    uint64_t x[ICHUNK];
+    const uint64_t row0 = rg * 32;
+    uint64_t v[8];
 #pragma unroll
-    for (uint32_t q = 0; q < ICHUNK; ++q)
-      x[q] = (row < n && j0 + q < W) ? __ldcs(p + q) : 0ull;
+    for (uint32_t i = 0; i < 8; ++i) {
+      const uint64_t row = row0 + 4 * i + lr;
+      v[i] = (wok && row < n) ? __ldcs(B + row * W + j0 + lw) : 0ull;
+    }
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) tl[(4 * i + lr) * ITILE + lw] = v[i];
+    __syncwarp();
 #pragma unroll
     for (uint32_t q = 0; q < ICHUNK; ++q) {
-      acc[2 * q] += __popc(warp_transpose32_fp((uint32_t)x[q]));
-      acc[2 * q + 1] += __popc(warp_transpose32_fp((uint32_t)(x[q] >> 32)));
+      const uint64_t x = tl[lane * ITILE + q];
+      acc[2 * q] += __popc(warp_transpose32_fp((uint32_t)x));
+      acc[2 * q + 1] += __popc(warp_transpose32_fp((uint32_t)(x >> 32)));
     }
+    __syncwarp();
   }
 #pragma unroll
   for (uint32_t q = 0; q < ICHUNK; ++q) {
