@@ -1152,8 +1152,7 @@ dic_status Miner::recover() {
       TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live + h_ctrl_->n_newbox));
       phase = st == ST_HASH ? PH_HASH : PH_COUNT;
     } else if (st == ST_CAND) {
-      TRY(grow_candidates(h_ctrl_->tail + h_ctrl_->n_gen));
-      h_ctrl_->n_gen = 0;
+      TRY(grow_candidates(h_ctrl_->tail + n_gen_of(*h_ctrl_)));
       phase = PH_GEN;
     } else {
       return fail(DIC_ECUDA, "unknown stall code %u", st);
@@ -1161,7 +1160,7 @@ dic_status Miner::recover() {
     if (phase == PH_COUNT) next_v_ready_ = false;
     pred_step_ = h_ctrl_->step;
     h_ctrl_->stall = ST_NONE;
-    h_ctrl_->blocks_done = 0;
+    h_ctrl_->gen_ticket = 0;  // no candidate drawn, no generate CTA done
     CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
     TRY(launch_stop_from(phase));
     TRY(sync_ctrl());

@@ -40,14 +40,17 @@ struct Ctrl {
   uint32_t n_newbox;   // promotions at this stop
   uint32_t n_pruned;   // circles erased by the bound at this stop
   uint32_t n_solid;    // records reaching a full pass at this stop
-  uint32_t n_gen;      // generation attempts at this stop (incl. overflow)
+  // low 32 bits: candidates emitted at this stop (their record slots are
+  // tail + 0, 1, ..., slots past the capacity included); high 32 bits: CTAs
+  // of the generate kernel that have finished (its last-block ticket). One
+  // word, so the last CTA's ticket returns the final count.
+  unsigned long long gen_ticket;
   uint32_t gen_tail0;  // tail before this stop's generation
   uint32_t cohort_head;
   uint32_t n_cohorts;
   uint32_t hash_used;  // occupied hash slots
   uint32_t max_k;      // largest itemset size ever placed in DASHED
   uint32_t n_trace;
-  uint32_t blocks_done;  // ticket of the generate kernel's last-block step
   uint32_t last_birth;   // creation stop of the newest cohort
   uint32_t solo;         // 1: the batched kernels leave this query alone
   uint32_t head_birth;   // creation stop of the oldest cohort in the window
@@ -61,6 +64,8 @@ struct Ctrl {
   unsigned long long work;   // algorithmic integer ops of the count kernels
   unsigned long long gram_rows;  // block rows whose pair cohort the GEMM counted
 };
+
+__host__ __device__ inline uint32_t n_gen_of(const Ctrl &c) { return (uint32_t)c.gen_ticket; }
 
 // Add per-thread PRUNE tallies and count work of one CTA to the loop state
 // with at most one atomic per field (every thread of the CTA must call; the

@@ -356,16 +356,15 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_ne
   pdl_wait();
   pdl_trigger();
   Ctrl *C = L.ctrl;
-  // the fields this kernel decides on, read by one thread per CTA (every
-  // warp asking L2 for the same line at once would serialise there)
-  __shared__ uint32_t s_f[5];
-  if (threadIdx.x == 0) {
-    s_f[0] = C->stall; s_f[1] = C->done; s_f[2] = C->n_newbox; s_f[3] = C->step;
-    s_f[4] = C->tail;
-  }
+  // the loop state, read by one thread per CTA (every warp asking L2 for the
+  // same line at once would serialise there); none of the fields the end of
+  // the stop reads changes during this kernel except the candidate count,
+  // which the last CTA's ticket returns
+  __shared__ Ctrl s_c;
+  if (threadIdx.x == 0) s_c = *C;
   __syncthreads();
-  const uint32_t P = s_f[2], g = s_f[3], base = s_f[4], l1 = L.l1;
-  if (s_f[0] || s_f[1]) return;
+  const uint32_t P = s_c.n_newbox, g = s_c.step, base = s_c.tail, l1 = L.l1;
+  if (s_c.stall || s_c.done) return;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slice_next)  // the columns of stop g+1 (count of stop g is complete)
@@ -381,18 +380,22 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_ne
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
     gen_candidate(L, C, (uint32_t)(w / l1), (uint32_t)(w % l1), g, base);
   }
-  // last block closes the stop
-  __shared__ bool last;
+  // the last CTA to finish closes the stop: its ticket (the high half of the
+  // word whose low half every emitted candidate incremented, all of this
+  // CTA's before the barrier) returns the stop's final candidate count
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&C->blocks_done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    C->blocks_done = 0;
-    if (!C->stall) finish_stop(L, C);
+    const unsigned long long old = atomicAdd(&C->gen_ticket, 1ull << 32);
+    if ((uint32_t)(old >> 32) == gridDim.x - 1) {
+      const uint32_t n_gen = (uint32_t)old;
+      // a slot past the capacity stalls the stop (ST_CAND, set by the CTA
+      // that drew it); the host grows the store and re-runs generation
+      if ((uint64_t)base + n_gen <= L.cap) {
+        Ctrl c = s_c;
+        c.gen_ticket = n_gen;
+        finish_stop_with(L, C, c);
+      }
+    }
   }
 }
 

@@ -179,7 +179,7 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
       // above, so only the canonical-parent rule remains (no box-set probe)
       if (a0 < r && p1 == g) return;
       if (a1 < r && p0 == g) return;
-      const uint32_t pos = base + atomicAdd(&C->n_gen, 1u);
+      const uint32_t pos = base + (uint32_t)atomicAdd(&C->gen_ticket, 1ull);
       if (pos >= L.cap) {
         C->stall = ST_CAND;
         return;
@@ -224,7 +224,7 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
       if (v == 0 || (i * 64 + b < r && v == g + 1)) return;
     }
   }
-  const uint32_t pos = base + atomicAdd(&C->n_gen, 1u);
+  const uint32_t pos = base + (uint32_t)atomicAdd(&C->gen_ticket, 1ull);
   if (pos >= L.cap) {
     C->stall = ST_CAND;
     return;
@@ -248,10 +248,19 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
 // End of stop g for one query: trace row, test count, the new cohort,
 // CHECKFULLPASS (cohorts whose full pass is complete leave the window [head,
 // tail)), |DASHED| and the loop test of Algorithm 2.
+__device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, const Ctrl &c);
+
 __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
   // one copy of the loop state in registers (independent loads, one round
-  // trip); every field this stop changes is stored once at the end
+  // trip)
   const Ctrl c = *C;
+  finish_stop_with(L, C, c);
+}
+
+// finish_stop from a copy of the loop state taken by the caller (with the
+// stop's final candidate count); every field this stop changes is stored
+// once at the end.
+__device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, const Ctrl &c) {
   const uint32_t g = c.step;
   uint32_t stop;
   uint64_t first, last;
@@ -263,18 +272,19 @@ __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
   }
   unsigned long long *row = L.trace + (uint64_t)c.n_trace * TRACE_COLS;
   row[0] = g; row[1] = stop; row[2] = first; row[3] = last;
-  row[4] = c.n_live; row[5] = c.n_newbox; row[6] = c.n_pruned; row[7] = c.n_gen;
+  const uint32_t n_gen = n_gen_of(c);
+  row[4] = c.n_live; row[5] = c.n_newbox; row[6] = c.n_pruned; row[7] = n_gen;
   row[8] = c.n_solid;
   if (L.trace_work) L.trace_work[c.n_trace] = c.work;
   uint32_t n_cohorts = c.n_cohorts;
-  if (c.n_gen) {
+  if (n_gen) {
     L.cohort_start[n_cohorts] = c.tail;
     L.cohort_birth[n_cohorts] = g;
     n_cohorts += 1;
     C->last_birth = g;
   }
-  const uint32_t tail = c.tail + c.n_gen;
-  const uint32_t n_live = c.n_live - c.n_pruned - c.n_solid + c.n_gen;
+  const uint32_t tail = c.tail + n_gen;
+  const uint32_t n_live = c.n_live - c.n_pruned - c.n_solid + n_gen;
   // CHECKFULLPASS: cohorts whose full pass ends with this stop leave the
   // window (a cohort born now never does: its birth + stop_max > g)
   // (head = the first remaining cohort's start; the new cohort, if any,
@@ -299,7 +309,7 @@ __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
   C->cohort_head = ch;
   C->head = head;
   C->head_birth = hb;
-  C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->n_gen = 0;
+  C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->gen_ticket = 0;
   C->n_trace = c.n_trace + 1;
   C->step = g + 1;
   if (n_live == 0) C->done = 1;
