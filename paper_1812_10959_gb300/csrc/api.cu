@@ -182,6 +182,49 @@ static void give_stream(int dev, cudaStream_t s) {
   g_free_streams.push_back({dev, s});
 }
 
+// A page-locked host staging buffer from the reuse cache above.
+template <class T>
+struct PinnedBuf {
+  T *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t get(size_t count) {
+    bytes = std::max<size_t>(count * sizeof(T), 16);
+    return pinned_alloc((void **)&p, bytes);
+  }
+  ~PinnedBuf() { pinned_free(p, bytes); }
+};
+
+// Itemset mask arrays of freed results, reused by later results (a fresh
+// array of this size would page-fault on every page as it is first written).
+namespace {
+std::mutex g_mask_pool_mu;
+std::vector<std::vector<uint64_t>> g_mask_pool;
+}  // namespace
+
+static std::vector<uint64_t> take_mask_array(size_t words) {
+  std::vector<uint64_t> v;
+  {
+    std::lock_guard<std::mutex> lk(g_mask_pool_mu);
+    size_t best = g_mask_pool.size();
+    for (size_t i = 0; i < g_mask_pool.size(); ++i)
+      if (g_mask_pool[i].capacity() >= words &&
+          (best == g_mask_pool.size() || g_mask_pool[i].capacity() < g_mask_pool[best].capacity()))
+        best = i;
+    if (best < g_mask_pool.size()) {
+      v = std::move(g_mask_pool[best]);
+      g_mask_pool.erase(g_mask_pool.begin() + best);
+    }
+  }
+  v.assign(words, 0);
+  return v;
+}
+
+static void give_mask_array(std::vector<uint64_t> &&v) {
+  if (v.capacity() < (1u << 12)) return;
+  std::lock_guard<std::mutex> lk(g_mask_pool_mu);
+  if (g_mask_pool.size() < 8) g_mask_pool.push_back(std::move(v));
+}
+
 static void init_pool(int dev) {
   static std::atomic<uint64_t> done_mask{0};
   if (dev < 64 && (done_mask.load() >> dev) & 1) return;
@@ -526,6 +569,7 @@ class Miner {
   // set_off_[q + 1]) in ascending order, its support supps_[q]
   std::vector<uint32_t> set_items_, set_off_;
   std::vector<uint32_t> supps_;
+  size_t n_first_ = 0;  // leading itemsets from the first pass (item order)
   bool has_loop_ = false;
   Ctrl *ext_ctrl_ = nullptr;
   bool own_h_ctrl_ = false;
@@ -883,6 +927,7 @@ dic_status Miner::prepare() {
       set_items_.push_back(i);
       supps_.push_back(h_cnt1_[i]);
     }
+  n_first_ = set_off_.size();
   // the first cohort: all pairs of frequent ranks, or (classic) all 1-itemsets
   const uint64_t npairs = classic ? (uint64_t)l1 : (uint64_t)l1 * (l1 - (l1 ? 1 : 0)) / 2;
   if (npairs > 0) {
@@ -1362,27 +1407,37 @@ dic_status Miner::collect(dic_result **out) {
     TRY(alloc(&d_cnt, 1, true));
     CU(launch_collect_boxes(L_, tail, d_idx, d_cnt, s_));
     ++launches_;
-    uint32_t nbox = 0;
-    CU(cudaMemcpyAsync(&nbox, d_cnt, 4, cudaMemcpyDeviceToHost, s_));
+    PinnedBuf<uint32_t> h_nbox;
+    CU(h_nbox.get(1));
+    CU(cudaMemcpyAsync(h_nbox.p, d_cnt, 4, cudaMemcpyDeviceToHost, s_));
     CU(cudaStreamSynchronize(s_));
+    const uint32_t nbox = *h_nbox.p;
     uint64_t *d_om = nullptr;
     uint32_t *d_os = nullptr;
     TRY(alloc(&d_om, (size_t)nbox * wc));
     TRY(alloc(&d_os, nbox));
     CU(launch_gather_boxes(L_, d_idx, nbox, d_om, d_os, s_));
     ++launches_;
-    std::vector<uint64_t> hm((size_t)nbox * wc);
-    std::vector<uint32_t> hs(nbox);
-    if (nbox) {
-      CU(cudaMemcpyAsync(hm.data(), d_om, hm.size() * 8, cudaMemcpyDeviceToHost, s_));
-      CU(cudaMemcpyAsync(hs.data(), d_os, hs.size() * 4, cudaMemcpyDeviceToHost, s_));
-    }
+    // staged in reused page-locked host blocks
+    PinnedBuf<uint64_t> hm_b;
+    PinnedBuf<uint32_t> hs_b;
+    PinnedBuf<unsigned long long> tr_b;
     const uint32_t ntr = h_ctrl_->n_trace;
-    std::vector<unsigned long long> tr((size_t)ntr * TRACE_COLS);
+    CU(hm_b.get((size_t)nbox * wc));
+    CU(hs_b.get(nbox));
+    CU(tr_b.get((size_t)ntr * TRACE_COLS));
+    const uint64_t *hm = hm_b.p;
+    const uint32_t *hs = hs_b.p;
+    const unsigned long long *tr = tr_b.p;
+    if (nbox) {
+      CU(cudaMemcpyAsync(hm_b.p, d_om, (size_t)nbox * wc * 8, cudaMemcpyDeviceToHost, s_));
+      CU(cudaMemcpyAsync(hs_b.p, d_os, (size_t)nbox * 4, cudaMemcpyDeviceToHost, s_));
+    }
     if (ntr)
-      CU(cudaMemcpyAsync(tr.data(), L_.trace, tr.size() * 8, cudaMemcpyDeviceToHost, s_));
+      CU(cudaMemcpyAsync(tr_b.p, L_.trace, (size_t)ntr * TRACE_COLS * 8, cudaMemcpyDeviceToHost,
+                         s_));
     CU(cudaStreamSynchronize(s_));
-    res->trace.assign(tr.begin(), tr.end());
+    res->trace.assign(tr, tr + (size_t)ntr * TRACE_COLS);
     res->stats.stops = ntr;
     if (ntr && (opt_.profile & DIC_PROFILE_COUNT)) {
       // count work of the stops whose count kernel was bracketed by events
@@ -1408,20 +1463,43 @@ dic_status Miner::collect(dic_result **out) {
   } else {
     res->stats.candidates = 0;
   }
-  // ---- canonical order (size, then lexicographic), original item space
+  // ---- canonical order (size, then lexicographic), original item space.
+  // The 1-itemsets come first and already in order; the rest are sorted by
+  // size and a key holding their first eight item ids (16 bits each, first
+  // item most significant), comparing whole item lists only on equal keys.
   const size_t nset = set_off_.size();
   set_off_.push_back((uint32_t)set_items_.size());
   const uint32_t *items = set_items_.data();
   const uint32_t *off = set_off_.data();
   std::vector<uint32_t> order(nset);
   for (uint32_t i = 0; i < nset; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-    const uint32_t ka = off[a + 1] - off[a], kb = off[b + 1] - off[b];
-    if (ka != kb) return ka < kb;
-    return std::lexicographical_compare(items + off[a], items + off[a + 1], items + off[b],
-                                        items + off[b + 1]);
-  });
-  res->masks.assign(nset * W, 0);
+  {
+    const size_t n1 = std::min(nset, n_first_);  // the first pass's 1-itemsets, in order
+    struct Key { uint64_t hi, lo; uint32_t k, idx; };
+    std::vector<Key> keys(nset - n1);
+    const bool narrow = db_->m <= 65536u;
+    for (size_t q = n1; q < nset; ++q) {
+      Key &kq = keys[q - n1];
+      kq.k = off[q + 1] - off[q];
+      kq.idx = (uint32_t)q;
+      kq.hi = kq.lo = 0;
+      if (narrow)
+        for (uint32_t j = 0; j < 8 && j < kq.k; ++j) {
+          const uint64_t v = items[off[q] + j];
+          if (j < 4) kq.hi |= v << (48 - 16 * j);
+          else kq.lo |= v << (48 - 16 * (j - 4));
+        }
+    }
+    std::sort(keys.begin(), keys.end(), [&](const Key &a, const Key &b) {
+      if (a.k != b.k) return a.k < b.k;
+      if (a.hi != b.hi) return a.hi < b.hi;
+      if (a.lo != b.lo) return a.lo < b.lo;
+      return std::lexicographical_compare(items + off[a.idx], items + off[a.idx + 1],
+                                          items + off[b.idx], items + off[b.idx + 1]);
+    });
+    for (size_t q = n1; q < nset; ++q) order[q] = keys[q - n1].idx;
+  }
+  res->masks = take_mask_array(nset * W);
   res->k.resize(nset);
   res->supp.resize(nset);
   for (size_t q = 0; q < nset; ++q) {
@@ -2398,7 +2476,11 @@ extern "C" dic_status dic_result_stats(const dic_result *r, dic_stats *out) {
   *out = r->stats;
   return DIC_OK;
 }
-extern "C" void dic_result_free(dic_result *r) { delete r; }
+extern "C" void dic_result_free(dic_result *r) {
+  if (!r) return;
+  give_mask_array(std::move(r->masks));
+  delete r;
+}
 
 // ------------------------------------------------------ association rules
 namespace {
