@@ -103,8 +103,10 @@ def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=No
     nl = sum(s[nkey[kind]] if kind in nkey else s["path_launches"][3] for s in stats)
     avg_ms = tot_ms / max(nl, 1)
     st = stats[0]
+    ev = bool(st.get("event_loop"))
     common = {"avg_launch_ms": avg_ms, "launches_timed": nl,
-              "timed_stops": f"one stop in {PROFILE_EVERY} of the timed steps",
+              "timed_stops": (f"one loop iteration in {PROFILE_EVERY} of the timed steps" if ev
+                              else f"one stop in {PROFILE_EVERY} of the timed steps"),
               "kind_ms_per_step_warmup": {k: v for k, v in shares_ms.items()}}
     if kind == "gram":
         flops = sum(s["gram_flops"] for s in stats) / max(nl, 1)
@@ -123,6 +125,8 @@ def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=No
         kern = COUNT_KERNELS[max((1, 2, 3), key=lambda i: pl[i])]
         if kern != "k_count_rows" and count_form == "tiled":
             kern = "k_count_bitslice"
+        if ev:  # the event-driven loop counts each cohort over its whole pass
+            kern = "k_cohort_pass"
         peak = alu_peak if alu_peak else ALU_PEAK_TOPS
         src = ("measured in this run: lop3.b32 issue rate (dic_measure_alu_peak)" if alu_peak
                else "derived: 152 SM x 64 INT32 lanes x 2070 MHz")
@@ -138,7 +142,9 @@ def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=No
         # W'*8 + ranks 32 + count, birth, shape, size 10 bytes), from the trace
         if trace is not None and len(trace):
             promoted, generated = float(trace[:, 5].sum()), float(trace[:, 7].sum())
-            byts = (promoted * l1 * 2 + generated * (wc * 8 + 32 + 10)) / len(trace)
+            # one launch per stop, or per loop iteration (event-driven loop)
+            nlaunch = st["event_iters"] if ev and st.get("event_iters") else len(trace)
+            byts = (promoted * l1 * 2 + generated * (wc * 8 + 32 + 10)) / nlaunch
         else:
             byts = 0.0
     else:

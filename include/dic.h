@@ -122,7 +122,19 @@ typedef struct {
                                least this many rows are mined alone by the
                                single-query path on a thread of their own,
                                beside the batched rounds; 0 = 2^19        */
-  uint32_t reserved[4];
+  uint32_t stop_loop;       /* 0 = count every dashed itemset at every
+                               stop; 1 = event-driven where it applies
+                               (single queries with prestaged columns and
+                               the pair cohort on the GEMM, at most 8,192
+                               blocks, otherwise 0): each cohort is counted
+                               over its whole pass when it is born, so its
+                               promotion and erase stops (Algorithm 4) are
+                               known in advance and only stops that promote
+                               something run MAKECANDIDATES, all inside one
+                               graph with a device-side loop. Same
+                               itemsets, supports and trace either way.
+                               Other values: DIC_EINVAL                    */
+  uint32_t reserved[3];
 } dic_options;
 
 /* Per-run statistics (dic_result_stats). */
@@ -163,7 +175,10 @@ typedef struct {
                                stop graphs                                 */
   double collect_ms;        /* host wall time from the last stop's check to
                                the result being ready                      */
-  uint64_t reserved[1];
+  uint32_t event_loop;      /* 1: the event-driven stop loop ran
+                               (dic_options.stop_loop)                     */
+  uint32_t event_iters;     /* its iterations (cohort pass + MAKECANDIDATES
+                               at one stop with promotions)                */
 } dic_stats;
 
 /* Columns of one trace row (one per iteration of Algorithm 2's loop). */

@@ -472,6 +472,7 @@ class Miner {
     if (eg0_) { cudaEventDestroy(eg0_); eg0_ = nullptr; }
     if (eg1_) { cudaEventDestroy(eg1_); eg1_ = nullptr; }
     if (s3_) { cudaStreamDestroy(s3_); s3_ = nullptr; }
+    if (evx_) { retire_graph(evx_, evg_); evx_ = nullptr; evg_ = nullptr; }
   }
 
   dic_status grow_candidates(uint32_t need);
@@ -583,6 +584,21 @@ class Miner {
   cudaEvent_t eg0_ = nullptr, eg1_ = nullptr;  // the all-blocks GEMM, profiled
   double setup_ms_ = 0, graph_ms_ = 0;         // host timings (dic_stats)
   dic_status ensure_rows();
+  // event-driven loop (L_.events): the cohort pass and the generate kernel
+  // replayed in a device-side WHILE loop of one graph (rebuilt when a buffer
+  // of the lattice changes), or launched directly when they are profiled
+  bool evmode_ = false;
+  cudaGraph_t evg_ = nullptr;
+  cudaGraphExec_t evx_ = nullptr;
+  uint64_t evg_version_ = 0;
+  cudaGraphConditionalHandle evh_ = 0;
+  int cp_grid_ = 0;
+  std::vector<uint32_t> prof_iters_;  // iterations launched with profiling
+  dic_status alloc_event_tallies(uint32_t ehcap);
+  dic_status launch_event_body(bool in_graph);
+  dic_status ensure_event_graph();
+  dic_status loop_events();
+  dic_status recover_events();
 };
 
 // Compacted rows (only the frequent items, by rank) for the kernels that
@@ -724,8 +740,10 @@ dic_status Miner::launch_phase(int phase) {
         }
         if (e == cudaSuccess) {
           if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT, s_));
+          // (the direct form: one resident wave, two CTAs of 256 threads
+          // per SM at its register use; warps stride over the records)
           e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_,
-                                    direct_ ? grid_ : bs_grid_, direct_, s_);
+                                    direct_ ? sm_count() * 2 : bs_grid_, direct_, s_);
           if (prof(DIC_PROFILE_COUNT)) TRY(iv_close(s_));
         }
         if (gram) CU(cudaStreamWaitEvent(s_, ev_join_, 0));  // join
@@ -848,6 +866,31 @@ dic_status Miner::grow_trace(uint32_t need) {
   CU(cudaMemcpyAsync(N.cohort_birth, L_.cohort_birth, ((size_t)L_.tcap + 2) * 4,
                      cudaMemcpyDeviceToDevice, s_));
   drop(L_.trace); drop(L_.trace_work); drop(L_.cohort_start); drop(L_.cohort_birth);
+  L_ = N;
+  if (L_.events) TRY(alloc_event_tallies(ncap + L_.stop_max + 2));
+  ++lat_version_;
+  return DIC_OK;
+}
+
+// Per-stop tallies of the event-driven loop for stops < ehcap (the old
+// entries copied, the rest zero).
+dic_status Miner::alloc_event_tallies(uint32_t ehcap) {
+  Lattice N = L_;
+  N.ehcap = ehcap;
+  TRY(alloc(&N.eh_box, ehcap, true));
+  TRY(alloc(&N.eh_pruned, ehcap, true));
+  TRY(alloc(&N.eh_solid, ehcap, true));
+  TRY(alloc(&N.eb_list, (size_t)ehcap * EV_LIST));
+  TRY(alloc(&N.ev_work, ehcap, true));
+  if (L_.ehcap) {
+    const size_t old = L_.ehcap;
+    CU(cudaMemcpyAsync(N.eh_box, L_.eh_box, old * 4, cudaMemcpyDeviceToDevice, s_));
+    CU(cudaMemcpyAsync(N.eh_pruned, L_.eh_pruned, old * 4, cudaMemcpyDeviceToDevice, s_));
+    CU(cudaMemcpyAsync(N.eh_solid, L_.eh_solid, old * 4, cudaMemcpyDeviceToDevice, s_));
+    CU(cudaMemcpyAsync(N.eb_list, L_.eb_list, old * EV_LIST * 4, cudaMemcpyDeviceToDevice, s_));
+    CU(cudaMemcpyAsync(N.ev_work, L_.ev_work, old * 8, cudaMemcpyDeviceToDevice, s_));
+    drop(L_.eh_box); drop(L_.eh_pruned); drop(L_.eh_solid); drop(L_.eb_list); drop(L_.ev_work);
+  }
   L_ = N;
   ++lat_version_;
   return DIC_OK;
@@ -1035,6 +1078,7 @@ dic_status Miner::prepare() {
     c.n_cohorts = 1;
     c.max_k = classic ? 1 : 2;
     c.tests = tests_;
+    c.ev_limit = ~0u;
     // ---- TENSOR path for the pair cohort: needs the BITSLICE path for the
     // rest, a block below 2^24 rows (exact fp32 sums), and enough pairs to
     // fill a tile (AUTO) or an explicit request. With every block staged and
@@ -1128,6 +1172,22 @@ dic_status Miner::prepare() {
       L_.ev_pruned = ev_pruned;
     }
     pdl_ = vall_;  // one stream per stop: kernels chained by programmatic launch
+    // ---- event-driven loop: every block staged, the pairs' events
+    // precomputed, a per-block counter array that fits shared memory
+    evmode_ = false;
+    L_.events = 0;
+    if (events_ && opt_.stop_loop == 1 && stop_max64 <= EV_STOPMAX &&
+        (L_.tw == 4 || L_.tw == 8 || L_.tw == 16) &&
+        cohort_pass_smem((uint32_t)stop_max64, l1) + 1024 <= smem_optin_) {
+      evmode_ = true;
+      L_.events = 1;
+      TRY(alloc_event_tallies(L_.tcap + (uint32_t)stop_max64 + 2));
+      cp_grid_ = sm_count() * 2;
+      // split-count scratch for cohorts of up to one record per CTA
+      L_.cp_records = (uint32_t)cp_grid_;
+      TRY(alloc(&L_.cp_cnt, (size_t)L_.cp_records * stop_max64));
+      TRY(alloc(&L_.cp_tick, L_.cp_records, true));
+    }
 
     has_loop_ = true;
   }
@@ -1335,8 +1395,177 @@ dic_status Miner::launch_stop(uint32_t nstops) {
   return DIC_OK;
 }
 
+// ---- phase 3, event-driven form (Lattice.events)
+// Inactive stops closed per cohort pass at most (each advances the loop by
+// one trace row).
+constexpr uint32_t kEventBudget = 4096;
+
+// One iteration: count the cohort of the stop generated last over its pass,
+// close that stop and advance to the next stop with promotions, then
+// MAKECANDIDATES at it.
+dic_status Miner::launch_event_body(bool in_graph) {
+  struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool on) : prev(pdl_enabled()) { pdl_enabled() = on; }
+    ~PdlScope() { pdl_enabled() = prev; }
+  } scope(true);
+  if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT, s_));
+  cudaError_t e = launch_cohort_pass(L_, cp_grid_, kEventBudget, in_graph ? 1u : 0u, evh_, s_);
+  if (e != cudaSuccess) return fail(DIC_ECUDA, "cohort pass launch: %s", cudaGetErrorString(e));
+  if (prof(DIC_PROFILE_COUNT)) TRY(iv_close(s_));
+  if (prof(DIC_PROFILE_GEN)) TRY(iv_open(IV_GEN, s_));
+  e = launch_generate_finish(L_, gen_grid_, false, s_);
+  if (e != cudaSuccess) return fail(DIC_ECUDA, "generate launch: %s", cudaGetErrorString(e));
+  if (prof(DIC_PROFILE_GEN)) TRY(iv_close(s_));
+  if (!in_graph) {
+    launches_ += 2;
+    path_launches_[DIC_COUNT_BITSLICE]++;
+  }
+  return DIC_OK;
+}
+
+// The loop graph: one WHILE node whose body is launch_event_body; the
+// cohort pass ends it when DASHED is empty, a stop stalls or the iteration
+// limit is reached.
+dic_status Miner::ensure_event_graph() {
+  if (evx_ && evg_version_ == lat_version_) return DIC_OK;
+  if (evx_) {
+    retire_graph(evx_, evg_);
+    evx_ = nullptr;
+    evg_ = nullptr;
+  }
+  const auto tg0 = std::chrono::steady_clock::now();
+  CU(cudaGraphCreate(&evg_, 0));
+  CU(cudaGraphConditionalHandleCreate(&evh_, evg_, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = evh_;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, evg_, nullptr, nullptr, 0, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  CU(cudaStreamBeginCaptureToGraph(s_, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  const uint32_t pn = prof_now_;
+  prof_now_ = 0;
+  dic_status st = launch_event_body(true);
+  prof_now_ = pn;
+  cudaGraph_t outg = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s_, &outg);
+  if (st != DIC_OK) return st;
+  if (ce != cudaSuccess) return fail(DIC_ECUDA, "loop graph capture: %s", cudaGetErrorString(ce));
+  CU(cudaGraphInstantiate(&evx_, evg_, 0));
+  evg_version_ = lat_version_;
+  graph_ms_ += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tg0)
+                   .count();
+  return DIC_OK;
+}
+
+dic_status Miner::recover_events() {
+  if (h_ctrl_->error) return device_error(h_ctrl_->error);
+  while (h_ctrl_->stall) {
+    const uint32_t st = h_ctrl_->stall;
+    bool regen = false;
+    if (st == ST_HASH_EV) {
+      TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live));
+    } else if (st == ST_TRACE) {
+      TRY(grow_trace(h_ctrl_->n_trace + 2 * L_.stop_max + 64));
+    } else if (st == ST_CAND) {
+      TRY(grow_candidates(h_ctrl_->tail + n_gen_of(*h_ctrl_)));
+      regen = true;
+    } else {
+      return fail(DIC_ECUDA, "unexpected stall code %u in the event-driven loop", st);
+    }
+    h_ctrl_->stall = ST_NONE;
+    if (regen) h_ctrl_->gen_ticket = 0;  // no candidate drawn, no generate CTA done
+    CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
+    if (regen) {
+      // re-run the stop's generation into the grown store; the loop then
+      // resumes with the cohort pass, which closes the stop
+      cudaError_t e = launch_generate_finish(L_, gen_grid_, false, s_);
+      if (e != cudaSuccess) return fail(DIC_ECUDA, "generate launch: %s", cudaGetErrorString(e));
+      ++launches_;
+      TRY(sync_ctrl());
+      if (h_ctrl_->error) return device_error(h_ctrl_->error);
+    }
+  }
+  return DIC_OK;
+}
+
+dic_status Miner::loop_events() {
+  setup_ms_ = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_)
+                  .count();
+  // Profiling the count or generate kernels times whole iterations one
+  // launch at a time: the graph runs up to the next profiled iteration (its
+  // limit), that iteration is launched directly between CUDA events, and the
+  // graph resumes. Without it one graph launch runs the whole loop.
+  const bool prof_iters = (opt_.profile & (DIC_PROFILE_COUNT | DIC_PROFILE_GEN)) != 0;
+  const uint32_t every = opt_.profile_every > 1 ? opt_.profile_every : 1u;
+  const bool graph = opt_.use_graph && !(prof_iters && every == 1);
+  while (!h_ctrl_->done) {
+    const uint32_t it0 = h_ctrl_->ev_iter;
+    uint32_t graph_runs = 0, direct_runs = 0;
+    if (!prof_iters && graph) {
+      TRY(ensure_event_graph());
+      CU(cudaGraphLaunch(evx_, s_));
+      graph_runs = 1;
+    } else {
+      // segments up to the next iteration that is a multiple of `every`
+      // (iterations launched after the loop has ended do nothing; without
+      // the graph fewer are enqueued between checks)
+      const uint32_t group = opt_.steps_per_sync ? opt_.steps_per_sync : graph ? 64u : 8u;
+      uint32_t it = it0;
+      for (uint32_t seg = 0; seg < group;) {
+        const uint32_t p = prof_iters ? (it + every - 1) / every * every : it + group;
+        if (graph && p > it) {
+          TRY(ensure_event_graph());
+          cudaError_t e = launch_set_ev_limit(L_.ctrl, p, s_);
+          if (e != cudaSuccess) return fail(DIC_ECUDA, "launch: %s", cudaGetErrorString(e));
+          ++launches_;
+          CU(cudaGraphLaunch(evx_, s_));
+          ++graph_runs;
+          seg += p - it;
+          it = p;
+        } else if (p > it) {  // graphs off: plain launches up to p
+          prof_now_ = 0;
+          TRY(launch_event_body(false));
+          ++direct_runs;
+          ++seg;
+          ++it;
+          continue;
+        }
+        prof_now_ = prof_iters ? opt_.profile : 0u;
+        prof_iters_.push_back(it);
+        TRY(launch_event_body(false));
+        prof_now_ = 0;
+        ++direct_runs;
+        ++seg;
+        ++it;
+      }
+      if (graph) {
+        cudaError_t e = launch_set_ev_limit(L_.ctrl, ~0u, s_);
+        if (e != cudaSuccess) return fail(DIC_ECUDA, "launch: %s", cudaGetErrorString(e));
+        ++launches_;
+      }
+    }
+    TRY(sync_ctrl());
+    if (graph_runs) {
+      // two kernels per graph iteration (a launch ending early runs one more)
+      const uint32_t done_it = h_ctrl_->ev_iter - it0;
+      const uint32_t n = (done_it > direct_runs ? done_it - direct_runs : 0u) +
+                         (h_ctrl_->done ? 0u : 1u);
+      launches_ += 2 * n;
+      path_launches_[DIC_COUNT_BITSLICE] += n;
+    }
+    TRY(recover_events());
+  }
+  return DIC_OK;
+}
+
 dic_status Miner::loop() {
   if (!has_loop_) return DIC_OK;
+  if (evmode_) return loop_events();
   setup_ms_ = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_)
                   .count();
   const uint32_t wc = L_.wc;
@@ -1439,7 +1668,16 @@ dic_status Miner::collect(dic_result **out) {
     CU(cudaStreamSynchronize(s_));
     res->trace.assign(tr, tr + (size_t)ntr * TRACE_COLS);
     res->stats.stops = ntr;
-    if (ntr && (opt_.profile & DIC_PROFILE_COUNT)) {
+    if (evmode_ && (opt_.profile & DIC_PROFILE_COUNT)) {
+      // count work of the profiled iterations' cohort passes
+      const uint32_t ni = std::min<uint32_t>(h_ctrl_->ev_iter, L_.ehcap);
+      std::vector<unsigned long long> ew(ni);
+      if (ni) CU(cudaMemcpy(ew.data(), L_.ev_work, (size_t)ni * 8, cudaMemcpyDeviceToHost));
+      uint64_t timed = 0;
+      for (uint32_t i : prof_iters_)
+        if (i < ni) timed += ew[i] - (i ? ew[i - 1] : 0ull);
+      res->stats.count_ops_timed = timed;
+    } else if (ntr && (opt_.profile & DIC_PROFILE_COUNT)) {
       // count work of the stops whose count kernel was bracketed by events
       std::vector<unsigned long long> tw(ntr);
       CU(cudaMemcpy(tw.data(), L_.trace_work, (size_t)ntr * 8, cudaMemcpyDeviceToHost));
@@ -1510,6 +1748,8 @@ dic_status Miner::collect(dic_result **out) {
     res->supp[q] = supps[o];
   }
   res->stats.tests = tests;
+  res->stats.event_loop = evmode_ ? 1u : 0u;
+  res->stats.event_iters = evmode_ && has_loop_ ? h_ctrl_->ev_iter : 0u;
   res->stats.frequent = order.size();
   res->stats.kernel_launches = launches_;
   for (int i = 0; i < 4; ++i) res->stats.path_launches[i] = path_launches_[i];
@@ -1562,6 +1802,7 @@ static dic_status check_options(const dic_options &o) {
     return fail(DIC_EINVAL, "unknown count_path %u", o.count_path);
   if (o.algorithm > 1) return fail(DIC_EINVAL, "algorithm must be 0 or 1 (got %u)", o.algorithm);
   if (o.prestage > 1) return fail(DIC_EINVAL, "prestage must be 0 or 1 (got %u)", o.prestage);
+  if (o.stop_loop > 1) return fail(DIC_EINVAL, "stop_loop must be 0 or 1 (got %u)", o.stop_loop);
   return DIC_OK;
 }
 

@@ -17,7 +17,13 @@ enum Shape : uint8_t { SH_NIL = 0, SH_CIRCLE = 1, SH_BOX = 2 };
 // ST_HASH: the box set is too full for this stop's insertions (raised by
 // the insert kernel, or by a count kernel that inserts in its epilogue, which
 // then resumes at PH_COUNT: ST_HASH_COUNT).
-enum Stall : uint32_t { ST_NONE = 0, ST_WIDTH = 1, ST_HASH = 2, ST_CAND = 3, ST_HASH_COUNT = 4 };
+// ST_HASH_EV: the box set has no room for a new cohort's future boxes (the
+// event-driven loop's cohort pass; it resumes there). ST_TRACE: the trace or
+// the per-stop tallies are full (the event-driven advance).
+enum Stall : uint32_t {
+  ST_NONE = 0, ST_WIDTH = 1, ST_HASH = 2, ST_CAND = 3, ST_HASH_COUNT = 4, ST_HASH_EV = 5,
+  ST_TRACE = 6
+};
 enum Phase : int { PH_COUNT = 0, PH_PROMOTE = 1, PH_HASH = 2, PH_GEN = 3 };
 
 constexpr int TRACE_COLS = 9;
@@ -63,6 +69,16 @@ struct Ctrl {
   unsigned long long tests;  // candidate-transaction tests so far
   unsigned long long work;   // algorithmic integer ops of the count kernels
   unsigned long long gram_rows;  // block rows whose pair cohort the GEMM counted
+  // event-driven loop (Lattice.events): CTAs of the cohort pass that have
+  // finished; iterations (cohort pass + generate) completed; the loop graph
+  // ends once ev_iter reaches ev_limit
+  uint32_t ev_ticket;
+  uint32_t ev_iter;
+  uint32_t ev_limit;
+  // 1 while a stop is prepared (tallies and promoted list) and awaits
+  // MAKECANDIDATES and its close in the next cohort pass
+  uint32_t ev_pending;
+  uint32_t pad_ev;
 };
 
 __host__ __device__ inline uint32_t n_gen_of(const Ctrl &c) { return (uint32_t)c.gen_ticket; }
@@ -160,11 +176,38 @@ struct Lattice {
   // and at stop_max ev_pruned[0] pair boxes complete their pass. Their
   // supports hold the full-pass totals from the start.
   uint32_t pair_events;
-  uint32_t pad3;
+  // 1: event-driven loop: every cohort born in the loop is counted over its
+  // whole pass at once (k_cohort_pass) and its promotions, erasures and
+  // solidifications are tallied per stop in advance: eh_box[s], eh_pruned[s],
+  // eh_solid[s] for stops s < ehcap, the first EV_LIST records promoted at s
+  // in eb_list[s * EV_LIST ..]. Boxes promoted at a later stop are already in
+  // the box set with that stop in cpromo; MAKECANDIDATES treats them as
+  // absent until then.
+  uint32_t events;
   const uint32_t *ev_off;     // [stop_max + 2]
   const uint32_t *ev_list;    // [pair_end]
   const uint32_t *ev_pruned;  // [stop_max + 1]
+  uint32_t *eh_box;           // [ehcap]
+  uint32_t *eh_pruned;        // [ehcap]
+  uint32_t *eh_solid;         // [ehcap]
+  uint32_t *eb_list;          // [ehcap][EV_LIST]
+  unsigned long long *ev_work;  // [ehcap] Ctrl.work after the cohort pass of
+                                // iteration i (event-driven loop)
+  uint32_t ehcap;
+  // cohorts of at most cp_records records split each record's blocks over
+  // several CTAs: per-block counts in cp_cnt[record][stop_max], the parts
+  // done in cp_tick[record] (zero between passes)
+  uint32_t cp_records;
+  uint32_t *cp_cnt;
+  uint32_t *cp_tick;
 };
+
+// Records promoted at one stop listed directly by the event-driven loop
+// (more are found by a scan of the window).
+constexpr uint32_t EV_LIST = 128;
+// Largest block count (stop_max) the event-driven loop takes: the cohort
+// pass keeps one counter per block in shared memory.
+constexpr uint32_t EV_STOPMAX = 8192;
 
 // The column buffer of stop g's block.
 __device__ __forceinline__ uint32_t *vcols(const Lattice &L, uint32_t g) {
@@ -270,7 +313,19 @@ cudaError_t launch_hash_insert(Lattice L, int grid, cudaStream_t s);
 // bookkeeping: trace row, cohort, CHECKFULLPASS, loop test.
 // With slice_next, the same launch also builds the BITSLICE columns of the
 // next stop's block (the count of this stop has finished reading them).
+// (Lattice.events: MAKECANDIDATES only; the cohort pass closes the stop.)
 cudaError_t launch_generate_finish(Lattice L, int grid, bool slice_next, cudaStream_t s);
+// Event-driven loop: count the cohort MAKECANDIDATES emitted at the prepared
+// stop over its whole pass and tally its events, then close that stop and
+// every following one without promotions (at most `budget`) and prepare the
+// next stop with promotions (kernels_events.cu). Inside the loop graph
+// (`use_cond` 1) it ends the graph's WHILE loop (handle `cond`) when nothing
+// is prepared or the iteration limit is reached.
+cudaError_t launch_cohort_pass(Lattice L, int grid, uint32_t budget, uint32_t use_cond,
+                               unsigned long long cond, cudaStream_t s);
+// Set Ctrl.ev_limit (stream-ordered).
+cudaError_t launch_set_ev_limit(Ctrl *C, uint32_t limit, cudaStream_t s);
+size_t cohort_pass_smem(uint32_t stop_max, uint32_t l1);
 cudaError_t launch_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap, cudaStream_t s);
 cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
                                  uint32_t *out_count, cudaStream_t s);

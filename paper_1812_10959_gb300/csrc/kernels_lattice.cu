@@ -364,12 +364,12 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_ne
   if (threadIdx.x == 0) s_c = *C;
   __syncthreads();
   const uint32_t P = s_c.n_newbox, g = s_c.step, base = s_c.tail, l1 = L.l1;
-  if (s_c.stall || s_c.done) return;
+  if (s_c.stall || s_c.done || s_c.error) return;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slice_next)  // the columns of stop g+1 (count of stop g is complete)
     slice_block_warps(L, g + 1, tid >> 5, stride >> 5);
-  if (L.vall) {
+  if (L.vall && !L.events) {
     // bring the next stop's columns into L2 ahead of its count (one
     // 128-byte line per thread)
     const uint32_t *nv = vcols(L, g + 1);
@@ -380,6 +380,9 @@ __global__ void __launch_bounds__(256) k_generate_finish(Lattice L, int slice_ne
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
     gen_candidate(L, C, (uint32_t)(w / l1), (uint32_t)(w % l1), g, base);
   }
+  // the event-driven loop's next cohort pass closes the stop (it reads the
+  // final candidate count from the loop state)
+  if (L.events) return;
   // the last CTA to finish closes the stop: its ticket (the high half of the
   // word whose low half every emitted candidate incremented, all of this
   // CTA's before the barrier) returns the stop's final candidate count

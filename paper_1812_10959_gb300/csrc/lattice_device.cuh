@@ -170,9 +170,9 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
     const uint64_t l1 = L.l1;
     const uint64_t i0 = r < a0 ? pair_record(r, a0, l1) : pair_record(a0, r, l1);
     const uint64_t i1 = r < a1 ? pair_record(r, a1, l1) : pair_record(a1, r, l1);
-    // promotion stops (~0: not a box)
+    // promotion stops (~0: not a box; a stop after g: not a box yet)
     const uint32_t p0 = L.cpromo[i0], p1 = L.cpromo[i1];
-    if (p0 == ~0u || p1 == ~0u) return;
+    if (p0 > g || p1 > g) return;
     if (kA == 2) {
       // A = {a0, a1}: the 2-subsets of C other than A are the pair records
       // {a1, r} = C \ {a0} and {a0, r} = C \ {a1}, both boxes by the check
@@ -220,8 +220,10 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
       ++k;
       const uint64_t bj = 1ull << b;
       const uint64_t sumS = sumC - hterm(Ci, i) + hterm(Ci & ~bj, i);
+      // (v = promotion stop + 1; the event-driven loop inserts boxes before
+      // their promotion stop, which do not count until then)
       const uint32_t v = box_lookup(L, A, wr, br, i, bj, sumS);
-      if (v == 0 || (i * 64 + b < r && v == g + 1)) return;
+      if (v == 0 || v > g + 1 || (i * 64 + b < r && v == g + 1)) return;
     }
   }
   const uint32_t pos = base + (uint32_t)atomicAdd(&C->gen_ticket, 1ull);
@@ -248,19 +250,19 @@ __device__ __forceinline__ void gen_candidate(const Lattice &L, Ctrl *C, uint32_
 // End of stop g for one query: trace row, test count, the new cohort,
 // CHECKFULLPASS (cohorts whose full pass is complete leave the window [head,
 // tail)), |DASHED| and the loop test of Algorithm 2.
-__device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, const Ctrl &c);
+__device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, Ctrl &c);
 
 __device__ __forceinline__ void finish_stop(const Lattice &L, Ctrl *C) {
   // one copy of the loop state in registers (independent loads, one round
   // trip)
-  const Ctrl c = *C;
+  Ctrl c = *C;
   finish_stop_with(L, C, c);
 }
 
 // finish_stop from a copy of the loop state taken by the caller (with the
 // stop's final candidate count); every field this stop changes is stored
-// once at the end.
-__device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, const Ctrl &c) {
+// once at the end, and the caller's copy is brought to the same state.
+__device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, Ctrl &c) {
   const uint32_t g = c.step;
   uint32_t stop;
   uint64_t first, last;
@@ -268,6 +270,8 @@ __device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, cons
   if (c.n_trace >= L.tcap) {
     C->error = 4;  // DIC_ECAPACITY
     C->done = 1;
+    c.error = 4;
+    c.done = 1;
     return;
   }
   unsigned long long *row = L.trace + (uint64_t)c.n_trace * TRACE_COLS;
@@ -282,6 +286,7 @@ __device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, cons
     L.cohort_birth[n_cohorts] = g;
     n_cohorts += 1;
     C->last_birth = g;
+    c.last_birth = g;
   }
   const uint32_t tail = c.tail + n_gen;
   const uint32_t n_live = c.n_live - c.n_pruned - c.n_solid + n_gen;
@@ -301,18 +306,32 @@ __device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, cons
       ++ch;
     }
   }
-  C->tests = c.tests + (unsigned long long)c.n_live * (last - first);
-  C->n_cohorts = n_cohorts;
-  C->tail = tail;
-  C->hash_used = c.hash_used + c.n_newbox;
-  C->n_live = n_live;
-  C->cohort_head = ch;
-  C->head = head;
-  C->head_birth = hb;
+  c.tests = c.tests + (unsigned long long)c.n_live * (last - first);
+  c.n_cohorts = n_cohorts;
+  c.tail = tail;
+  c.hash_used = c.hash_used + c.n_newbox;
+  c.n_live = n_live;
+  c.cohort_head = ch;
+  c.head = head;
+  c.head_birth = hb;
+  c.n_newbox = 0; c.n_pruned = 0; c.n_solid = 0; c.gen_ticket = 0;
+  c.n_trace = c.n_trace + 1;
+  c.step = g + 1;
+  C->tests = c.tests;
+  C->n_cohorts = c.n_cohorts;
+  C->tail = c.tail;
+  C->hash_used = c.hash_used;
+  C->n_live = c.n_live;
+  C->cohort_head = c.cohort_head;
+  C->head = c.head;
+  C->head_birth = c.head_birth;
   C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->gen_ticket = 0;
-  C->n_trace = c.n_trace + 1;
-  C->step = g + 1;
-  if (n_live == 0) C->done = 1;
+  C->n_trace = c.n_trace;
+  C->step = c.step;
+  if (n_live == 0) {
+    C->done = 1;
+    c.done = 1;
+  }
 }
 
 

@@ -32,7 +32,7 @@ class Options(ctypes.Structure):
                 ("profile_every", ctypes.c_uint32), ("tile_words", ctypes.c_uint32),
                 ("count_form", ctypes.c_uint32), ("algorithm", ctypes.c_uint32),
                 ("prestage", ctypes.c_uint32), ("solo_rows", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("stop_loop", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("gen_launches", ctypes.c_uint64), ("gram_flops", ctypes.c_uint64),
                 ("count_ops_timed", ctypes.c_uint64), ("setup_ms", ctypes.c_double),
                 ("graph_ms", ctypes.c_double), ("collect_ms", ctypes.c_double),
-                ("reserved", ctypes.c_uint64 * 1)]
+                ("event_loop", ctypes.c_uint32), ("event_iters", ctypes.c_uint32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "path_launches")}
@@ -267,12 +267,14 @@ ALGORITHMS = {"paralleldic": 0, "classic": 1}
 
 
 PRESTAGE = {"auto": 0, "off": 1}
+STOP_LOOPS = {"per-stop": 0, "events": 1}
 
 
 def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
             profile=False, max_candidates: int = 0, profile_every: int = 0,
             tile_words: int = 0, count_form: str = "auto",
-            algorithm: str = "paralleldic", prestage: str = "auto") -> Options:
+            algorithm: str = "paralleldic", prestage: str = "auto",
+            stop_loop: str = "per-stop") -> Options:
     o = Options()
     _lib.dic_options_init(ctypes.byref(o))
     o.count_path = PATHS[path]
@@ -284,6 +286,7 @@ def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
     o.count_form = COUNT_FORMS[count_form]
     o.algorithm = ALGORITHMS[algorithm]
     o.prestage = PRESTAGE[prestage]
+    o.stop_loop = STOP_LOOPS[stop_loop]
     o.max_candidates = max_candidates
     return o
 
@@ -292,14 +295,17 @@ def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
          profile=False, steps_per_sync: int = 0, use_graph: bool = True,
          max_candidates: int = 0, profile_every: int = 0, tile_words: int = 0,
          count_form: str = "auto", algorithm: str = "paralleldic",
-         prestage: str = "auto") -> Result:
+         prestage: str = "auto", stop_loop: str = "per-stop") -> Result:
     """All itemsets with support >= minsup (integer count), blocks of M rows.
     algorithm: "paralleldic" (Algorithm 2, first pass then pairs) or
     "classic" (Algorithm 1, every 1-itemset a dashed circle). prestage:
     "auto" (stage every block's columns, and count the pair cohort over the
-    whole pass, before the loop when they fit) or "off" (per stop)."""
+    whole pass, before the loop when they fit) or "off" (per stop).
+    stop_loop: "per-stop" (every dashed itemset counted at every stop) or
+    "events" (event-driven where it applies: each cohort counted over its
+    whole pass when born, only stops with promotions generate)."""
     o = options(path, steps_per_sync, use_graph, profile, max_candidates, profile_every,
-                tile_words, count_form, algorithm, prestage)
+                tile_words, count_form, algorithm, prestage, stop_loop)
     h = ctypes.c_void_p()
     _check(_lib.dic_mine_ex(db.handle, minsup, M, ctypes.byref(o), _stream_handle(stream),
                             ctypes.byref(h)))
