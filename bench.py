@@ -55,7 +55,7 @@ COUNT_KERNELS = {1: "k_count_rows", 2: "k_count_direct", 3: "k_count_direct"}  #
 FP8_PER_BF16 = 2.0
 # the timed steps bracket the dominant kernel kind with CUDA events on one
 # stop in this many
-PROFILE_EVERY = 32
+PROFILE_EVERY = 64
 # timed kinds of the stop loop: stats key prefix -> profile name, kernels
 KINDS = {"count": "count", "gram": "gram", "settle": "settle", "gen": "gen"}
 KIND_KERNELS = {"gram": "k_gram_pairs", "settle": "k_settle_pairs",

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -234,6 +235,28 @@ static void init_pool(int dev) {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   if (dev < 64) done_mask.fetch_or(1ull << dev);
+}
+
+// Free device memory for the prestaging rule, refreshed at most every
+// 50 ms per device (the query costs tens of microseconds; the rule only
+// needs its order of magnitude).
+static size_t free_device_memory() {
+  static std::mutex mu;
+  static std::map<int, std::pair<std::chrono::steady_clock::time_point, size_t>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto now = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end() && now - it->second.first < std::chrono::milliseconds(50))
+    return it->second.second;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  cache[dev] = {now, free_b};
+  return free_b;
 }
 
 static int sm_count() {
@@ -485,6 +508,7 @@ class Miner {
   dic_status launch_stop_from(int phase);
   dic_status sync_ctrl();
   int count_path_for_stop() const;
+  uint32_t stop_profile_bits() const;
 
   const dic_db *db_;
   uint32_t minsup_;
@@ -571,6 +595,7 @@ class Miner {
   std::vector<uint32_t> set_items_, set_off_;
   std::vector<uint32_t> supps_;
   size_t n_first_ = 0;  // leading itemsets from the first pass (item order)
+  size_t n_ordered_ = 0;  // leading itemsets already in canonical order
   bool has_loop_ = false;
   Ctrl *ext_ctrl_ = nullptr;
   bool own_h_ctrl_ = false;
@@ -579,7 +604,9 @@ class Miner {
   // counted over the whole pass with precomputed events (L_.pair_events),
   // and the stop kernels chained by programmatic dependent launch
   bool vall_ = false, events_ = false, pc_wide_ = false, pdl_ = false;
-  int32_t *d_rank_ = nullptr;  // rank of each item (-1: not frequent)
+  int32_t *d_rank_ = nullptr;  // rank of each item (-1: not frequent), chunk
+                               // starts, then the item of each rank
+  size_t item_of_off_ = 0;     // where the item of each rank starts in d_rank_
   bool rows_ready_ = false;    // L_.rows (compacted rows) built
   cudaEvent_t eg0_ = nullptr, eg1_ = nullptr;  // the all-blocks GEMM, profiled
   double setup_ms_ = 0, graph_ms_ = 0;         // host timings (dic_stats)
@@ -992,6 +1019,9 @@ dic_status Miner::prepare() {
         rank_of[(size_t)W * 64 + c] = (int32_t)r;
       }
     }
+    // (then the item of every rank, for the result's item ids)
+    item_of_off_ = rank_of.size();
+    for (uint32_t r = 0; r < l1; ++r) rank_of.push_back((int32_t)l1items[r]);
     TRY(alloc(&d_rank_, rank_of.size()));
     CU(cudaMemcpyAsync(d_rank_, rank_of.data(), rank_of.size() * 4, cudaMemcpyHostToDevice, s_));
 
@@ -1024,8 +1054,7 @@ dic_status Miner::prepare() {
     // query runs its own loop and they fit the memory rule (a quarter of the
     // free device memory, at most 16 GiB); otherwise the loop transposes
     // each stop's block (double-buffered, one stop ahead).
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
+    const size_t free_b = free_device_memory();
     const uint64_t stage_cap = std::min<uint64_t>(free_b / 4, 16ull << 30);
     vall_ = false;
     if (bs_ok_ && vdouble_ && opt_.prestage == 0 &&
@@ -1274,9 +1303,18 @@ dic_status Miner::recover() {
   return DIC_OK;
 }
 
+// Profiling bits that put CUDA events into a stop (the pair GEMM runs once
+// before the loop when the pair events are precomputed).
+uint32_t Miner::stop_profile_bits() const {
+  uint32_t b = DIC_PROFILE_COUNT | DIC_PROFILE_GEN | DIC_PROFILE_SETTLE;
+  if (!L_.pair_events) b |= DIC_PROFILE_GRAM;
+  return opt_.profile & b;
+}
+
 dic_status Miner::launch_stop(uint32_t nstops) {
-  prof_now_ = (opt_.profile_every <= 1 || pred_step_ % opt_.profile_every == 0) ? opt_.profile
-                                                                               : 0u;
+  prof_now_ = (opt_.profile_every <= 1 || pred_step_ % opt_.profile_every == 0)
+                  ? stop_profile_bits()
+                  : 0u;
   if (!opt_.use_graph) {
     for (uint32_t i = 0; i < nstops; ++i) TRY(launch_stop_from(PH_COUNT));
     return DIC_OK;
@@ -1600,8 +1638,9 @@ dic_status Miner::loop() {
       if (multi) {
         const uint32_t cap = std::min<uint32_t>(kStopsPerGraph, group - i);
         u = 0;
-        while (u < cap && !(opt_.profile && (opt_.profile_every <= 1 ||
-                                             (pred_step_ + u) % opt_.profile_every == 0)))
+        const bool prof_stops = stop_profile_bits() != 0;
+        while (u < cap && !(prof_stops && (opt_.profile_every <= 1 ||
+                                           (pred_step_ + u) % opt_.profile_every == 0)))
           ++u;
         if (u == 0) u = 1;  // the profiled stop itself, alone
       }
@@ -1630,42 +1669,54 @@ dic_status Miner::collect(dic_result **out) {
     const uint32_t tail = h_ctrl_->tail;
     res->stats.candidates = tail;
 
-    // ---- SOLID boxes (k >= 2) to the host
+    // ---- SOLID boxes (k >= 2) to the host, in record order, as item ids
+    const uint32_t nch = collect_chunks(tail);
     uint32_t *d_idx = nullptr, *d_cnt = nullptr;
-    TRY(alloc(&d_idx, tail));
-    TRY(alloc(&d_cnt, 1, true));
-    CU(launch_collect_boxes(L_, tail, d_idx, d_cnt, s_));
-    ++launches_;
+    TRY(alloc(&d_idx, std::max<uint32_t>(tail, 1)));
+    TRY(alloc(&d_cnt, (size_t)nch + 1));
+    CU(launch_collect_boxes(L_, tail, d_cnt, d_idx, s_));
+    launches_ += 3;
     PinnedBuf<uint32_t> h_nbox;
     CU(h_nbox.get(1));
-    CU(cudaMemcpyAsync(h_nbox.p, d_cnt, 4, cudaMemcpyDeviceToHost, s_));
+    CU(cudaMemcpyAsync(h_nbox.p, d_cnt + nch, 4, cudaMemcpyDeviceToHost, s_));
     CU(cudaStreamSynchronize(s_));
-    const uint32_t nbox = *h_nbox.p;
+    const uint32_t nbox = tail ? *h_nbox.p : 0u;
+    // masks only when some itemset has more items than a record's ranks
+    const bool long_sets = h_ctrl_->max_k > (uint32_t)KRMAX;
+    uint32_t *d_k = nullptr, *d_s = nullptr, *d_it = nullptr;
     uint64_t *d_om = nullptr;
-    uint32_t *d_os = nullptr;
-    TRY(alloc(&d_om, (size_t)nbox * wc));
-    TRY(alloc(&d_os, nbox));
-    CU(launch_gather_boxes(L_, d_idx, nbox, d_om, d_os, s_));
+    TRY(alloc(&d_k, nbox));
+    TRY(alloc(&d_s, nbox));
+    TRY(alloc(&d_it, (size_t)nbox * KRMAX));
+    if (long_sets) TRY(alloc(&d_om, (size_t)nbox * wc));
+    CU(launch_gather_boxes(L_, d_idx, nbox,
+                           reinterpret_cast<const uint32_t *>(d_rank_) + item_of_off_, d_k, d_s,
+                           d_it, d_om, s_));
     ++launches_;
     // staged in reused page-locked host blocks
+    PinnedBuf<uint32_t> hk_b, hs_b, hi_b, hx_b;
     PinnedBuf<uint64_t> hm_b;
-    PinnedBuf<uint32_t> hs_b;
     PinnedBuf<unsigned long long> tr_b;
     const uint32_t ntr = h_ctrl_->n_trace;
-    CU(hm_b.get((size_t)nbox * wc));
+    CU(hk_b.get(nbox));
     CU(hs_b.get(nbox));
+    CU(hi_b.get((size_t)nbox * KRMAX));
+    CU(hx_b.get(nbox));
+    if (long_sets) CU(hm_b.get((size_t)nbox * wc));
     CU(tr_b.get((size_t)ntr * TRACE_COLS));
-    const uint64_t *hm = hm_b.p;
-    const uint32_t *hs = hs_b.p;
-    const unsigned long long *tr = tr_b.p;
     if (nbox) {
-      CU(cudaMemcpyAsync(hm_b.p, d_om, (size_t)nbox * wc * 8, cudaMemcpyDeviceToHost, s_));
-      CU(cudaMemcpyAsync(hs_b.p, d_os, (size_t)nbox * 4, cudaMemcpyDeviceToHost, s_));
+      CU(cudaMemcpyAsync(hk_b.p, d_k, (size_t)nbox * 4, cudaMemcpyDeviceToHost, s_));
+      CU(cudaMemcpyAsync(hs_b.p, d_s, (size_t)nbox * 4, cudaMemcpyDeviceToHost, s_));
+      CU(cudaMemcpyAsync(hi_b.p, d_it, (size_t)nbox * KRMAX * 4, cudaMemcpyDeviceToHost, s_));
+      CU(cudaMemcpyAsync(hx_b.p, d_idx, (size_t)nbox * 4, cudaMemcpyDeviceToHost, s_));
+      if (long_sets)
+        CU(cudaMemcpyAsync(hm_b.p, d_om, (size_t)nbox * wc * 8, cudaMemcpyDeviceToHost, s_));
     }
     if (ntr)
       CU(cudaMemcpyAsync(tr_b.p, L_.trace, (size_t)ntr * TRACE_COLS * 8, cudaMemcpyDeviceToHost,
                          s_));
     CU(cudaStreamSynchronize(s_));
+    const unsigned long long *tr = tr_b.p;
     res->trace.assign(tr, tr + (size_t)ntr * TRACE_COLS);
     res->stats.stops = ntr;
     if (evmode_ && (opt_.profile & DIC_PROFILE_COUNT)) {
@@ -1689,22 +1740,40 @@ dic_status Miner::collect(dic_result **out) {
       }
       res->stats.count_ops_timed = timed;
     }
-    // ranks -> item ids (rank order is item order, so items come out sorted)
-    set_items_.reserve(set_items_.size() + (size_t)nbox * 4);
+    // item lists (items come out ascending: rank order is item order)
+    const uint32_t *hk = hk_b.p, *hsup = hs_b.p, *hit = hi_b.p;
+    set_items_.reserve(set_items_.size() + (size_t)nbox * 3);
     for (uint32_t q = 0; q < nbox; ++q) {
       set_off_.push_back((uint32_t)set_items_.size());
-      for (uint32_t w = 0; w < wc; ++w)
-        for (uint64_t x = hm[(size_t)q * wc + w]; x; x &= x - 1)
-          set_items_.push_back(l1items[w * 64 + (uint32_t)__builtin_ctzll(x)]);
-      supps.push_back(hs[q]);
+      const uint32_t k = hk[q];
+      if (k <= (uint32_t)KRMAX) {
+        set_items_.insert(set_items_.end(), hit + (size_t)q * KRMAX, hit + (size_t)q * KRMAX + k);
+      } else {
+        for (uint32_t w = 0; w < wc; ++w)
+          for (uint64_t x = hm_b.p[(size_t)q * wc + w]; x; x &= x - 1)
+            set_items_.push_back(l1items[w * 64 + (uint32_t)__builtin_ctzll(x)]);
+      }
+      supps.push_back(hsup[q]);
+    }
+    // boxes of the first pass's pair cohort (records below pair_lex_end)
+    // are already in canonical order and precede all longer itemsets
+    n_ordered_ = n_first_;
+    if (L_.pairs_lex) {
+      const uint32_t pend = (uint32_t)((uint64_t)L_.l1 * (L_.l1 - (L_.l1 ? 1 : 0)) / 2);
+      const uint32_t *hx = hx_b.p;
+      uint32_t q = 0;
+      while (q < nbox && hx[q] < pend) ++q;
+      n_ordered_ += q;
     }
   } else {
     res->stats.candidates = 0;
+    n_ordered_ = n_first_;
   }
   // ---- canonical order (size, then lexicographic), original item space.
-  // The 1-itemsets come first and already in order; the rest are sorted by
-  // size and a key holding their first eight item ids (16 bits each, first
-  // item most significant), comparing whole item lists only on equal keys.
+  // The 1-itemsets and the pair cohort's boxes come first and already in
+  // order; the rest are sorted by size and a key holding their first eight
+  // item ids (16 bits each, first item most significant), comparing whole
+  // item lists only on equal keys.
   const size_t nset = set_off_.size();
   set_off_.push_back((uint32_t)set_items_.size());
   const uint32_t *items = set_items_.data();
@@ -1712,7 +1781,7 @@ dic_status Miner::collect(dic_result **out) {
   std::vector<uint32_t> order(nset);
   for (uint32_t i = 0; i < nset; ++i) order[i] = i;
   {
-    const size_t n1 = std::min(nset, n_first_);  // the first pass's 1-itemsets, in order
+    const size_t n1 = std::min(nset, n_ordered_);
     struct Key { uint64_t hi, lo; uint32_t k, idx; };
     std::vector<Key> keys(nset - n1);
     const bool narrow = db_->m <= 65536u;

@@ -327,10 +327,17 @@ cudaError_t launch_cohort_pass(Lattice L, int grid, uint32_t budget, uint32_t us
 cudaError_t launch_set_ev_limit(Ctrl *C, uint32_t limit, cudaStream_t s);
 size_t cohort_pass_smem(uint32_t stop_max, uint32_t l1);
 cudaError_t launch_rehash(Lattice L, const uint32_t *oslot, uint32_t ocap, cudaStream_t s);
-cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
-                                 uint32_t *out_count, cudaStream_t s);
-cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
-                                uint32_t *supp, cudaStream_t s);
+// The boxes among records [0, tail) in record order: out_idx[0 .. total),
+// total = chunk_cnt[collect_chunks(tail)] (chunk_cnt holds
+// collect_chunks(tail) + 1 words).
+cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *chunk_cnt, uint32_t *out_idx,
+                                 cudaStream_t s);
+uint32_t collect_chunks(uint32_t tail);
+// Size, support and item ids (item_of[rank], at most KRMAX per box, row
+// stride KRMAX) of boxes idx[0 .. cnt); masks (row stride wc) when not NULL.
+cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt,
+                                const uint32_t *item_of, uint32_t *out_k, uint32_t *out_supp,
+                                uint32_t *items, uint64_t *masks, cudaStream_t s);
 
 // Columns of every block of the pass (L.vall), transposed once from the
 // original rows B[n][W] (item p -> rank rank_of[p], -1 = not frequent);

@@ -407,36 +407,122 @@ cudaError_t launch_generate_finish(Lattice L, int grid, bool slice_next, cudaStr
 }
 
 // --------------------------------------------------------------- output
-__global__ void k_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx, uint32_t *out_count) {
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < tail; c += gridDim.x * blockDim.x)
-    if (L.cshape[c] == SH_BOX) out_idx[atomicAdd(out_count, 1u)] = c;
-}
+// The boxes among records [0, tail), compacted in record order (so the
+// first pass's pair records, which are in lexicographic rank order, come out
+// in canonical order), in three launches: box counts per chunk of
+// BOX_CHUNK records, an exclusive scan of those counts (one CTA), and a
+// scatter of each chunk's box indices at its offset.
+constexpr uint32_t BOX_CHUNK = 1024;
+constexpr uint32_t BOX_THREADS = 256;
 
-cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *out_idx,
-                                   uint32_t *out_count, cudaStream_t s) {
-  if (tail == 0) return cudaSuccess;
-  int grid = (int)((tail + 255) / 256 < 65535u * 4 ? (tail + 255) / 256 : 65535u * 4);
-  k_collect_boxes<<<grid, 256, 0, s>>>(L, tail, out_idx, out_count);
-  return cudaGetLastError();
-}
-
-__global__ void k_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
-                               uint32_t *supp) {
-  const uint64_t total = (uint64_t)cnt * L.wc;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t q = (uint32_t)(i / L.wc), w = (uint32_t)(i % L.wc);
-    masks[i] = L.cmask[(uint64_t)idx[q] * L.wc + w];
-    if (w == 0) supp[q] = L.csupp[idx[q]];
+__global__ void __launch_bounds__(BOX_THREADS) k_box_count(Lattice L, uint32_t tail,
+                                                           uint32_t *chunk_cnt) {
+  const uint64_t c0 = (uint64_t)blockIdx.x * BOX_CHUNK;
+  uint32_t n = 0;
+  for (uint64_t c = c0 + threadIdx.x; c < c0 + BOX_CHUNK && c < tail; c += BOX_THREADS)
+    n += L.cshape[c] == SH_BOX ? 1u : 0u;
+  n = __reduce_add_sync(0xffffffffu, n);
+  __shared__ uint32_t s_n[BOX_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) s_n[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t w = 0; w < BOX_THREADS / 32; ++w) t += s_n[w];
+    chunk_cnt[blockIdx.x] = t;
   }
 }
 
-cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt, uint64_t *masks,
-                                uint32_t *supp, cudaStream_t s) {
+// In place: chunk_cnt[i] = boxes before chunk i; chunk_cnt[nchunks] = all.
+__global__ void __launch_bounds__(1024) k_box_scan(uint32_t *chunk_cnt, uint32_t nchunks) {
+  __shared__ uint32_t part[1024];
+  const uint32_t per = (nchunks + 1023) / 1024;
+  const uint32_t i0 = threadIdx.x * per;
+  uint32_t sum = 0;
+  for (uint32_t i = i0; i < i0 + per && i < nchunks; ++i) sum += chunk_cnt[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t t = 0; t < 1024; ++t) { const uint32_t v = part[t]; part[t] = run; run += v; }
+    chunk_cnt[nchunks] = run;
+  }
+  __syncthreads();
+  uint32_t run = part[threadIdx.x];
+  for (uint32_t i = i0; i < i0 + per && i < nchunks; ++i) {
+    const uint32_t v = chunk_cnt[i];
+    chunk_cnt[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(BOX_THREADS) k_box_scatter(Lattice L, uint32_t tail,
+                                                             const uint32_t *chunk_off,
+                                                             uint32_t *out_idx) {
+  __shared__ uint32_t s_w[BOX_THREADS / 32];
+  __shared__ uint32_t s_base;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_base = chunk_off[blockIdx.x];
+  const uint64_t c0 = (uint64_t)blockIdx.x * BOX_CHUNK;
+  for (uint32_t r0 = 0; r0 < BOX_CHUNK; r0 += BOX_THREADS) {
+    const uint64_t c = c0 + r0 + threadIdx.x;
+    const bool box = c < tail && L.cshape[c] == SH_BOX;
+    const uint32_t bal = __ballot_sync(0xffffffffu, box);
+    __syncthreads();  // s_base and s_w of the previous round are settled
+    if (lane == 0) s_w[warp] = __popc(bal);
+    __syncthreads();
+    uint32_t before = s_base;
+    for (uint32_t w = 0; w < warp; ++w) before += s_w[w];
+    if (box) out_idx[before + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)c;
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (uint32_t w = 0; w < BOX_THREADS / 32; ++w) s_base += s_w[w];
+  }
+}
+
+cudaError_t launch_collect_boxes(Lattice L, uint32_t tail, uint32_t *chunk_cnt, uint32_t *out_idx,
+                                 cudaStream_t s) {
+  if (tail == 0) return cudaMemsetAsync(chunk_cnt, 0, 4, s);
+  const uint32_t nchunks = (uint32_t)(((uint64_t)tail + BOX_CHUNK - 1) / BOX_CHUNK);
+  k_box_count<<<nchunks, BOX_THREADS, 0, s>>>(L, tail, chunk_cnt);
+  k_box_scan<<<1, 1024, 0, s>>>(chunk_cnt, nchunks);
+  k_box_scatter<<<nchunks, BOX_THREADS, 0, s>>>(L, tail, chunk_cnt, out_idx);
+  return cudaGetLastError();
+}
+
+uint32_t collect_chunks(uint32_t tail) {
+  return (uint32_t)(((uint64_t)tail + BOX_CHUNK - 1) / BOX_CHUNK);
+}
+
+// Box q = record idx[q]: its size and support, and its items as original
+// item ids (item_of[rank], ascending) in items[q][0 .. min(k, KRMAX)); with
+// `masks` (itemsets longer than KRMAX exist) also its rank mask.
+__global__ void k_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt,
+                               const uint32_t *item_of, uint32_t *out_k, uint32_t *out_supp,
+                               uint32_t *items, uint64_t *masks) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = idx[q];
+    const uint32_t k = L.ck[c];
+    out_k[q] = k;
+    out_supp[q] = L.csupp[c];
+    const uint4 *rk4 = reinterpret_cast<const uint4 *>(L.cranks + (uint64_t)c * KRMAX);
+    const uint4 ra = rk4[0], rb = rk4[1];
+    const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+    const uint32_t kk = k < (uint32_t)KRMAX ? k : (uint32_t)KRMAX;
+    for (uint32_t j = 0; j < kk; ++j)
+      items[q * KRMAX + j] = item_of[(rw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu];
+    if (masks)
+      for (uint32_t w = 0; w < L.wc; ++w) masks[q * L.wc + w] = L.cmask[(uint64_t)c * L.wc + w];
+  }
+}
+
+cudaError_t launch_gather_boxes(Lattice L, const uint32_t *idx, uint32_t cnt,
+                                const uint32_t *item_of, uint32_t *out_k, uint32_t *out_supp,
+                                uint32_t *items, uint64_t *masks, cudaStream_t s) {
   if (cnt == 0) return cudaSuccess;
-  uint64_t want = ((uint64_t)cnt * L.wc + 255) / 256;
-  int grid = (int)(want < 65535ull * 4 ? want : 65535ull * 4);
-  k_gather_boxes<<<grid, 256, 0, s>>>(L, idx, cnt, masks, supp);
+  const uint64_t want = ((uint64_t)cnt + 255) / 256;
+  const int grid = (int)(want < 65535ull * 4 ? want : 65535ull * 4);
+  k_gather_boxes<<<grid, 256, 0, s>>>(L, idx, cnt, item_of, out_k, out_supp, items, masks);
   return cudaGetLastError();
 }
 
