@@ -13,7 +13,8 @@
 // transposition, 32 rows per word): for every 128-row chunk, twelve
 // expander warps (a thread per rank row) load each rank's four column words
 // (a few chunks ahead, one 16-byte load) and write them to shared memory as
-// e4m3 bytes (0, or 0x08 = 2^-6 for a set bit) in the K-major no-swizzle core-matrix layout
+// e4m3 bytes (0, or 0x08 = 2^-6 for a set bit; the chunk's rows in a fixed
+// order along K, the same for both operands) in the K-major no-swizzle core-matrix layout
 // of tcgen05 (8 ranks x 16 rows per 128-byte core matrix), through a
 // 4-stage ring guarded by mbarriers; one thread of a seventeenth warp issues
 // tcgen05.mma.kind::f8f6f4 (M = 128, N = 256, K = 32 per instruction, fp32
@@ -54,24 +55,22 @@ constexpr long long WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz before giving 
 // c < 2^24; the epilogue scales back by 2^12.
 constexpr float GRAM_UNIT_INV = 4096.0f;
 
-// Byte offset of element (rank r, row k) inside a tile of 128-row chunks:
+// Byte offset of element (rank r, K position k) inside a tile of 128-row chunks:
 // core matrix (r/8, k/16) at (r/8)*1024 + (k/16)*128, element (r%8)*16 +
 // k%16.
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t k) {
   return (r >> 3) * 1024u + (k >> 4) * 128u + (r & 7u) * 16u + (k & 15u);
 }
 
-// Four 0/1 bits -> four bytes of 0 or 0x08: the multiply adds the nibble
-// shifted by 3, 10, 17 and 24 bits (disjoint ranges, no carries), which puts
-// bit q at bit 8q + 3 in the copy shifted by 3 + 7q; the mask keeps those.
-__device__ __forceinline__ uint32_t expand4(uint32_t nib) {
-  return (nib * 0x01020408u) & 0x08080808u;
-}
-// Bits [pos, pos + 4) of x.
-__device__ __forceinline__ uint32_t nibble(uint32_t x, uint32_t pos) {
-  uint32_t r;
-  asm("bfe.u32 %0, %1, %2, 4;" : "=r"(r) : "r"(x), "r"(pos));
-  return r;
+// Rows j, j + 8, j + 16 and j + 24 of a 32-row column word x as four e4m3
+// bytes of 0 or 0x08: bit j + 8q moves to bit 8q + 3 with one shift, and the
+// mask keeps those bits. A chunk's rows are thus laid out along K in a fixed
+// order that is not row order; A and B use the same order, so every product
+// X[a][t] * X[b][t] is still formed once and the contraction over the chunk's
+// rows is unchanged.
+template <uint32_t J>
+__device__ __forceinline__ uint32_t spread_rows(uint32_t x) {
+  return (J <= 3 ? (x << (3 - J)) : (x >> (J - 3))) & 0x08080808u;
 }
 
 // ---------------------------------------------------------- PTX helpers
@@ -245,12 +244,17 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
         if (!__shfl_sync(0xffffffffu, slot_ok ? 1u : 0u, 0)) { failed = 1; break; }
         uint8_t *dst = row0 + s * stage_bytes;
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        // core matrix columns 2q and 2q + 1 take word q's 32 rows: bytes of
+        // rows {j, j+8, j+16, j+24} for j = 0..3, then for j = 4..7
 #pragma unroll
-        for (uint32_t h = 0; h < 8; ++h) {  // 16 rows each: core matrix column h
-          const uint32_t x = ws[h >> 1], b = 16 * (h & 1);
-          *reinterpret_cast<uint4 *>(dst + h * 128u) =
-              make_uint4(expand4(nibble(x, b)), expand4(nibble(x, b + 4)),
-                         expand4(nibble(x, b + 8)), expand4(nibble(x, b + 12)));
+        for (uint32_t q = 0; q < 4; ++q) {
+          const uint32_t x = ws[q];
+          *reinterpret_cast<uint4 *>(dst + (2 * q) * 128u) =
+              make_uint4(spread_rows<0>(x), spread_rows<1>(x), spread_rows<2>(x),
+                         spread_rows<3>(x));
+          *reinterpret_cast<uint4 *>(dst + (2 * q + 1) * 128u) =
+              make_uint4(spread_rows<4>(x), spread_rows<5>(x), spread_rows<6>(x),
+                         spread_rows<7>(x));
         }
         fence_proxy_async_smem();
         __syncwarp();
