@@ -85,18 +85,19 @@ size_t slice_all_smem(uint32_t tw) {
   return (size_t)tw * 32 * SROWPAD * 8 + (size_t)SRANKS * (tw + 1) * 4 + SRANKS * 4;
 }
 
+template <uint32_t TW>
 __global__ void __launch_bounds__(256) k_slice_all(Lattice L, const uint64_t *__restrict__ B,
                                                    uint32_t W,
                                                    const int32_t *__restrict__ rank_of,
                                                    const uint32_t *__restrict__ chunk_lo) {
   extern __shared__ __align__(16) uint8_t ssm[];
-  const uint32_t tw = L.tw, l1p = L.l1p, st = bs_stride((int)tw);
-  const uint32_t rows_t = tw * 32;
-  uint64_t *sin = reinterpret_cast<uint64_t *>(ssm);                   // [rows_t][SROWPAD]
-  uint32_t *sout = reinterpret_cast<uint32_t *>(sin + (size_t)rows_t * SROWPAD);  // [SRANKS][tw+1]
-  int32_t *srank = reinterpret_cast<int32_t *>(sout + (size_t)SRANKS * (tw + 1));  // [SRANKS]
+  constexpr uint32_t ST = bs_stride((int)TW), ROWS = TW * 32, OS = TW + 1;
+  const uint32_t l1p = L.l1p;
+  uint64_t *sin = reinterpret_cast<uint64_t *>(ssm);                   // [ROWS][SROWPAD]
+  uint32_t *sout = reinterpret_cast<uint32_t *>(sin + (size_t)ROWS * SROWPAD);  // [SRANKS][OS]
+  int32_t *srank = reinterpret_cast<int32_t *>(sout + (size_t)SRANKS * OS);  // [SRANKS]
   const uint64_t blockmax = L.M < L.n ? L.M : L.n;
-  const uint32_t ntiles = (uint32_t)(((blockmax + 31) / 32 + tw - 1) / tw);
+  const uint32_t ntiles = (uint32_t)(((blockmax + 31) / 32 + TW - 1) / TW);
   const uint32_t nch = (W + SJC - 1) / SJC;
   const uint64_t items = (uint64_t)L.stop_max * ntiles * nch;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -107,10 +108,10 @@ __global__ void __launch_bounds__(256) k_slice_all(Lattice L, const uint64_t *__
     const uint32_t j0 = c * SJC;
     const uint64_t first = b * L.M;
     const uint64_t last = first + L.M < L.n ? first + L.M : L.n;
-    const uint64_t row0 = first + (uint64_t)t * rows_t;
+    const uint64_t row0 = first + (uint64_t)t * ROWS;
     const uint32_t rlo = chunk_lo[c], rhi = chunk_lo[c + 1];
     __syncthreads();  // the previous item's tiles are free
-    for (uint32_t e = threadIdx.x; e < rows_t * SJC; e += blockDim.x) {
+    for (uint32_t e = threadIdx.x; e < ROWS * SJC; e += blockDim.x) {
       const uint32_t r = e / SJC, w = e % SJC;
       const uint64_t row = row0 + r;
       sin[r * SROWPAD + w] = (row < last && j0 + w < W) ? __ldcs(B + row * W + j0 + w) : 0ull;
@@ -118,22 +119,29 @@ __global__ void __launch_bounds__(256) k_slice_all(Lattice L, const uint64_t *__
     for (uint32_t e = threadIdx.x; e < SRANKS; e += blockDim.x)
       srank[e] = j0 * 64 + e < W * 64 ? __ldg(rank_of + j0 * 64 + e) : -1;
     __syncthreads();
-    for (uint32_t q = warp; q < tw * SJC; q += nwarp) {
+    for (uint32_t q = warp; q < TW * SJC; q += nwarp) {
       const uint32_t g = q / SJC, j = q % SJC;
       const uint64_t x = sin[(g * 32 + lane) * SROWPAD + j];
       const uint32_t lo = warp_transpose32((uint32_t)x);
       const uint32_t hi = warp_transpose32((uint32_t)(x >> 32));
       const int32_t r0 = srank[j * 64 + lane], r1 = srank[j * 64 + 32 + lane];
-      if (r0 >= 0) sout[((uint32_t)r0 - rlo) * (tw + 1) + g] = lo;
-      if (r1 >= 0) sout[((uint32_t)r1 - rlo) * (tw + 1) + g] = hi;
+      if (r0 >= 0) sout[((uint32_t)r0 - rlo) * OS + g] = lo;
+      if (r1 >= 0) sout[((uint32_t)r1 - rlo) * OS + g] = hi;
     }
     __syncthreads();
+    // each rank's TW words of this tile, four per 16-byte store (a tile row
+    // starts on a 16-byte boundary: ST words are a multiple of four)
     uint32_t *Vb = L.V + b * L.vwords;
-    for (uint32_t e = threadIdx.x; e < (rhi - rlo) * tw; e += blockDim.x) {
-      const uint32_t rr = e / tw, w = e % tw;
-      const uint64_t idx = ((uint64_t)t * l1p + rlo + rr) * st + w;
-      if (idx < L.vwords && rlo + rr < l1p && rr < SRANKS) Vb[idx] = sout[rr * (tw + 1) + w];
-      else L.ctrl->error = DIC_INTERNAL_BOUNDS;
+    const uint32_t nq = (rhi - rlo) * (TW / 4);
+    for (uint32_t e = threadIdx.x; e < nq; e += blockDim.x) {
+      const uint32_t rr = e / (TW / 4), w = 4 * (e % (TW / 4));
+      const uint64_t idx = ((uint64_t)t * l1p + rlo + rr) * ST + w;
+      if (idx + 3 < L.vwords && rlo + rr < l1p && rr < SRANKS) {
+        const uint32_t *src = sout + rr * OS + w;
+        *reinterpret_cast<uint4 *>(Vb + idx) = make_uint4(src[0], src[1], src[2], src[3]);
+      } else {
+        L.ctrl->error = DIC_INTERNAL_BOUNDS;
+      }
     }
   }
 }
@@ -144,10 +152,12 @@ cudaError_t launch_slice_all(Lattice L, const uint64_t *B, uint32_t W, const int
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = slice_all_smem(L.tw);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_slice_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*kern)(Lattice, const uint64_t *, uint32_t, const int32_t *, const uint32_t *) =
+      L.tw == 16 ? k_slice_all<16> : L.tw == 8 ? k_slice_all<8> : k_slice_all<4>;
+  if (L.tw != 16 && L.tw != 8 && L.tw != 4) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_slice_all<<<sms * 3, 256, smem, s>>>(L, B, W, rank_of, chunk_lo);
+  kern<<<sms * 3, 256, smem, s>>>(L, B, W, rank_of, chunk_lo);
   return cudaGetLastError();
 }
 

@@ -19,72 +19,143 @@ namespace dic {
 
 // --------------------------------------------------------- first pass
 // supp1[i] = number of rows with bit i set, over all n rows (FIRSTPASS of
-// Section 4.2). A warp takes 32 rows at a time and ICHUNK of their 64-bit
-// words: it loads the 32 x ICHUNK words with row-contiguous 8-byte loads
-// into its own shared-memory tile, then lane t takes row t's words and each
-// word, transposed across the warp (lane t ends with the 32 rows' bits of
-// items 64j+t and 64j+32+t), adds two popcounts to the lane's registers. A
-// warp walks many row groups of the same words, then adds its 2*ICHUNK
-// counters once.
-constexpr uint32_t ICHUNK = 8;
-constexpr uint32_t ITILE = ICHUNK + 1;  // padded row of a warp's tile (words)
+// Section 4.2). Each thread owns one 64-bit word column j and a strided set
+// of rows and keeps a bit-sliced counter of the column: plane k holds bit k
+// of the 64 items' counts. Words are added sixteen at a time through a
+// carry-save adder tree (Harley-Seal: a full adder per bit position is one
+// XOR3 and one majority, a LOP3 each per 32-bit half), so a word costs about
+// eight integer instructions instead of a transposition. At the end the
+// threads of a column add their counters with bit-sliced ripple adders in
+// shared memory, and a warp turns each column's planes into 64 counts (lane b
+// reads bit b of every plane) with one atomic per item per CTA.
+constexpr uint32_t IC_THREADS = 256;
+constexpr int IC_PLANES = 21;  // counts below 2^21 per CTA (the launch keeps them there)
 
-__device__ __forceinline__ uint32_t warp_transpose32_fp(uint32_t x) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t lo_masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const uint32_t j = 16u >> st, mlo = lo_masks[st];
-    const uint32_t v = __shfl_xor_sync(0xffffffffu, x, j);
-    x = (lane & j) ? ((x & ~mlo) | ((v >> j) & mlo)) : ((x & mlo) | ((v << j) & ~mlo));
-  }
-  return x;
+// One full-adder column step: sum and carry of a + b + c, bitwise.
+__device__ __forceinline__ void csa(uint64_t &h, uint64_t &l, uint64_t a, uint64_t b,
+                                    uint64_t c) {
+  const uint64_t u = a ^ b;
+  h = (a & b) | (u & c);
+  l = u ^ c;
 }
 
-__global__ void __launch_bounds__(256) k_item_count(const uint64_t *__restrict__ B, uint64_t n,
-                                                    uint32_t W, uint32_t m,
-                                                    uint32_t *__restrict__ cnt) {
-  __shared__ uint64_t tile[8][32 * ITILE];
-  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint64_t *tl = tile[wib];
-  const uint32_t njc = (W + ICHUNK - 1) / ICHUNK;
-  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  const uint64_t wpc = nw / njc;  // warps per word chunk (the launch makes it >= 1)
-  if (gw / njc >= wpc) return;
-  const uint32_t j0 = (uint32_t)(gw % njc) * ICHUNK;
-  const uint64_t ngroups = (n + 31) / 32;
-  uint32_t acc[2 * ICHUNK];
+// Add sixteen words to the bit-sliced counter P (planes 0-3 take the tree's
+// ones, twos, fours and eights; its sixteens ripple into planes 4 and up).
+__device__ __forceinline__ void csa16(uint64_t (&P)[IC_PLANES], const uint64_t (&x)[16]) {
+  uint64_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
+  csa(twosA, P[0], P[0], x[0], x[1]);
+  csa(twosB, P[0], P[0], x[2], x[3]);
+  csa(foursA, P[1], P[1], twosA, twosB);
+  csa(twosA, P[0], P[0], x[4], x[5]);
+  csa(twosB, P[0], P[0], x[6], x[7]);
+  csa(foursB, P[1], P[1], twosA, twosB);
+  csa(eightsA, P[2], P[2], foursA, foursB);
+  csa(twosA, P[0], P[0], x[8], x[9]);
+  csa(twosB, P[0], P[0], x[10], x[11]);
+  csa(foursA, P[1], P[1], twosA, twosB);
+  csa(twosA, P[0], P[0], x[12], x[13]);
+  csa(twosB, P[0], P[0], x[14], x[15]);
+  csa(foursB, P[1], P[1], twosA, twosB);
+  csa(eightsB, P[2], P[2], foursA, foursB);
+  csa(sixteens, P[3], P[3], eightsA, eightsB);
+  uint64_t carry = sixteens;
 #pragma unroll
-  for (int q = 0; q < 2 * (int)ICHUNK; ++q) acc[q] = 0;
-  // load pattern: lane l takes word l % 8 of rows l / 8, 4 + l / 8, ...
-  const uint32_t lw = lane % ICHUNK, lr = lane / ICHUNK;
-  const bool wok = j0 + lw < W;
-  for (uint64_t rg = gw / njc; rg < ngroups; rg += wpc) {
-    const uint64_t row0 = rg * 32;
-    uint64_t v[8];
-#pragma unroll
-    for (uint32_t i = 0; i < 8; ++i) {
-      const uint64_t row = row0 + 4 * i + lr;
-      v[i] = (wok && row < n) ? __ldcs(B + row * W + j0 + lw) : 0ull;
-    }
-#pragma unroll
-    for (uint32_t i = 0; i < 8; ++i) tl[(4 * i + lr) * ITILE + lw] = v[i];
-    __syncwarp();
-#pragma unroll
-    for (uint32_t q = 0; q < ICHUNK; ++q) {
-      const uint64_t x = tl[lane * ITILE + q];
-      acc[2 * q] += __popc(warp_transpose32_fp((uint32_t)x));
-      acc[2 * q + 1] += __popc(warp_transpose32_fp((uint32_t)(x >> 32)));
-    }
-    __syncwarp();
+  for (int k = 4; k < IC_PLANES; ++k) {
+    const uint64_t t = P[k] & carry;
+    P[k] ^= carry;
+    carry = t;
   }
+}
+
+// Columns of JC words per CTA (blockIdx.y picks the chunk), IC_THREADS / JC
+// row threads per column; JC = 32, or the power of two at least W below 32,
+// so a warp's loads cover consecutive words of consecutive rows.
+template <uint32_t JC>
+__global__ void __launch_bounds__(IC_THREADS) k_item_count(const uint64_t *__restrict__ B,
+                                                           uint64_t n, uint32_t W, uint32_t m,
+                                                           uint32_t *__restrict__ cnt) {
+  constexpr uint32_t RT = IC_THREADS / JC;
+  __shared__ uint64_t sp[IC_PLANES][IC_THREADS];
+  const uint32_t t = threadIdx.x, jl = t % JC, rt = t / JC;
+  const uint32_t j = blockIdx.y * JC + jl;
+  const bool col = j < W;
+  const uint64_t stride = (uint64_t)gridDim.x * RT;
+  uint64_t P[IC_PLANES];
 #pragma unroll
-  for (uint32_t q = 0; q < ICHUNK; ++q) {
-    const uint32_t i0 = (j0 + q) * 64 + lane, i1 = i0 + 32;
-    if (i0 < m && acc[2 * q]) atomicAdd(&cnt[i0], acc[2 * q]);
-    if (i1 < m && acc[2 * q + 1]) atomicAdd(&cnt[i1], acc[2 * q + 1]);
+  for (int k = 0; k < IC_PLANES; ++k) P[k] = 0;
+  uint64_t r = (uint64_t)blockIdx.x * RT + rt;
+  for (; r + 15 * stride < n; r += 16 * stride) {
+    uint64_t x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = col ? __ldcs(B + (r + i * stride) * W + j) : 0ull;
+    csa16(P, x);
   }
+  if (r < n) {  // the last rows of this thread (fewer than sixteen)
+    uint64_t x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint64_t rr = r + i * stride;
+      x[i] = (col && rr < n) ? __ldcs(B + rr * W + j) : 0ull;
+    }
+    csa16(P, x);
+  }
+  // the row threads of a column add their counters: at each step the upper
+  // half hands its planes over through shared memory (ripple-carry adders,
+  // bitwise; the totals fit the planes)
+  for (uint32_t step = RT / 2; step >= 1; step >>= 1) {
+    if (rt >= step && rt < 2 * step)
+#pragma unroll
+      for (int k = 0; k < IC_PLANES; ++k) sp[k][t] = P[k];
+    __syncthreads();
+    if (rt < step) {
+      uint64_t c = 0;
+#pragma unroll
+      for (int k = 0; k < IC_PLANES; ++k) {
+        const uint64_t b = sp[k][t + step * JC];
+        uint64_t h, l;
+        csa(h, l, P[k], b, c);
+        P[k] = l;
+        c = h;
+      }
+    }
+    __syncthreads();
+  }
+  if (rt == 0)
+#pragma unroll
+    for (int k = 0; k < IC_PLANES; ++k) sp[k][jl] = P[k];
+  __syncthreads();
+  // a warp per column: lane b gathers bit b (and b + 32) of every plane
+  const uint32_t lane = t & 31, warp = t >> 5;
+  for (uint32_t c = warp; c < JC; c += IC_THREADS / 32) {
+    const uint32_t jc = blockIdx.y * JC + c;
+    if (jc >= W) continue;
+    uint32_t v0 = 0, v1 = 0;
+#pragma unroll
+    for (int k = 0; k < IC_PLANES; ++k) {
+      const uint64_t pk = sp[k][c];
+      v0 |= (uint32_t)((pk >> lane) & 1u) << k;
+      v1 |= (uint32_t)((pk >> (lane + 32)) & 1u) << k;
+    }
+    const uint32_t i0 = jc * 64 + lane, i1 = i0 + 32;
+    if (i0 < m && v0) atomicAdd(&cnt[i0], v0);
+    if (i1 < m && v1) atomicAdd(&cnt[i1], v1);
+  }
+}
+
+template <uint32_t JC>
+static cudaError_t go_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_t m,
+                                 uint32_t *cnt, int sms, cudaStream_t s) {
+  constexpr uint32_t RT = IC_THREADS / JC;
+  // two CTAs per SM over the column chunks, and enough CTAs that the rows one
+  // CTA adds up (its column totals) stay below 2^IC_PLANES
+  const uint32_t ny = (W + JC - 1) / JC;
+  uint64_t gx = std::max<uint64_t>(1, (uint64_t)sms * 2 / ny);
+  const uint64_t cap = ((uint64_t)1 << IC_PLANES) - 1;
+  gx = std::max<uint64_t>(gx, (n + cap - 1) / cap);
+  gx = std::min<uint64_t>(gx, std::max<uint64_t>(1, (n + RT - 1) / RT));
+  if (gx > 0x7FFFFFFFull || ny > 65535) return cudaErrorInvalidValue;
+  k_item_count<JC><<<dim3((unsigned)gx, ny), IC_THREADS, 0, s>>>(B, n, W, m, cnt);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_t m,
@@ -94,17 +165,12 @@ cudaError_t launch_item_count(const uint64_t *B, uint64_t n, uint32_t W, uint32_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)m * 4, s);
   if (e != cudaSuccess || n == 0) return e;
-  const uint32_t njc = (W + ICHUNK - 1) / ICHUNK;
-  const uint64_t groups = (n + 31) / 32;
-  // enough warps to cover every word chunk, at most one warp per row group
-  // and chunk, at most 8 CTAs of 8 warps per SM
-  uint64_t warps = std::min<uint64_t>((uint64_t)sms * 64, groups * njc);
-  warps = std::max<uint64_t>(warps, njc);
-  warps = (warps + njc - 1) / njc * njc;
-  const uint64_t grid = (warps + 7) / 8;
-  if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-  k_item_count<<<(unsigned)grid, 256, 0, s>>>(B, n, W, m, cnt);
-  return cudaGetLastError();
+  if (W >= 32) return go_item_count<32>(B, n, W, m, cnt, sms, s);
+  if (W > 8) return go_item_count<16>(B, n, W, m, cnt, sms, s);
+  if (W > 4) return go_item_count<8>(B, n, W, m, cnt, sms, s);
+  if (W > 2) return go_item_count<4>(B, n, W, m, cnt, sms, s);
+  if (W > 1) return go_item_count<2>(B, n, W, m, cnt, sms, s);
+  return go_item_count<1>(B, n, W, m, cnt, sms, s);
 }
 
 // ----------------------------------------------------- column compaction
