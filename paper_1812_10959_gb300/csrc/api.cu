@@ -767,10 +767,12 @@ dic_status Miner::launch_phase(int phase) {
         }
         if (e == cudaSuccess) {
           if (prof(DIC_PROFILE_COUNT)) TRY(iv_open(IV_COUNT, s_));
-          // (the direct form: one resident wave, two CTAs of 256 threads
-          // per SM at its register use; warps stride over the records)
+          // (the direct form: one resident wave of CTAs at its register
+          // use; warps stride over the records)
           e = launch_count_bitslice(L_, bs_V_, bs_tw_, kre, bs_l1p_, chunk, bs_V_words_,
-                                    direct_ ? sm_count() * 2 : bs_grid_, direct_, s_);
+                                    direct_ ? sm_count() * count_direct_ctas_per_sm(kre)
+                                            : bs_grid_,
+                                    direct_, s_);
           if (prof(DIC_PROFILE_COUNT)) TRY(iv_close(s_));
         }
         if (gram) CU(cudaStreamWaitEvent(s_, ev_join_, 0));  // join

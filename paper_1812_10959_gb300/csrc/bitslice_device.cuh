@@ -134,7 +134,7 @@ constexpr uint32_t BS_DIRECT_MAX = 24576;
 // that a lane's column loads, and those of its next words, are all in
 // flight together. Whole warps must call this
 // (grid-stride over records by warp).
-template <int TW, int KRE>
+template <int TW, int KRE, uint32_t UJ = 4>
 __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint32_t g,
                                                 uint32_t lo, uint32_t hi, uint32_t nw32,
                                                 uint32_t &pruned, uint32_t &solid,
@@ -168,7 +168,6 @@ __device__ __forceinline__ void bs_count_direct(const Lattice &L, Ctrl *C, uint3
     // (a tile row holds TW = 4, 8 or 16 words, so the four share a tile;
     // words past the block's rows are zero in the buffer). UJ loads per
     // rank are issued before any AND.
-    constexpr uint32_t UJ = 4;
     const uint32_t nv = (nw32 + 3) / 4;
     uint32_t cnt = 0;
     for (uint32_t j0 = 0; j0 < nv; j0 += 32 * UJ) {

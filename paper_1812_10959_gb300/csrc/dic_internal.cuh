@@ -369,6 +369,9 @@ cudaError_t launch_slice_block(Lattice L, uint32_t ahead, cudaStream_t s);
 cudaError_t launch_count_bitslice(Lattice L, const uint32_t *V, int tw, int kre, uint32_t l1p,
                                   uint32_t chunk, uint64_t vwords, int grid, bool direct,
                                   cudaStream_t s);
+// CTAs of 256 threads per SM the direct count kernel is built for, by rank
+// bucket (its grid is one resident wave).
+int count_direct_ctas_per_sm(int kre);
 // Windows of at most this many counted records get the direct form.
 constexpr uint32_t BS_DIRECT_HOST_MAX = 8192;
 // Batched rounds (kernels_batch.cu): one launch per phase for all queries.

@@ -85,8 +85,10 @@ size_t slice_all_smem(uint32_t tw) {
   return (size_t)tw * 32 * SROWPAD * 8 + (size_t)SRANKS * (tw + 1) * 4 + SRANKS * 4;
 }
 
+constexpr uint32_t SLICE_THREADS = 256;
+
 template <uint32_t TW>
-__global__ void __launch_bounds__(256) k_slice_all(Lattice L, const uint64_t *__restrict__ B,
+__global__ void __launch_bounds__(SLICE_THREADS) k_slice_all(Lattice L, const uint64_t *__restrict__ B,
                                                    uint32_t W,
                                                    const int32_t *__restrict__ rank_of,
                                                    const uint32_t *__restrict__ chunk_lo) {
@@ -111,14 +113,28 @@ __global__ void __launch_bounds__(256) k_slice_all(Lattice L, const uint64_t *__
     const uint64_t row0 = first + (uint64_t)t * ROWS;
     const uint32_t rlo = chunk_lo[c], rhi = chunk_lo[c + 1];
     __syncthreads();  // the previous item's tiles are free
-    for (uint32_t e = threadIdx.x; e < ROWS * SJC; e += blockDim.x) {
-      const uint32_t r = e / SJC, w = e % SJC;
-      const uint64_t row = row0 + r;
-      sin[r * SROWPAD + w] = (row < last && j0 + w < W) ? __ldcs(B + row * W + j0 + w) : 0ull;
+    {
+      // every load of the tile issued before any is stored (the launch has
+      // SLICE_THREADS threads)
+      constexpr uint32_t NL = ROWS * SJC / SLICE_THREADS;
+      uint64_t v[NL];
+#pragma unroll
+      for (uint32_t i = 0; i < NL; ++i) {
+        const uint32_t e = threadIdx.x + i * SLICE_THREADS;
+        const uint32_t r = e / SJC, w = e % SJC;
+        const uint64_t row = row0 + r;
+        v[i] = (row < last && j0 + w < W) ? __ldcs(B + row * W + j0 + w) : 0ull;
+      }
+#pragma unroll
+      for (uint32_t i = 0; i < NL; ++i) {
+        const uint32_t e = threadIdx.x + i * SLICE_THREADS;
+        sin[(e / SJC) * SROWPAD + e % SJC] = v[i];
+      }
     }
     for (uint32_t e = threadIdx.x; e < SRANKS; e += blockDim.x)
       srank[e] = j0 * 64 + e < W * 64 ? __ldg(rank_of + j0 * 64 + e) : -1;
     __syncthreads();
+#pragma unroll 4
     for (uint32_t q = warp; q < TW * SJC; q += nwarp) {
       const uint32_t g = q / SJC, j = q % SJC;
       const uint64_t x = sin[(g * 32 + lane) * SROWPAD + j];
@@ -157,7 +173,7 @@ cudaError_t launch_slice_all(Lattice L, const uint64_t *B, uint32_t W, const int
   if (L.tw != 16 && L.tw != 8 && L.tw != 4) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<sms * 3, 256, smem, s>>>(L, B, W, rank_of, chunk_lo);
+  kern<<<sms * 3, SLICE_THREADS, smem, s>>>(L, B, W, rank_of, chunk_lo);
   return cudaGetLastError();
 }
 
@@ -234,8 +250,16 @@ __global__ void __launch_bounds__(BS_THREADS) k_count_bitslice(Lattice L,
 // The same count for a window the host expects to be small: direct mode
 // only (it is exact at any window size), no shared memory, so its CTAs can
 // share SMs with the pair-cohort GEMM of the same stop.
+// Three CTAs per SM for itemsets of at most four items (three 16-byte
+// loads per rank in flight: 96 x 4 words cover a 12,288-row block in one
+// round, at most 85 registers); one for longer ones, whose unrolled rank
+// loads take more registers than two CTAs per SM leave.
+__host__ __device__ constexpr int direct_ctas_per_sm(int kre) { return kre <= 4 ? 3 : 1; }
+__host__ __device__ constexpr uint32_t direct_unroll(int kre) { return kre <= 4 ? 3u : 4u; }
+int count_direct_ctas_per_sm(int kre) { return direct_ctas_per_sm(kre); }
+
 template <int TW, int KRE>
-__global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
+__global__ void __launch_bounds__(256, direct_ctas_per_sm(KRE)) k_count_direct(Lattice L) {
   pdl_wait();
   pdl_trigger();
   Ctrl *C = L.ctrl;
@@ -253,7 +277,8 @@ __global__ void __launch_bounds__(256) k_count_direct(Lattice L) {
   apply_pair_events_range(L, C, g, ev, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                           (uint64_t)gridDim.x * blockDim.x, pruned, solid);
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) stage_next_events(L, C, g);
-  if (lo < tail) bs_count_direct<TW, KRE>(L, C, g, lo, tail, nw32, pruned, solid, work);
+  if (lo < tail)
+    bs_count_direct<TW, KRE, direct_unroll(KRE)>(L, C, g, lo, tail, nw32, pruned, solid, work);
   block_add_tallies(C, pruned, solid, work);
 }
 
