@@ -122,18 +122,21 @@ typedef struct {
                                least this many rows are mined alone by the
                                single-query path on a thread of their own,
                                beside the batched rounds; 0 = 2^19        */
-  uint32_t stop_loop;       /* 0 = count every dashed itemset at every
-                               stop; 1 = event-driven where it applies
-                               (single queries with prestaged columns and
-                               the pair cohort on the GEMM, at most 8,192
-                               blocks, otherwise 0): each cohort is counted
+  uint32_t stop_loop;       /* 0 = per stop, handing over to the
+                               event-driven form once the first pass's pair
+                               cohort has passed and 10 stops in a row have
+                               promoted nothing (where the event-driven form
+                               applies); 1 = event-driven throughout where
+                               it applies (single queries with prestaged
+                               columns and the pair cohort on the GEMM, at
+                               most 8,192 blocks): each cohort is counted
                                over its whole pass when it is born, so its
                                promotion and erase stops (Algorithm 4) are
                                known in advance and only stops that promote
                                something run MAKECANDIDATES, all inside one
-                               graph with a device-side loop. Same
-                               itemsets, supports and trace either way.
-                               Other values: DIC_EINVAL                    */
+                               graph with a device-side loop; 2 = per stop
+                               only. Same itemsets, supports and trace in
+                               every case. Other values: DIC_EINVAL        */
   uint32_t reserved[3];
 } dic_options;
 
@@ -175,8 +178,9 @@ typedef struct {
                                stop graphs                                 */
   double collect_ms;        /* host wall time from the last stop's check to
                                the result being ready                      */
-  uint32_t event_loop;      /* 1: the event-driven stop loop ran
-                               (dic_options.stop_loop)                     */
+  uint32_t event_loop;      /* the stop loop that ran (dic_options.
+                               stop_loop): 0 per stop, 1 event-driven, 2
+                               per stop, then event-driven from a stop on  */
   uint32_t event_iters;     /* its iterations (cohort pass + MAKECANDIDATES
                                at one stop with promotions)                */
 } dic_stats;

@@ -615,6 +615,10 @@ class Miner {
   // replayed in a device-side WHILE loop of one graph (rebuilt when a buffer
   // of the lattice changes), or launched directly when they are profiled
   bool evmode_ = false;
+  bool ev_ok_ = false;       // the event-driven form can take the loop
+  bool ev_switched_ = false; // it took over from the per-stop form
+  dic_status switch_to_events();
+  dic_status alloc_event_buffers();
   cudaGraph_t evg_ = nullptr;
   cudaGraphExec_t evx_ = nullptr;
   uint64_t evg_version_ = 0;
@@ -1206,18 +1210,16 @@ dic_status Miner::prepare() {
     // ---- event-driven loop: every block staged, the pairs' events
     // precomputed, a per-block counter array that fits shared memory
     evmode_ = false;
+    ev_switched_ = false;
     L_.events = 0;
-    if (events_ && opt_.stop_loop == 1 && stop_max64 <= EV_STOPMAX &&
-        (L_.tw == 4 || L_.tw == 8 || L_.tw == 16) &&
-        cohort_pass_smem((uint32_t)stop_max64, l1) + 1024 <= smem_optin_) {
+    ev_ok_ = events_ && opt_.stop_loop != 2 && stop_max64 <= EV_STOPMAX &&
+             (L_.tw == 4 || L_.tw == 8 || L_.tw == 16) &&
+             cohort_pass_smem((uint32_t)stop_max64, l1) + 1024 <= smem_optin_;
+    cp_grid_ = sm_count() * 2;
+    if (ev_ok_ && opt_.stop_loop == 1) {
       evmode_ = true;
       L_.events = 1;
-      TRY(alloc_event_tallies(L_.tcap + (uint32_t)stop_max64 + 2));
-      cp_grid_ = sm_count() * 2;
-      // split-count scratch for cohorts of up to one record per CTA
-      L_.cp_records = (uint32_t)cp_grid_;
-      TRY(alloc(&L_.cp_cnt, (size_t)L_.cp_records * stop_max64));
-      TRY(alloc(&L_.cp_tick, L_.cp_records, true));
+      TRY(alloc_event_buffers());
     }
 
     has_loop_ = true;
@@ -1229,6 +1231,11 @@ dic_status Miner::prepare() {
 // Stops the newest cohort still needs (more may follow if cohorts appear).
 // Stops captured into one graph where the loop allows it.
 constexpr uint32_t kStopsPerGraph = 8;
+// Stops without promotions after which the per-stop loop hands over to the
+// event-driven form (stop_loop 0), and the group size it checks at once the
+// pair cohort has passed.
+constexpr uint32_t kStopsQuiet = 10;
+constexpr uint32_t kGroupAfterPairs = 16;
 
 static uint32_t stops_needed(const Ctrl &c, uint32_t stop_max, uint32_t cap) {
   const uint64_t end = (uint64_t)c.last_birth + stop_max + 1;
@@ -1533,9 +1540,44 @@ dic_status Miner::recover_events() {
   return DIC_OK;
 }
 
+// The event-driven form's per-stop tallies and the split-count scratch of
+// its cohort passes (cohorts of up to one record per CTA).
+dic_status Miner::alloc_event_buffers() {
+  TRY(alloc_event_tallies(L_.tcap + L_.stop_max + 2));
+  L_.cp_records = (uint32_t)cp_grid_;
+  TRY(alloc(&L_.cp_cnt, (size_t)L_.cp_records * L_.stop_max));
+  TRY(alloc(&L_.cp_tick, L_.cp_records, true));
+  return DIC_OK;
+}
+
+// Hand the rest of the loop to the event-driven form at the current stop
+// boundary: the live records of three or more items are counted over the
+// blocks left of their passes and their events tallied (the pair cohort has
+// left the window: the hand-over waits for stop_max to pass).
+dic_status Miner::switch_to_events() {
+  if ((uint64_t)(h_ctrl_->hash_used + h_ctrl_->n_live) * 2 > L_.hcap)
+    TRY(grow_hash((uint64_t)h_ctrl_->hash_used + h_ctrl_->n_live));
+  TRY(alloc_event_buffers());
+  L_.events = 1;
+  evmode_ = true;
+  ev_switched_ = true;
+  ++lat_version_;
+  h_ctrl_->ev_pending = 0;
+  h_ctrl_->ev_iter = 0;
+  h_ctrl_->ev_limit = ~0u;
+  h_ctrl_->ev_ticket = 0;
+  CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
+  const uint32_t lo = std::max(h_ctrl_->head, L_.pair_end);
+  cudaError_t e = launch_window_pass(L_, lo, h_ctrl_->tail, h_ctrl_->step, cp_grid_, s_);
+  if (e != cudaSuccess) return fail(DIC_ECUDA, "window pass launch: %s", cudaGetErrorString(e));
+  ++launches_;
+  return DIC_OK;
+}
+
 dic_status Miner::loop_events() {
-  setup_ms_ = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_)
-                  .count();
+  if (!ev_switched_)
+    setup_ms_ = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_)
+                    .count();
   // Profiling the count or generate kernels times whole iterations one
   // launch at a time: the graph runs up to the next profiled iteration (its
   // limit), that iteration is launched directly between CUDA events, and the
@@ -1613,7 +1655,11 @@ dic_status Miner::loop() {
   // 64 between host checks
   const uint32_t group_max = opt_.steps_per_sync ? opt_.steps_per_sync : 64;
   while (!h_ctrl_->done) {
-    const uint32_t group = stops_needed(*h_ctrl_, L_.stop_max, group_max);
+    uint32_t group = stops_needed(*h_ctrl_, L_.stop_max, group_max);
+    // after the pair cohort, shorter groups let the hand-over to the
+    // event-driven form come soon after promotions stop
+    if (ev_ok_ && opt_.stop_loop == 0 && !opt_.steps_per_sync && h_ctrl_->step > L_.stop_max)
+      group = std::min(group, kGroupAfterPairs);
     TRY(reserve(group));
     int bucket = rows_width_bucket(h_ctrl_->max_k, wc);
     nw_ = bucket ? (uint32_t)bucket : 0;
@@ -1651,6 +1697,14 @@ dic_status Miner::loop() {
     }
     TRY(sync_ctrl());
     TRY(recover());
+    // once the pair cohort has passed and the last kStopsQuiet stops promoted
+    // nothing, the stops left are mostly ones without promotions: the
+    // event-driven form closes those from tallies (stop_loop 0)
+    if (ev_ok_ && !h_ctrl_->done && h_ctrl_->step > L_.stop_max &&
+        h_ctrl_->step > h_ctrl_->last_promo + kStopsQuiet) {
+      TRY(switch_to_events());
+      return loop_events();
+    }
   }
   return DIC_OK;
 }
@@ -1819,7 +1873,7 @@ dic_status Miner::collect(dic_result **out) {
     res->supp[q] = supps[o];
   }
   res->stats.tests = tests;
-  res->stats.event_loop = evmode_ ? 1u : 0u;
+  res->stats.event_loop = ev_switched_ ? 2u : evmode_ ? 1u : 0u;
   res->stats.event_iters = evmode_ && has_loop_ ? h_ctrl_->ev_iter : 0u;
   res->stats.frequent = order.size();
   res->stats.kernel_launches = launches_;
@@ -1873,7 +1927,7 @@ static dic_status check_options(const dic_options &o) {
     return fail(DIC_EINVAL, "unknown count_path %u", o.count_path);
   if (o.algorithm > 1) return fail(DIC_EINVAL, "algorithm must be 0 or 1 (got %u)", o.algorithm);
   if (o.prestage > 1) return fail(DIC_EINVAL, "prestage must be 0 or 1 (got %u)", o.prestage);
-  if (o.stop_loop > 1) return fail(DIC_EINVAL, "stop_loop must be 0 or 1 (got %u)", o.stop_loop);
+  if (o.stop_loop > 2) return fail(DIC_EINVAL, "stop_loop must be 0, 1 or 2 (got %u)", o.stop_loop);
   return DIC_OK;
 }
 

@@ -78,7 +78,9 @@ struct Ctrl {
   // 1 while a stop is prepared (tallies and promoted list) and awaits
   // MAKECANDIDATES and its close in the next cohort pass
   uint32_t ev_pending;
-  uint32_t pad_ev;
+  // the last stop that promoted anything (the host's test for handing the
+  // rest of the loop to the event-driven form)
+  uint32_t last_promo;
 };
 
 __host__ __device__ inline uint32_t n_gen_of(const Ctrl &c) { return (uint32_t)c.gen_ticket; }
@@ -323,6 +325,12 @@ cudaError_t launch_generate_finish(Lattice L, int grid, bool slice_next, cudaStr
 // is prepared or the iteration limit is reached.
 cudaError_t launch_cohort_pass(Lattice L, int grid, uint32_t budget, uint32_t use_cond,
                                unsigned long long cond, cudaStream_t s);
+// Hand the loop from the per-stop form to the event-driven one at a stop
+// boundary: every live record of three or more items in [lo, tail) is
+// counted over the blocks left of its pass, from its count so far, and its
+// events are tallied as the cohort pass does (kernels_events.cu).
+cudaError_t launch_window_pass(Lattice L, uint32_t lo, uint32_t tail, uint32_t step, int grid,
+                               cudaStream_t s);
 // Set Ctrl.ev_limit (stream-ordered).
 cudaError_t launch_set_ev_limit(Ctrl *C, uint32_t limit, cudaStream_t s);
 size_t cohort_pass_smem(uint32_t stop_max, uint32_t l1);

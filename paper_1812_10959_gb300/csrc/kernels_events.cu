@@ -422,6 +422,148 @@ __global__ void __launch_bounds__(CP_THREADS, 2) k_cohort_pass(Lattice L, uint32
   }
 }
 
+// Window pass (the hand-over from the per-stop loop at stop `step`): one
+// CTA per live record c of [lo, tail) at a time. The record has been counted
+// over ages 1..a0 (a0 = step - 1 - birth blocks) and holds that count in
+// csupp; its blocks of ages a0 + 1..S (a cyclic range of block indices, at
+// most two runs) are counted now, and warp 0 continues Algorithm 4 from there
+// in stop order: a circle's promotion or erase stop, a box's full-pass
+// support; the tallies and box-set entries are those of the cohort pass.
+template <int TW>
+__global__ void __launch_bounds__(CP_THREADS, 2) k_window_pass(Lattice L, uint32_t lo,
+                                                               uint32_t tail, uint32_t step) {
+  extern __shared__ __align__(16) uint8_t cps[];
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(cps);
+  uint16_t *s_rank = reinterpret_cast<uint16_t *>(cps + (size_t)L.stop_max * 4);
+  __shared__ uint32_t s_k, s_birth, s_a0, s_cum, s_sh;
+  Ctrl *C = L.ctrl;
+  const uint32_t S = L.stop_max;
+  const uint64_t blockmax = L.M < L.n ? L.M : L.n;
+  const uint32_t nw32max = (uint32_t)((blockmax + 31) / 32);
+  const uint32_t nvmax = (nw32max + 3) / 4;
+  const uint64_t last_rows = L.n - (uint64_t)(S - 1) * L.M;
+  unsigned long long work = 0;
+  for (uint32_t c = lo + blockIdx.x; c < tail; c += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const uint8_t sh = L.cshape[c];
+      const uint32_t birth = L.cbirth[c];
+      const uint32_t a0 = step - 1 - birth;
+      s_sh = (sh == SH_NIL || a0 >= S) ? (uint32_t)SH_NIL : sh;
+      s_birth = birth;
+      s_a0 = a0;
+      s_cum = L.csupp[c];
+      uint32_t k = L.ck[c];
+      if (k <= (uint32_t)KRMAX) {
+        for (uint32_t q = 0; q < k; ++q) s_rank[q] = L.cranks[(uint64_t)c * KRMAX + q];
+      } else {
+        k = 0;
+        for (uint32_t i = 0; i < L.wc; ++i)
+          for (uint64_t x = L.cmask[(uint64_t)c * L.wc + i]; x; x &= x - 1)
+            if (k < L.l1) s_rank[k++] = (uint16_t)(i * 64 + __ffsll((long long)x) - 1);
+      }
+      s_k = k;
+    }
+    for (uint32_t a = threadIdx.x; a < S; a += blockDim.x) s_cnt[a] = 0;
+    __syncthreads();
+    const uint32_t sh = s_sh, k = s_k, birth = s_birth, a0 = s_a0;
+    if (sh != SH_NIL && k) {
+      // blocks of ages a0 + 1 .. S: from (birth + a0) mod S on, S - a0 of them
+      const uint32_t x = (birth + a0) % S, len = S - a0;
+      const uint32_t e1 = x + len < S ? x + len : S;
+      cp_count<TW>(L, s_rank, k, x, e1, nvmax, s_cnt + x);
+      if (x + len > S) cp_count<TW>(L, s_rank, k, 0, x + len - S, nvmax, s_cnt);
+    }
+    __syncthreads();
+    if (sh != SH_NIL && threadIdx.x < 32) {
+      const uint32_t lane = threadIdx.x;
+      uint64_t rest = 0;
+      for (uint32_t a = lane; a < S; a += 32) rest += s_cnt[a];
+      for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+      const uint64_t total = s_cum + rest;
+      uint32_t ev_age = 0, ev_promote = 0;
+      uint64_t ev_cum = 0;
+      if (sh == SH_CIRCLE) {
+        uint64_t carry = s_cum;
+        for (uint32_t base = a0; base < S; base += 32) {
+          const uint32_t age = base + lane + 1;
+          const uint32_t v = age <= S ? s_cnt[(birth + age - 1) % S] : 0u;
+          uint64_t cum = v;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, cum, o);
+            if (lane >= (uint32_t)o) cum += y;
+          }
+          cum += carry;
+          const bool prom = age <= S && cum >= L.minsup;
+          const bool drop = age <= S && cum + L.M * (uint64_t)(S - age) < (uint64_t)L.minsup;
+          const uint32_t bal = __ballot_sync(0xffffffffu, prom || drop);
+          if (bal) {
+            const int src = __ffs(bal) - 1;
+            ev_age = base + src + 1;
+            ev_promote = __shfl_sync(0xffffffffu, prom ? 1u : 0u, src);
+            ev_cum = __shfl_sync(0xffffffffu, cum, src);
+            break;
+          }
+          carry = __shfl_sync(0xffffffffu, cum, 31);
+        }
+      }
+      if (lane == 0) {
+        const uint32_t solid_at = birth + S;
+        if (solid_at + 1 >= L.ehcap || (sh == SH_CIRCLE && ev_age == 0)) {
+          C->error = DIC_INTERNAL_BOUNDS;
+        } else if (sh == SH_BOX) {  // promoted earlier: the rest of its pass
+          L.csupp[c] = (uint32_t)total;
+          atomicAdd(&L.eh_solid[solid_at], 1u);
+        } else if (ev_promote) {
+          const uint32_t p = birth + ev_age;
+          L.csupp[c] = (uint32_t)total;
+          L.cshape[c] = SH_BOX;
+          L.cpromo[c] = p;
+          box_insert(L, c, mask_hash_sum(L.cmask + (uint64_t)c * L.wc, L.wc));
+          const uint32_t i = atomicAdd(&L.eh_box[p], 1u);
+          if (i < EV_LIST) L.eb_list[(uint64_t)p * EV_LIST + i] = c;
+          atomicAdd(&L.eh_solid[solid_at], 1u);
+        } else {
+          const uint32_t p = birth + ev_age;
+          L.csupp[c] = (uint32_t)ev_cum;
+          L.cshape[c] = SH_NIL;
+          atomicAdd(&L.eh_pruned[p], 1u);
+        }
+        // 32-row words of the blocks counted now
+        uint64_t words = 0;
+        for (uint32_t a = a0 + 1; a <= S; ++a) {
+          const uint32_t bl = (birth + a - 1) % S;
+          words += bl + 1 == S ? (last_rows + 31) / 32 : nw32max;
+        }
+        work += (unsigned long long)(k + 1) * words;
+      }
+    }
+    __syncthreads();  // shared counts and ranks are reused by the next record
+  }
+  if (threadIdx.x == 0 && work) atomicAdd(&C->work, work);
+}
+
+template <int TW>
+static cudaError_t go_wp(Lattice L, uint32_t lo, uint32_t tail, uint32_t step, int grid,
+                         cudaStream_t s) {
+  const size_t smem = cohort_pass_smem(L.stop_max, L.l1);
+  cudaError_t e = cudaFuncSetAttribute(k_window_pass<TW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_window_pass<TW><<<grid, CP_THREADS, smem, s>>>(L, lo, tail, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_pass(Lattice L, uint32_t lo, uint32_t tail, uint32_t step, int grid,
+                               cudaStream_t s) {
+  if (lo >= tail) return cudaSuccess;
+  switch (L.tw) {
+    case 16: return go_wp<16>(L, lo, tail, step, grid, s);
+    case 8: return go_wp<8>(L, lo, tail, step, grid, s);
+    case 4: return go_wp<4>(L, lo, tail, step, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 __global__ void k_set_ev_limit(Ctrl *C, uint32_t limit) { C->ev_limit = limit; }
 
 cudaError_t launch_set_ev_limit(Ctrl *C, uint32_t limit, cudaStream_t s) {

@@ -306,6 +306,7 @@ __device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, Ctrl
       ++ch;
     }
   }
+  if (c.n_newbox) c.last_promo = g;
   c.tests = c.tests + (unsigned long long)c.n_live * (last - first);
   c.n_cohorts = n_cohorts;
   c.tail = tail;
@@ -326,6 +327,7 @@ __device__ __forceinline__ void finish_stop_with(const Lattice &L, Ctrl *C, Ctrl
   C->head = c.head;
   C->head_birth = c.head_birth;
   C->n_newbox = 0; C->n_pruned = 0; C->n_solid = 0; C->gen_ticket = 0;
+  C->last_promo = c.last_promo;
   C->n_trace = c.n_trace;
   C->step = c.step;
   if (n_live == 0) {

@@ -267,14 +267,14 @@ ALGORITHMS = {"paralleldic": 0, "classic": 1}
 
 
 PRESTAGE = {"auto": 0, "off": 1}
-STOP_LOOPS = {"per-stop": 0, "events": 1}
+STOP_LOOPS = {"auto": 0, "events": 1, "per-stop": 2}
 
 
 def options(path: str = "auto", steps_per_sync: int = 0, use_graph: bool = True,
             profile=False, max_candidates: int = 0, profile_every: int = 0,
             tile_words: int = 0, count_form: str = "auto",
             algorithm: str = "paralleldic", prestage: str = "auto",
-            stop_loop: str = "per-stop") -> Options:
+            stop_loop: str = "auto") -> Options:
     o = Options()
     _lib.dic_options_init(ctypes.byref(o))
     o.count_path = PATHS[path]
@@ -295,15 +295,16 @@ def mine(db: Database, minsup: int, M: int, path: str = "auto", stream=None,
          profile=False, steps_per_sync: int = 0, use_graph: bool = True,
          max_candidates: int = 0, profile_every: int = 0, tile_words: int = 0,
          count_form: str = "auto", algorithm: str = "paralleldic",
-         prestage: str = "auto", stop_loop: str = "per-stop") -> Result:
+         prestage: str = "auto", stop_loop: str = "auto") -> Result:
     """All itemsets with support >= minsup (integer count), blocks of M rows.
     algorithm: "paralleldic" (Algorithm 2, first pass then pairs) or
     "classic" (Algorithm 1, every 1-itemset a dashed circle). prestage:
     "auto" (stage every block's columns, and count the pair cohort over the
     whole pass, before the loop when they fit) or "off" (per stop).
-    stop_loop: "per-stop" (every dashed itemset counted at every stop) or
-    "events" (event-driven where it applies: each cohort counted over its
-    whole pass when born, only stops with promotions generate)."""
+    stop_loop: "auto" (per stop, handing over to the event-driven form once
+    promotions have stopped), "events" (event-driven where it applies: each
+    cohort counted over its whole pass when born, only stops with promotions
+    generate) or "per-stop" (every dashed itemset counted at every stop)."""
     o = options(path, steps_per_sync, use_graph, profile, max_candidates, profile_every,
                 tile_words, count_form, algorithm, prestage, stop_loop)
     h = ctypes.c_void_p()

@@ -33,7 +33,7 @@ def to_csr(rows):
 def both_forms(dic, rp, it, n, m, minsup, M, **kw):
     db = dic.load_db_csr(rp, it, n, m)
     ev = dic.mine(db, minsup, M, path="tensor", stop_loop="events", **kw)
-    ps = dic.mine(db, minsup, M, path="tensor", **kw)
+    ps = dic.mine(db, minsup, M, path="tensor", stop_loop="per-stop", **kw)
     db.free()
     assert ev.stats["event_loop"] == 1 and ps.stats["event_loop"] == 0
     assert ev.itemsets() == ps.itemsets()
@@ -120,3 +120,24 @@ def test_dense_reduced_rows(dic):
     ref = oracle.dic(db.row_ptr, db.items, db.n, db.m, db.minsup, 400, superset_loop=False)
     assert ev.itemsets() == ref.itemsets
     assert ev.trace.tolist() == ref.trace.tolist()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_hand_over_from_the_per_stop_loop(dic, seed):
+    """stop_loop "auto": the per-stop loop hands the rest of the loop to the
+    event-driven form once the pair cohort has passed and promotions have
+    stopped; the live records are counted over the blocks left of their
+    passes from their counts so far. Result, trace and test count equal the
+    per-stop loop's and the oracle's."""
+    rp, it = synth.planted(seed=seed, n=4000, m=60, n_patterns=40, pat_len_mean=4.0,
+                           tx_len_mean=9.0)
+    n, m, minsup, M = 4000, 60, 60, 40   # 100 blocks
+    db = dic.load_db_csr(rp, it, n, m)
+    au = dic.mine(db, minsup, M, path="tensor")
+    ps = dic.mine(db, minsup, M, path="tensor", stop_loop="per-stop")
+    db.free()
+    ref = oracle.dic(rp, it, n, m, minsup, M, superset_loop=False)
+    assert au.stats["event_loop"] == 2 and ps.stats["event_loop"] == 0
+    assert au.itemsets() == ps.itemsets() == ref.itemsets
+    assert au.trace.tolist() == ps.trace.tolist() == ref.trace.tolist()
+    assert au.stats["tests"] == ps.stats["tests"] == ref.tests
