@@ -103,9 +103,13 @@ def roofline_of(kind, stats, shares_ms, step_ms, db, count_form="auto", trace=No
     nl = sum(s[nkey[kind]] if kind in nkey else s["path_launches"][3] for s in stats)
     avg_ms = tot_ms / max(nl, 1)
     st = stats[0]
-    ev = bool(st.get("event_loop"))
+    # event_loop 1: event-driven throughout; 2: per stop, then handed over
+    # (only the per-stop stops are timed)
+    ev = st.get("event_loop") == 1
     common = {"avg_launch_ms": avg_ms, "launches_timed": nl,
               "timed_stops": (f"one loop iteration in {PROFILE_EVERY} of the timed steps" if ev
+                              else f"one stop in {PROFILE_EVERY} of the per-stop part of the "
+                              "timed steps" if st.get("event_loop") == 2
                               else f"one stop in {PROFILE_EVERY} of the timed steps"),
               "kind_ms_per_step_warmup": {k: v for k, v in shares_ms.items()}}
     if kind == "gram":

@@ -617,6 +617,7 @@ class Miner {
   bool evmode_ = false;
   bool ev_ok_ = false;       // the event-driven form can take the loop
   bool ev_switched_ = false; // it took over from the per-stop form
+  uint64_t switch_step_ = 0;  // first stop it closed
   dic_status switch_to_events();
   dic_status alloc_event_buffers();
   cudaGraph_t evg_ = nullptr;
@@ -1561,6 +1562,7 @@ dic_status Miner::switch_to_events() {
   L_.events = 1;
   evmode_ = true;
   ev_switched_ = true;
+  switch_step_ = h_ctrl_->step;
   ++lat_version_;
   h_ctrl_->ev_pending = 0;
   h_ctrl_->ev_iter = 0;
@@ -1582,7 +1584,9 @@ dic_status Miner::loop_events() {
   // launch at a time: the graph runs up to the next profiled iteration (its
   // limit), that iteration is launched directly between CUDA events, and the
   // graph resumes. Without it one graph launch runs the whole loop.
-  const bool prof_iters = (opt_.profile & (DIC_PROFILE_COUNT | DIC_PROFILE_GEN)) != 0;
+  // (after a hand-over the per-stop stops alone are timed)
+  const bool prof_iters =
+      !ev_switched_ && (opt_.profile & (DIC_PROFILE_COUNT | DIC_PROFILE_GEN)) != 0;
   const uint32_t every = opt_.profile_every > 1 ? opt_.profile_every : 1u;
   const bool graph = opt_.use_graph && !(prof_iters && every == 1);
   while (!h_ctrl_->done) {
@@ -1775,7 +1779,7 @@ dic_status Miner::collect(dic_result **out) {
     const unsigned long long *tr = tr_b.p;
     res->trace.assign(tr, tr + (size_t)ntr * TRACE_COLS);
     res->stats.stops = ntr;
-    if (evmode_ && (opt_.profile & DIC_PROFILE_COUNT)) {
+    if (evmode_ && !ev_switched_ && (opt_.profile & DIC_PROFILE_COUNT)) {
       // count work of the profiled iterations' cohort passes
       const uint32_t ni = std::min<uint32_t>(h_ctrl_->ev_iter, L_.ehcap);
       std::vector<unsigned long long> ew(ni);
@@ -1791,7 +1795,8 @@ dic_status Miner::collect(dic_result **out) {
       uint64_t timed = 0;
       for (uint32_t i = 0; i < ntr; ++i) {
         const uint64_t step = tr[(size_t)i * TRACE_COLS];
-        const bool profiled = opt_.profile_every <= 1 || step % opt_.profile_every == 0;
+        const bool profiled = (opt_.profile_every <= 1 || step % opt_.profile_every == 0) &&
+                              (!ev_switched_ || step < switch_step_);
         if (profiled) timed += tw[i] - (i ? tw[i - 1] : 0ull);
       }
       res->stats.count_ops_timed = timed;

@@ -135,7 +135,12 @@ def test_hand_over_from_the_per_stop_loop(dic, seed):
     db = dic.load_db_csr(rp, it, n, m)
     au = dic.mine(db, minsup, M, path="tensor")
     ps = dic.mine(db, minsup, M, path="tensor", stop_loop="per-stop")
+    # profiling times the per-stop stops only and changes nothing
+    pr = dic.mine(db, minsup, M, path="tensor", profile=["count", "gen"], profile_every=3)
     db.free()
+    assert pr.stats["event_loop"] == 2
+    assert pr.itemsets() == au.itemsets() and pr.trace.tolist() == au.trace.tolist()
+    assert pr.stats["count_launches"] >= 1 and pr.stats["count_ops_timed"] > 0
     ref = oracle.dic(rp, it, n, m, minsup, M, superset_loop=False)
     assert au.stats["event_loop"] == 2 and ps.stats["event_loop"] == 0
     assert au.itemsets() == ps.itemsets() == ref.itemsets
