@@ -1569,10 +1569,20 @@ dic_status Miner::switch_to_events() {
   h_ctrl_->ev_limit = ~0u;
   h_ctrl_->ev_ticket = 0;
   CU(cudaMemcpyAsync(L_.ctrl, h_ctrl_, sizeof(Ctrl), cudaMemcpyHostToDevice, s_));
-  const uint32_t lo = std::max(h_ctrl_->head, L_.pair_end);
-  cudaError_t e = launch_window_pass(L_, lo, h_ctrl_->tail, h_ctrl_->step, cp_grid_, s_);
-  if (e != cudaSuccess) return fail(DIC_ECUDA, "window pass launch: %s", cudaGetErrorString(e));
-  ++launches_;
+  const uint32_t lo = std::max(h_ctrl_->head, L_.pair_end), tail = h_ctrl_->tail;
+  if (lo >= tail) return DIC_OK;
+  const uint32_t batch = window_pass_batch(L_.stop_max, tail - lo);
+  uint32_t *rows = nullptr, *tick = nullptr;
+  TRY(alloc(&rows, (size_t)batch * L_.stop_max));
+  TRY(alloc(&tick, batch, true));
+  for (uint32_t b = lo; b < tail; b += batch) {
+    const uint32_t hi = tail - b > batch ? b + batch : tail;
+    cudaError_t e = launch_window_pass(L_, b, hi, h_ctrl_->step, rows, tick, cp_grid_, s_);
+    if (e != cudaSuccess) return fail(DIC_ECUDA, "window pass launch: %s", cudaGetErrorString(e));
+    ++launches_;
+  }
+  drop(rows);
+  drop(tick);
   return DIC_OK;
 }
 

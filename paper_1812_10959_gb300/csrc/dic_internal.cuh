@@ -328,9 +328,13 @@ cudaError_t launch_cohort_pass(Lattice L, int grid, uint32_t budget, uint32_t us
 // Hand the loop from the per-stop form to the event-driven one at a stop
 // boundary: every live record of three or more items in [lo, tail) is
 // counted over the blocks left of its pass, from its count so far, and its
-// events are tallied as the cohort pass does (kernels_events.cu).
-cudaError_t launch_window_pass(Lattice L, uint32_t lo, uint32_t tail, uint32_t step, int grid,
-                               cudaStream_t s);
+// events are tallied as the cohort pass does (kernels_events.cu). One launch
+// takes the records of [lo, hi), at most window_pass_batch(stop_max, n) of
+// them, with scratch rows[batch][stop_max] (uninitialised) and tick[batch]
+// (zero; left zero).
+uint32_t window_pass_batch(uint32_t stop_max, uint32_t nrec);
+cudaError_t launch_window_pass(Lattice L, uint32_t lo, uint32_t hi, uint32_t step,
+                               uint32_t *rows, uint32_t *tick, int grid, cudaStream_t s);
 // Set Ctrl.ev_limit (stream-ordered).
 cudaError_t launch_set_ev_limit(Ctrl *C, uint32_t limit, cudaStream_t s);
 size_t cohort_pass_smem(uint32_t stop_max, uint32_t l1);

@@ -31,6 +31,7 @@
 //   k_generate_finish  MAKECANDIDATES at the prepared stop (Lattice.events:
 //                      generation only; the next cohort pass closes the
 //                      stop).
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -178,16 +179,17 @@ __device__ void ev_advance(const Lattice &L, Ctrl *C, uint32_t budget, uint32_t 
 // at a time; the 16-byte words of four ranks are loaded for all U items
 // before any AND (a rank index past k repeats rank 0: ANDing a column twice
 // changes nothing), then each item's popc goes to its block's counter.
+// Threads tid = 0..nt-1 of the caller's group (the CTA, or one warp) share
+// the work items.
 template <int TW>
 __device__ __forceinline__ void cp_count(const Lattice &L, const uint16_t *s_rank, uint32_t k,
                                          uint32_t b0, uint32_t b1, uint32_t nvmax,
-                                         uint32_t *s_cnt) {
+                                         uint32_t *s_cnt, uint32_t tid, uint32_t nt) {
   constexpr uint32_t ST = bs_stride(TW);
   constexpr int U = 4;
   const uint32_t l1p = L.l1p;
   const uint64_t items = (uint64_t)(b1 - b0) * nvmax;
-  const uint32_t nt = blockDim.x;
-  for (uint64_t it0 = threadIdx.x; it0 < items; it0 += (uint64_t)nt * U) {
+  for (uint64_t it0 = tid; it0 < items; it0 += (uint64_t)nt * U) {
     const uint32_t *Vu[U];
     uint32_t blk[U];
 #pragma unroll
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(CP_THREADS, 2) k_cohort_pass(Lattice L, uint32
     for (uint32_t a = threadIdx.x; a < b1 - b0; a += blockDim.x) s_cnt[a] = 0;
     __syncthreads();
     const uint32_t k = s_k;
-    if (k) cp_count<TW>(L, s_rank, k, b0, b1, nvmax, s_cnt);
+    if (k) cp_count<TW>(L, s_rank, k, b0, b1, nvmax, s_cnt, threadIdx.x, blockDim.x);
     __syncthreads();
     if (R == 1) {
       if (threadIdx.x < 32) cp_events(L, C, c, g, s_cnt, false);
@@ -422,144 +424,209 @@ __global__ void __launch_bounds__(CP_THREADS, 2) k_cohort_pass(Lattice L, uint32
   }
 }
 
-// Window pass (the hand-over from the per-stop loop at stop `step`): one
-// CTA per live record c of [lo, tail) at a time. The record has been counted
-// over ages 1..a0 (a0 = step - 1 - birth blocks) and holds that count in
-// csupp; its blocks of ages a0 + 1..S (a cyclic range of block indices, at
-// most two runs) are counted now, and warp 0 continues Algorithm 4 from there
-// in stop order: a circle's promotion or erase stop, a box's full-pass
-// support; the tallies and box-set entries are those of the cohort pass.
+// Window pass (the hand-over from the per-stop loop at stop `step`) over the
+// live records c of [lo, hi). A record has been counted over ages 1..a0
+// (a0 = step - 1 - birth blocks) and holds that count in csupp; its blocks
+// of ages a0 + 1..S (a cyclic range of block indices) are counted now, in
+// work units of up to `cb` blocks shared out among all warps: a record born
+// just before the hand-over has nearly a whole pass left, one near the end
+// of its pass a block or two, and units keep the warps evenly loaded. A
+// unit's per-block counts go to the record's scratch row rows[c - lo][block];
+// the warp that finishes the record's last unit (ticket tick[c - lo]) scans
+// the row in stop order and continues Algorithm 4 from there: a circle's
+// promotion or erase stop, a box's full-pass support; the tallies and
+// box-set entries are those of the cohort pass. Each warp first looks at 32
+// units at once (a lane each: the record's shape and birth) and counts only
+// those that are live.
+constexpr uint32_t WP_CBMAX = 64;  // blocks per unit at most
+constexpr uint32_t WP_WARPS = CP_THREADS / 32;
+
 template <int TW>
-__global__ void __launch_bounds__(CP_THREADS, 2) k_window_pass(Lattice L, uint32_t lo,
-                                                               uint32_t tail, uint32_t step) {
+__global__ void __launch_bounds__(CP_THREADS, 2)
+    k_window_pass(Lattice L, uint32_t lo, uint32_t hi, uint32_t step, uint32_t cb,
+                  uint32_t rank_stride, uint32_t *__restrict__ rows,
+                  uint32_t *__restrict__ tick) {
   extern __shared__ __align__(16) uint8_t cps[];
-  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(cps);
-  uint16_t *s_rank = reinterpret_cast<uint16_t *>(cps + (size_t)L.stop_max * 4);
-  __shared__ uint32_t s_k, s_birth, s_a0, s_cum, s_sh;
+  __shared__ uint32_t s_cnt_all[WP_WARPS][WP_CBMAX];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   Ctrl *C = L.ctrl;
-  const uint32_t S = L.stop_max;
+  const uint32_t S = L.stop_max, P = (S + cb - 1) / cb;
+  uint32_t *s_cnt = s_cnt_all[warp];
+  uint16_t *s_rank = reinterpret_cast<uint16_t *>(cps) + (size_t)warp * rank_stride;
   const uint64_t blockmax = L.M < L.n ? L.M : L.n;
   const uint32_t nw32max = (uint32_t)((blockmax + 31) / 32);
   const uint32_t nvmax = (nw32max + 3) / 4;
   const uint64_t last_rows = L.n - (uint64_t)(S - 1) * L.M;
+  const uint32_t last_w32 = (uint32_t)((last_rows + 31) / 32);
+  const uint64_t units = (uint64_t)(hi - lo) * P;
+  const uint64_t gw = (uint64_t)blockIdx.x * nwarp + warp, nw = (uint64_t)gridDim.x * nwarp;
   unsigned long long work = 0;
-  for (uint32_t c = lo + blockIdx.x; c < tail; c += gridDim.x) {
-    if (threadIdx.x == 0) {
-      const uint8_t sh = L.cshape[c];
-      const uint32_t birth = L.cbirth[c];
+  for (uint64_t r0 = 0; gw + r0 * nw < units; r0 += 32) {
+    // lane i looks at unit gw + (r0 + i) * nw
+    const uint64_t u = gw + (r0 + lane) * nw;
+    uint32_t ci = 0, part = 0, birth = 0, sh = SH_NIL;
+    bool live = false;
+    if (u < units) {
+      ci = (uint32_t)(u / P);
+      part = (uint32_t)(u % P);
+      sh = L.cshape[lo + ci];
+      birth = L.cbirth[lo + ci];
       const uint32_t a0 = step - 1 - birth;
-      s_sh = (sh == SH_NIL || a0 >= S) ? (uint32_t)SH_NIL : sh;
-      s_birth = birth;
-      s_a0 = a0;
-      s_cum = L.csupp[c];
-      uint32_t k = L.ck[c];
+      live = sh != SH_NIL && a0 < S && part * cb < S - a0;
+    }
+    for (uint32_t bal = __ballot_sync(0xffffffffu, live); bal; bal &= bal - 1) {
+      const int src = __ffs(bal) - 1;
+      const uint32_t uci = __shfl_sync(0xffffffffu, ci, src);
+      const uint32_t upart = __shfl_sync(0xffffffffu, part, src);
+      const uint32_t ub = __shfl_sync(0xffffffffu, birth, src);
+      const uint32_t ush = __shfl_sync(0xffffffffu, sh, src);
+      const uint32_t c = lo + uci, a0 = step - 1 - ub, len = S - a0;
+      const uint32_t nparts = (len + cb - 1) / cb, off = upart * cb;
+      const uint32_t cnt = len - off < cb ? len - off : cb;
+      uint32_t k = 0;
+      if (lane == 0) k = L.ck[c];
+      k = __shfl_sync(0xffffffffu, k, 0);
       if (k <= (uint32_t)KRMAX) {
-        for (uint32_t q = 0; q < k; ++q) s_rank[q] = L.cranks[(uint64_t)c * KRMAX + q];
+        if (lane < k) s_rank[lane] = L.cranks[(uint64_t)c * KRMAX + lane];
       } else {
-        k = 0;
-        for (uint32_t i = 0; i < L.wc; ++i)
-          for (uint64_t x = L.cmask[(uint64_t)c * L.wc + i]; x; x &= x - 1)
-            if (k < L.l1) s_rank[k++] = (uint16_t)(i * 64 + __ffsll((long long)x) - 1);
-      }
-      s_k = k;
-    }
-    for (uint32_t a = threadIdx.x; a < S; a += blockDim.x) s_cnt[a] = 0;
-    __syncthreads();
-    const uint32_t sh = s_sh, k = s_k, birth = s_birth, a0 = s_a0;
-    if (sh != SH_NIL && k) {
-      // blocks of ages a0 + 1 .. S: from (birth + a0) mod S on, S - a0 of them
-      const uint32_t x = (birth + a0) % S, len = S - a0;
-      const uint32_t e1 = x + len < S ? x + len : S;
-      cp_count<TW>(L, s_rank, k, x, e1, nvmax, s_cnt + x);
-      if (x + len > S) cp_count<TW>(L, s_rank, k, 0, x + len - S, nvmax, s_cnt);
-    }
-    __syncthreads();
-    if (sh != SH_NIL && threadIdx.x < 32) {
-      const uint32_t lane = threadIdx.x;
-      uint64_t rest = 0;
-      for (uint32_t a = lane; a < S; a += 32) rest += s_cnt[a];
-      for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
-      const uint64_t total = s_cum + rest;
-      uint32_t ev_age = 0, ev_promote = 0;
-      uint64_t ev_cum = 0;
-      if (sh == SH_CIRCLE) {
-        uint64_t carry = s_cum;
-        for (uint32_t base = a0; base < S; base += 32) {
-          const uint32_t age = base + lane + 1;
-          const uint32_t v = age <= S ? s_cnt[(birth + age - 1) % S] : 0u;
-          uint64_t cum = v;
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xffffffffu, cum, o);
-            if (lane >= (uint32_t)o) cum += y;
-          }
-          cum += carry;
-          const bool prom = age <= S && cum >= L.minsup;
-          const bool drop = age <= S && cum + L.M * (uint64_t)(S - age) < (uint64_t)L.minsup;
-          const uint32_t bal = __ballot_sync(0xffffffffu, prom || drop);
-          if (bal) {
-            const int src = __ffs(bal) - 1;
-            ev_age = base + src + 1;
-            ev_promote = __shfl_sync(0xffffffffu, prom ? 1u : 0u, src);
-            ev_cum = __shfl_sync(0xffffffffu, cum, src);
-            break;
-          }
-          carry = __shfl_sync(0xffffffffu, cum, 31);
+        if (lane == 0) {
+          k = 0;
+          for (uint32_t i = 0; i < L.wc; ++i)
+            for (uint64_t x = L.cmask[(uint64_t)c * L.wc + i]; x; x &= x - 1)
+              if (k < L.l1) s_rank[k++] = (uint16_t)(i * 64 + __ffsll((long long)x) - 1);
         }
+        k = __shfl_sync(0xffffffffu, k, 0);
       }
+      for (uint32_t j = lane; j < cb; j += 32) s_cnt[j] = 0;
+      __syncwarp();
+      // this unit's blocks: cnt of them from (birth + a0 + off) mod S on
+      const uint32_t x = (ub + a0 + off) % S;
+      const uint32_t e1 = x + cnt < S ? x + cnt : S;
+      if (k) {
+        cp_count<TW>(L, s_rank, k, x, e1, nvmax, s_cnt, lane, 32);
+        if (x + cnt > S) cp_count<TW>(L, s_rank, k, 0, x + cnt - S, nvmax, s_cnt + (S - x), lane, 32);
+      }
+      __syncwarp();
+      uint32_t *row = rows + (uint64_t)uci * S;
+      for (uint32_t j = lane; j < cnt; j += 32) row[(x + j) % S] = s_cnt[j];
+      __syncwarp();
+      uint32_t last = 0;
       if (lane == 0) {
-        const uint32_t solid_at = birth + S;
-        if (solid_at + 1 >= L.ehcap || (sh == SH_CIRCLE && ev_age == 0)) {
-          C->error = DIC_INTERNAL_BOUNDS;
-        } else if (sh == SH_BOX) {  // promoted earlier: the rest of its pass
-          L.csupp[c] = (uint32_t)total;
-          atomicAdd(&L.eh_solid[solid_at], 1u);
-        } else if (ev_promote) {
-          const uint32_t p = birth + ev_age;
-          L.csupp[c] = (uint32_t)total;
-          L.cshape[c] = SH_BOX;
-          L.cpromo[c] = p;
-          box_insert(L, c, mask_hash_sum(L.cmask + (uint64_t)c * L.wc, L.wc));
-          const uint32_t i = atomicAdd(&L.eh_box[p], 1u);
-          if (i < EV_LIST) L.eb_list[(uint64_t)p * EV_LIST + i] = c;
-          atomicAdd(&L.eh_solid[solid_at], 1u);
-        } else {
-          const uint32_t p = birth + ev_age;
-          L.csupp[c] = (uint32_t)ev_cum;
-          L.cshape[c] = SH_NIL;
-          atomicAdd(&L.eh_pruned[p], 1u);
+        __threadfence();
+        const uint32_t t = atomicAdd(&tick[uci], 1u);
+        last = t == nparts - 1 ? 1u : 0u;
+        if (last) {
+          __threadfence();
+          tick[uci] = 0;  // ready for the next batch
         }
-        // 32-row words of the blocks counted now
-        uint64_t words = 0;
-        for (uint32_t a = a0 + 1; a <= S; ++a) {
-          const uint32_t bl = (birth + a - 1) % S;
-          words += bl + 1 == S ? (last_rows + 31) / 32 : nw32max;
-        }
-        work += (unsigned long long)(k + 1) * words;
       }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        uint32_t cum0 = 0;
+        if (lane == 0) cum0 = L.csupp[c];
+        cum0 = __shfl_sync(0xffffffffu, cum0, 0);
+        uint64_t rest = 0;
+        for (uint32_t age = a0 + 1 + lane; age <= S; age += 32)
+          rest += __ldcg(row + (ub + age - 1) % S);
+        for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+        const uint64_t total = cum0 + rest;
+        uint32_t ev_age = 0, ev_promote = 0;
+        uint64_t ev_cum = 0;
+        if (ush == SH_CIRCLE) {
+          uint64_t carry = cum0;
+          for (uint32_t base = a0; base < S; base += 32) {
+            const uint32_t age = base + lane + 1;
+            const uint32_t v = age <= S ? __ldcg(row + (ub + age - 1) % S) : 0u;
+            uint64_t cum = v;
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint64_t y = __shfl_up_sync(0xffffffffu, cum, o);
+              if (lane >= (uint32_t)o) cum += y;
+            }
+            cum += carry;
+            const bool prom = age <= S && cum >= L.minsup;
+            const bool drop = age <= S && cum + L.M * (uint64_t)(S - age) < (uint64_t)L.minsup;
+            const uint32_t b2 = __ballot_sync(0xffffffffu, prom || drop);
+            if (b2) {
+              const int s2 = __ffs(b2) - 1;
+              ev_age = base + s2 + 1;
+              ev_promote = __shfl_sync(0xffffffffu, prom ? 1u : 0u, s2);
+              ev_cum = __shfl_sync(0xffffffffu, cum, s2);
+              break;
+            }
+            carry = __shfl_sync(0xffffffffu, cum, 31);
+          }
+        }
+        if (lane == 0) {
+          const uint32_t solid_at = ub + S;
+          if (solid_at + 1 >= L.ehcap || (ush == SH_CIRCLE && ev_age == 0)) {
+            C->error = DIC_INTERNAL_BOUNDS;
+          } else if (ush == SH_BOX) {  // promoted earlier: the rest of its pass
+            L.csupp[c] = (uint32_t)total;
+            atomicAdd(&L.eh_solid[solid_at], 1u);
+          } else if (ev_promote) {
+            const uint32_t p = ub + ev_age;
+            L.csupp[c] = (uint32_t)total;
+            L.cshape[c] = SH_BOX;
+            L.cpromo[c] = p;
+            box_insert(L, c, mask_hash_sum(L.cmask + (uint64_t)c * L.wc, L.wc));
+            const uint32_t i = atomicAdd(&L.eh_box[p], 1u);
+            if (i < EV_LIST) L.eb_list[(uint64_t)p * EV_LIST + i] = c;
+            atomicAdd(&L.eh_solid[solid_at], 1u);
+          } else {
+            const uint32_t p = ub + ev_age;
+            L.csupp[c] = (uint32_t)ev_cum;
+            L.cshape[c] = SH_NIL;
+            atomicAdd(&L.eh_pruned[p], 1u);
+          }
+          // 32-row words of the blocks counted now: len full blocks, the
+          // last block of the pass (index S - 1) shorter if among them
+          const uint32_t x0 = (ub + a0) % S;
+          const bool has_last = (S - 1 + S - x0) % S < len;
+          const uint64_t words =
+              (uint64_t)len * nw32max - (has_last ? (uint64_t)(nw32max - last_w32) : 0ull);
+          work += (unsigned long long)(k + 1) * words;
+        }
+      }
+      __syncwarp();  // the warp's shared counts and ranks are reused next
     }
-    __syncthreads();  // shared counts and ranks are reused by the next record
   }
-  if (threadIdx.x == 0 && work) atomicAdd(&C->work, work);
+  if (lane == 0 && work) atomicAdd(&C->work, work);
+}
+
+// Scratch of one window-pass launch: per-block count rows and tickets of
+// up to this many records (the host launches one batch after another).
+uint32_t window_pass_batch(uint32_t stop_max, uint32_t nrec) {
+  const uint64_t per = std::max<uint64_t>(1, (256ull << 20) / ((uint64_t)stop_max * 4));
+  return (uint32_t)std::min<uint64_t>(nrec, per);
 }
 
 template <int TW>
-static cudaError_t go_wp(Lattice L, uint32_t lo, uint32_t tail, uint32_t step, int grid,
-                         cudaStream_t s) {
-  const size_t smem = cohort_pass_smem(L.stop_max, L.l1);
+static cudaError_t go_wp(Lattice L, uint32_t lo, uint32_t hi, uint32_t step, uint32_t *rows,
+                         uint32_t *tick, int grid, cudaStream_t s) {
+  const uint64_t blockmax = L.M < L.n ? L.M : L.n;
+  const uint32_t nvmax = (uint32_t)(((blockmax + 31) / 32 + 3) / 4);
+  // about 512 work items (four 32-row words each) per unit
+  const uint32_t cb = std::max<uint32_t>(1, std::min<uint32_t>(WP_CBMAX, 512 / nvmax));
+  // each warp's ranks (a record's items, from its mask past KRMAX): as many
+  // warps per CTA, up to eight, as fit 96 KiB
+  const uint32_t rank_stride = (L.l1 + 7) & ~7u;
+  uint32_t nwarp = (uint32_t)((96u << 10) / ((size_t)rank_stride * 2));
+  nwarp = std::max<uint32_t>(1, std::min<uint32_t>(WP_WARPS, nwarp));
+  const size_t smem = (size_t)nwarp * rank_stride * 2;
   cudaError_t e = cudaFuncSetAttribute(k_window_pass<TW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_window_pass<TW><<<grid, CP_THREADS, smem, s>>>(L, lo, tail, step);
+  k_window_pass<TW><<<grid, nwarp * 32, smem, s>>>(L, lo, hi, step, cb, rank_stride, rows, tick);
   return cudaGetLastError();
 }
 
-cudaError_t launch_window_pass(Lattice L, uint32_t lo, uint32_t tail, uint32_t step, int grid,
-                               cudaStream_t s) {
-  if (lo >= tail) return cudaSuccess;
+cudaError_t launch_window_pass(Lattice L, uint32_t lo, uint32_t hi, uint32_t step,
+                               uint32_t *rows, uint32_t *tick, int grid, cudaStream_t s) {
+  if (lo >= hi) return cudaSuccess;
   switch (L.tw) {
-    case 16: return go_wp<16>(L, lo, tail, step, grid, s);
-    case 8: return go_wp<8>(L, lo, tail, step, grid, s);
-    case 4: return go_wp<4>(L, lo, tail, step, grid, s);
+    case 16: return go_wp<16>(L, lo, hi, step, rows, tick, grid, s);
+    case 8: return go_wp<8>(L, lo, hi, step, rows, tick, grid, s);
+    case 4: return go_wp<4>(L, lo, hi, step, rows, tick, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
