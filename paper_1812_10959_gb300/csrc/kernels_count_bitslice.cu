@@ -145,16 +145,21 @@ __global__ void __launch_bounds__(SLICE_THREADS) k_slice_all(Lattice L, const ui
       if (r1 >= 0) sout[((uint32_t)r1 - rlo) * OS + g] = hi;
     }
     __syncthreads();
-    // each rank's TW words of this tile, four per 16-byte store (a tile row
-    // starts on a 16-byte boundary: ST words are a multiple of four)
+    // each rank's ST words of this tile (its TW words, then the padding as
+    // zeros), four per 16-byte store: a tile row starts on a 16-byte
+    // boundary (ST words are a multiple of four), and writing the padding
+    // too leaves no 32-byte sector partly written (a partial sector costs
+    // the memory a read before the write)
     uint32_t *Vb = L.V + b * L.vwords;
-    const uint32_t nq = (rhi - rlo) * (TW / 4);
+    constexpr uint32_t SQ = ST / 4;
+    const uint32_t nq = (rhi - rlo) * SQ;
     for (uint32_t e = threadIdx.x; e < nq; e += blockDim.x) {
-      const uint32_t rr = e / (TW / 4), w = 4 * (e % (TW / 4));
+      const uint32_t rr = e / SQ, w = 4 * (e % SQ);
       const uint64_t idx = ((uint64_t)t * l1p + rlo + rr) * ST + w;
       if (idx + 3 < L.vwords && rlo + rr < l1p && rr < SRANKS) {
         const uint32_t *src = sout + rr * OS + w;
-        *reinterpret_cast<uint4 *>(Vb + idx) = make_uint4(src[0], src[1], src[2], src[3]);
+        *reinterpret_cast<uint4 *>(Vb + idx) =
+            w < TW ? make_uint4(src[0], src[1], src[2], src[3]) : make_uint4(0u, 0u, 0u, 0u);
       } else {
         L.ctrl->error = DIC_INTERNAL_BOUNDS;
       }
