@@ -10,13 +10,15 @@
 //
 // k_gram_pairs: one CTA per (128-rank A tile i, 256-rank B tile j >= i/2,
 // K split). The operands come from the stop's bit columns V (the BITSLICE
-// transposition, 32 rows per word): for every 128-row chunk, twelve
-// expander warps (a thread per rank row) load each rank's four column words
-// (a few chunks ahead, one 16-byte load) and write them to shared memory as
+// transposition, 32 rows per word): for every 256-row chunk, twelve
+// expander warps (a thread per rank row) load each rank's eight column words
+// (a chunk or two ahead, two 16-byte loads) and write them to shared memory as
 // e4m3 bytes (0, or 0x08 = 2^-6 for a set bit; the chunk's rows in a fixed
 // order along K, the same for both operands) in the K-major no-swizzle core-matrix layout
 // of tcgen05 (8 ranks x 16 rows per 128-byte core matrix), through a
-// 4-stage ring guarded by mbarriers; one thread of a seventeenth warp issues
+// 2-stage ring guarded by mbarriers (a stage of 256 rows halves the waits,
+// fences and arrivals per row of 128-row stages and gives each expander
+// eight independent words); one thread of a seventeenth warp issues
 // tcgen05.mma.kind::f8f6f4 (M = 128, N = 256, K = 32 per instruction, fp32
 // accumulation in tensor memory). Sixteen warps then bring the 128x256 tile
 // out with tcgen05.ld, turn its rows through shared memory and add the
@@ -39,13 +41,15 @@ namespace dic {
 
 constexpr uint32_t GM = 128;             // A-tile ranks (MMA M, TMEM lanes)
 constexpr uint32_t GN = 256;             // B-tile ranks (MMA N, TMEM columns)
-constexpr uint32_t GK = 128;             // rows (K) per chunk = bytes per rank row of a tile
-constexpr uint32_t GSTAGES = 4;
-constexpr uint32_t GTILE_A = GM * GK;    // 16 KiB
-constexpr uint32_t GTILE_B = GN * GK;    // 32 KiB
+constexpr uint32_t GK = 256;             // rows (K) per chunk = bytes per rank row of a tile
+constexpr uint32_t GSTAGES = 2;
+constexpr uint32_t GTILE_A = GM * GK;    // 32 KiB
+constexpr uint32_t GTILE_B = GN * GK;    // 64 KiB
+constexpr uint32_t GQ = GK / 128;        // 16-byte column loads (four words) per rank and chunk
+constexpr uint32_t GSBO = GK / 16 * 128; // bytes between 8-rank groups of a tile
 constexpr uint32_t GEXP_WARPS = 16;      // epilogue warps (4 TMEM lane quarters x 4)
 constexpr uint32_t GLOAD_WARPS = (GM + GN) / 32;  // expander warps: one thread per rank row
-constexpr uint32_t GPREFETCH = 4;        // chunks of column words loaded ahead
+constexpr uint32_t GPREFETCH = 2;        // chunks of column words loaded ahead
 constexpr uint32_t GEXP_THREADS = GEXP_WARPS * 32;
 constexpr uint32_t GRAM_THREADS = GEXP_THREADS + 32;  // + the MMA warp
 static_assert((GM + GN) % 32 == 0 && GLOAD_WARPS <= GEXP_WARPS, "expander warps");
@@ -55,11 +59,11 @@ constexpr long long WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz before giving 
 // c < 2^24; the epilogue scales back by 2^12.
 constexpr float GRAM_UNIT_INV = 4096.0f;
 
-// Byte offset of element (rank r, K position k) inside a tile of 128-row chunks:
-// core matrix (r/8, k/16) at (r/8)*1024 + (k/16)*128, element (r%8)*16 +
-// k%16.
+// Byte offset of element (rank r, K position k) inside a tile of GK-row
+// chunks: core matrix (r/8, k/16) at (r/8)*GSBO + (k/16)*128, element
+// (r%8)*16 + k%16.
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t k) {
-  return (r >> 3) * 1024u + (k >> 4) * 128u + (r & 7u) * 16u + (k & 15u);
+  return (r >> 3) * GSBO + (k >> 4) * 128u + (r & 7u) * 16u + (k & 15u);
 }
 
 // Rows j, j + 8, j + 16 and j + 24 of a 32-row column word x as four e4m3
@@ -207,8 +211,8 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
 
   if (warp < GLOAD_WARPS) {
     // expanders: thread rr owns rank row rr (the A tile's 128, then the B
-    // tile's 256) and writes its 128 rows of every chunk; the rank's four
-    // column words of a chunk are one 16-byte load, issued GPREFETCH chunks
+    // tile's 256) and writes its GK rows of every chunk; the rank's eight
+    // column words of a chunk are two 16-byte loads, issued GPREFETCH chunks
     // ahead
     const uint32_t rr = threadIdx.x;
     const bool is_a = rr < GM;
@@ -220,39 +224,50 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
     const uint32_t *col = vcols(L, g) + (ok ? rank : 0) * st;
     uint8_t *row0 = gsm + (is_a ? 0u : GSTAGES * GTILE_A) + core_offset(is_a ? rr : rr - GM, 0);
     const uint32_t stage_bytes = is_a ? GTILE_A : GTILE_B;
-    auto load = [&](uint32_t kc) -> uint4 {
-      const uint32_t w0 = kc * (GK / 32);
-      return ok ? __ldg(reinterpret_cast<const uint4 *>(col + (w0 >> tw_shift) * tile_words +
-                                                        (w0 & (tw - 1))))
-                : make_uint4(0u, 0u, 0u, 0u);
+    // the block's words end at a whole tile; a chunk's words past them
+    // (4-word tiles: the last chunk may reach past the last tile) read as 0
+    const uint32_t nw32 = (nrows + 31) / 32, wpad = (nw32 + tw - 1) / tw * tw;
+    auto load = [&](uint32_t kc, uint32_t h) -> uint4 {
+      const uint32_t w0 = kc * (GK / 32) + 4 * h;
+      return ok && w0 < wpad
+                 ? __ldg(reinterpret_cast<const uint4 *>(col + (w0 >> tw_shift) * tile_words +
+                                                         (w0 & (tw - 1))))
+                 : make_uint4(0u, 0u, 0u, 0u);
     };
-    uint4 q[GPREFETCH];
+    uint4 q[GPREFETCH][GQ];
 #pragma unroll
-    for (uint32_t d = 0; d < GPREFETCH; ++d) q[d] = d < nk ? load(kc0 + d) : make_uint4(0, 0, 0, 0);
+    for (uint32_t d = 0; d < GPREFETCH; ++d)
+#pragma unroll
+      for (uint32_t h = 0; h < GQ; ++h)
+        q[d][h] = d < nk ? load(kc0 + d, h) : make_uint4(0, 0, 0, 0);
     for (uint32_t i0 = 0; i0 < nk; i0 += GPREFETCH) {
 #pragma unroll
       for (uint32_t d = 0; d < GPREFETCH; ++d) {
         const uint32_t i = i0 + d;
         if (i >= nk || __shfl_sync(0xffffffffu, failed, 0)) break;  // warp-uniform
         const uint32_t s = i % GSTAGES, use = i / GSTAGES;
-        const uint4 w = q[d];
-        if (i + GPREFETCH < nk) q[d] = load(kc0 + i + GPREFETCH);
+        uint4 w[GQ];
+#pragma unroll
+        for (uint32_t h = 0; h < GQ; ++h) {
+          w[h] = q[d][h];
+          if (i + GPREFETCH < nk) q[d][h] = load(kc0 + i + GPREFETCH, h);
+        }
         // one lane per warp waits for the ring slot and one arrives for the
         // warp (the barrier counts warps, not threads)
         bool slot_ok = true;
         if (use > 0 && lane == 0) slot_ok = mbar_wait(&empty[s], (use - 1) & 1);
         if (!__shfl_sync(0xffffffffu, slot_ok ? 1u : 0u, 0)) { failed = 1; break; }
         uint8_t *dst = row0 + s * stage_bytes;
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-        // core matrix columns 2q and 2q + 1 take word q's 32 rows: bytes of
+        // core matrix columns 2v and 2v + 1 take word v's 32 rows: bytes of
         // rows {j, j+8, j+16, j+24} for j = 0..3, then for j = 4..7
 #pragma unroll
-        for (uint32_t q = 0; q < 4; ++q) {
-          const uint32_t x = ws[q];
-          *reinterpret_cast<uint4 *>(dst + (2 * q) * 128u) =
+        for (uint32_t v = 0; v < 4 * GQ; ++v) {
+          const uint4 &wq = w[v / 4];
+          const uint32_t x = v % 4 == 0 ? wq.x : v % 4 == 1 ? wq.y : v % 4 == 2 ? wq.z : wq.w;
+          *reinterpret_cast<uint4 *>(dst + (2 * v) * 128u) =
               make_uint4(spread_rows<0>(x), spread_rows<1>(x), spread_rows<2>(x),
                          spread_rows<3>(x));
-          *reinterpret_cast<uint4 *>(dst + (2 * q + 1) * 128u) =
+          *reinterpret_cast<uint4 *>(dst + (2 * v + 1) * 128u) =
               make_uint4(spread_rows<4>(x), spread_rows<5>(x), spread_rows<6>(x),
                          spread_rows<7>(x));
         }
@@ -262,7 +277,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
       }
     }
   } else if (warp == GEXP_WARPS && lane == 0) {
-    // MMA issuer: 4 instructions (K = 32 bytes each) per 128-row chunk
+    // MMA issuer: 8 instructions (K = 32 bytes each) per 256-row chunk
     for (uint32_t i = 0; i < nk; ++i) {
       const uint32_t s = i % GSTAGES, use = i / GSTAGES;
       if (failed || !mbar_wait(&full[s], use & 1)) { failed = 1; break; }
@@ -271,7 +286,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
       const uint32_t b0 = sm_addr(stage_b + s * GTILE_B);
 #pragma unroll
       for (uint32_t k = 0; k < GK / 32; ++k)
-        mma_f8(tmem, smem_desc(a0 + k * 256, 128, 1024), smem_desc(b0 + k * 256, 128, 1024),
+        mma_f8(tmem, smem_desc(a0 + k * 256, 128, GSBO), smem_desc(b0 + k * 256, 128, GSBO),
                (i | k) != 0);
       mma_commit(&empty[s]);
     }
