@@ -31,6 +31,7 @@
 // Every wait on an mbarrier is bounded; a wait that gives up records
 // DIC_ETIMEOUT in the loop state, lets the tensor instructions already
 // issued finish, frees the tensor memory and returns.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -149,7 +150,9 @@ __host__ __device__ __forceinline__ uint32_t gram_pairs_of(uint32_t na, uint32_t
 // counters (atomics; `nsplit` CTAs split each tile pair's rows).
 // ALL = true: CTA (block b, tile pair) writes the pairs' counts over block b
 // of the pass to pc[b * pairs + record] (plain stores; every pair of frequent
-// ranks gets one, zeros included), for all blocks in one launch.
+// ranks gets one, zeros included), for all blocks in one launch; with
+// `nsplit` > 1 (32-bit counts) nsplit CTAs split the block's rows and add
+// their partial counts to the zeroed array.
 template <bool ALL, class T>
 __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint32_t nsplit,
                                                                 uint32_t kre, T *pc) {
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
   const uint32_t na = (L.l1 + GM - 1) / GM, nb = (L.l1 + GN - 1) / GN;
   const uint32_t ntp = gram_pairs_of(na, nb);
   // stop g whose block this CTA counts (ALL: the stop of pass block b)
-  const uint32_t g = ALL ? blockIdx.x / ntp + 1 : C->step;
+  const uint32_t g = ALL ? blockIdx.x / (ntp * nsplit) + 1 : C->step;
   uint32_t stop;
   uint64_t first, last;
   block_of(g, L.stop_max, L.M, L.n, &stop, &first, &last);
@@ -174,9 +177,8 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
   if (!ALL && blockIdx.x == 0 && threadIdx.x == 0) C->gram_rows += nrows;
   const uint32_t nkc = (nrows + GK - 1) / GK;
   // which tile pair (A tile ti, B tile tj >= ti / 2) and which K split
-  const uint32_t pair = ALL ? blockIdx.x % ntp : blockIdx.x / nsplit;
-  const uint32_t split = ALL ? 0u : blockIdx.x % nsplit;
-  if (ALL) nsplit = 1;
+  const uint32_t pair = ALL ? (blockIdx.x / nsplit) % ntp : blockIdx.x / nsplit;
+  const uint32_t split = blockIdx.x % nsplit;
   uint32_t ti = 0, rem = pair;
   while (ti < na && rem >= nb - ti / 2) { rem -= nb - ti / 2; ++ti; }
   if (ti >= na) return;
@@ -335,7 +337,13 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram_pairs(Lattice L, uint3
         const uint64_t a = a0 + r;
         const uint32_t cnt = stage[r * 33 + lane];
         if (ALL) {
-          if (b > a && b < l1) pc_out[pair_record(a, b, l1)] = (T)cnt;
+          if (b > a && b < l1) {
+            if (nsplit == 1) {
+              pc_out[pair_record(a, b, l1)] = (T)cnt;
+            } else if (cnt) {  // K splits (32-bit counts only) meet in L2
+              if constexpr (sizeof(T) == 4) atomicAdd(&pc_out[pair_record(a, b, l1)], cnt);
+            }
+          }
         } else if (b > a && b < l1 && cnt) {
           atomicAdd(&L.csupp[pair_record(a, b, l1)], cnt);
         }
@@ -366,16 +374,35 @@ cudaError_t launch_gram_pairs(Lattice L, uint32_t nsplit, uint32_t kre, cudaStre
   return cudaGetLastError();
 }
 
+// A pass of few large blocks gives fewer (block, tile pair) CTAs than SMs:
+// with 32-bit counts each block's rows are then split across nsplit CTAs
+// (at least 16 chunks each) whose partial counts are added into the zeroed
+// count array.
 template <class T>
 static cudaError_t gram_all(Lattice L, T *pc, cudaStream_t s) {
   const uint64_t grid = (uint64_t)gram_tile_pairs(L.l1) * L.stop_max;
   if (grid == 0 || grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t nsplit = 1;
+  if (sizeof(T) == 4 && grid < (uint64_t)sms) {
+    const uint64_t blockmax = L.M < L.n ? L.M : L.n;
+    const uint64_t by_chunks = gram_chunks(blockmax) / 16;
+    const uint64_t want = ((uint64_t)sms + grid - 1) / grid;
+    nsplit = (uint32_t)std::max<uint64_t>(1, std::min(want, by_chunks));
+  }
+  if (nsplit > 1) {
+    const uint64_t l1 = L.l1;
+    cudaError_t e = cudaMemsetAsync(pc, 0, (size_t)L.stop_max * (l1 * (l1 - 1) / 2) * sizeof(T), s);
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = GSTAGES * (GTILE_A + GTILE_B);
   auto kern = k_gram_pairs<true, T>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)grid, GRAM_THREADS, smem, s>>>(L, 1u, 0u, pc);
+  kern<<<(unsigned)(grid * nsplit), GRAM_THREADS, smem, s>>>(L, nsplit, 0u, pc);
   return cudaGetLastError();
 }
 

@@ -281,3 +281,19 @@ def test_direct_launches_equal_graph_replays(dic, path):
     # one count launch per stop, or per iteration of the event-driven loop
     assert a.stats["count_launches"] >= (a.stats["event_iters"] if a.stats["event_loop"]
                                          else len(ref.trace))
+
+
+def test_pair_gemm_split_over_few_large_blocks(dic):
+    """Two blocks of 75,000 rows: the all-blocks pair GEMM has fewer (block,
+    tile pair) CTAs than SMs, so each block's rows are split across CTAs
+    whose 32-bit partial counts are added up. Result, trace and test count
+    equal the oracle's."""
+    n, m, minsup, M = 150_000, 300, 1_500, 75_000
+    rp, it = synth.planted(5, n, m, 60, 4.0, 9.0)
+    db = dic.load_db_csr(rp, it, n, m)
+    r = dic.mine(db, minsup, M, path="tensor")
+    db.free()
+    ref = oracle.dic(rp, it, n, m, minsup, M, superset_loop=False)
+    assert r.itemsets() == ref.itemsets
+    assert r.trace.tolist() == ref.trace.tolist()
+    assert r.stats["tests"] == ref.tests
