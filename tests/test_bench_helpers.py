@@ -35,6 +35,18 @@ def test_roofline_count_kind_is_alu_against_the_derived_peak():
     assert abs(r["frac"] - 0.5 / bench.ALU_PEAK_TOPS) < 1e-12
 
 
+def test_roofline_count_kernel_follows_the_stop_loop_form():
+    # per stop throughout, or handed over to the event-driven form (only the
+    # per-stop stops are timed): the per-stop count kernel; event-driven
+    # throughout: the cohort pass
+    for loop, kern in ((0, "k_count_direct"), (2, "k_count_direct"), (1, "k_cohort_pass")):
+        st = _stats(event_loop=loop, event_iters=3)
+        r = bench.roofline_of("count", [st], {"count": 2.0}, 10.0, _Db())
+        assert r["kernel"] == kern, (loop, r["kernel"])
+        assert ("loop iteration" in r["timed_stops"]) == (loop == 1)
+        assert ("per-stop part" in r["timed_stops"]) == (loop == 2)
+
+
 def test_roofline_gram_kind_is_tensor_against_fp8_peak():
     r = bench.roofline_of("gram", [_stats()], {"gram": 1.0}, 10.0, _Db())
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
