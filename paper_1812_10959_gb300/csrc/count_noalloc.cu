@@ -80,43 +80,36 @@ __global__ void k_noalloc_slice(const uint64_t *__restrict__ words, uint32_t W, 
   }
 }
 
-// supp[c] += rows of the slab containing masks[c]; 8 column words at a time.
+// supp[c] += rows of the slab containing masks[c]: one warp per candidate,
+// its lanes on consecutive 32-row column words (coalesced loads of each
+// item's column), the lanes' popcounts summed across the warp.
 __global__ void k_noalloc_count(const uint64_t *__restrict__ masks, uint32_t ncand, uint32_t W,
                                 uint32_t m, const uint32_t *__restrict__ cols, uint32_t vw,
                                 uint32_t nrows, uint32_t *__restrict__ supp) {
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t nw = (nrows + 31) / 32;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncand;
-       c += gridDim.x * blockDim.x) {
-    const uint64_t *mk = masks + (uint64_t)c * W;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncand;
+       c += nwarps) {
+    const uint64_t *mk = masks + c * W;
     uint32_t cnt = 0;
-    for (uint32_t w0 = 0; w0 < nw; w0 += 8) {
-      uint32_t acc[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t w = w0 + q;
-        // rows of the slab that exist: all 32 bits except in the last word
-        acc[q] = w < nw ? (w + 1 < nw || nrows % 32 == 0 ? 0xffffffffu
-                                                         : (1u << (nrows % 32)) - 1u)
-                        : 0u;
-      }
-      for (uint32_t j = 0; j < W; ++j) {
+    for (uint32_t w = lane; w < nw; w += 32) {
+      // rows of the slab that exist: all 32 bits except in the last word
+      uint32_t acc = w + 1 < nw || nrows % 32 == 0 ? 0xffffffffu : (1u << (nrows % 32)) - 1u;
+      for (uint32_t j = 0; j < W && acc; ++j) {
         for (uint64_t x = __ldg(mk + j); x; x &= x - 1) {
           const uint32_t item = j * 64 + (uint32_t)(__ffsll((long long)x) - 1);
           if (item >= m) {  // no row holds an item >= m
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] = 0;
-            continue;
+            acc = 0;
+            break;
           }
-          const uint32_t *col = cols + (uint64_t)item * vw + w0;
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (w0 + q < nw) acc[q] &= __ldg(col + q);
+          acc &= __ldg(cols + (uint64_t)item * vw + w);
         }
       }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) cnt += __popc(acc[q]);
+      cnt += __popc(acc);
     }
-    supp[c] += cnt;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) supp[c] += cnt;
   }
 }
 
@@ -171,7 +164,8 @@ extern "C" dic_status dic_count_support_noalloc(const uint64_t *dev_words, uint6
     cudaError_t e = cudaLaunchKernelEx(&cfg, k_noalloc_slice, dev_words, W, m, r0, nrows, cols, vw);
     if (e != cudaSuccess)
       return noalloc_fail(DIC_ECUDA, "dic_count_support_noalloc: slice launch failed");
-    int g2 = (int)((ncand + 255) / 256 < (uint32_t)sms * 8 ? (ncand + 255) / 256 : sms * 8);
+    // one warp per candidate, eight per CTA
+    int g2 = (int)((ncand + 7) / 8 < (uint32_t)sms * 8 ? (ncand + 7) / 8 : sms * 8);
     cfg.gridDim = dim3(g2);
     e = cudaLaunchKernelEx(&cfg, k_noalloc_count, dev_masks, ncand, W, m,
                            (const uint32_t *)cols, vw, nrows, dev_supp);
